@@ -1,0 +1,439 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the fused finite-volume Euler step (cell updates/s).
+
+Default workload: the 1M-triangle channel with a 10%-thick circular-arc bump
+(graded 4x over the bump and at the lower wall, jittered interior nodes,
+far-field inflow/outflow at Mach 0.5, slip walls), RCM cell order, FP32
+state, forward Euler at CFL 0.4.  One benchmark step = one call of the time
+loop (10,000 time steps, each one fused kernel, replayed as captured CUDA
+graphs) followed by the FP64 conserved totals -- every row of the hot path.
+
+Prints ONE JSON line.  Also reported: the same workload in FP64 (throughput,
+speedup of FP32 over it, and the FP32 error against it), the 16.8M-triangle
+periodic square (the HBM-bound headline), the roofline of the step kernel,
+the FP64 CPU oracle timed on one host core, and an end-to-end figure with
+host buffers.  `--impl reference` times the CPU oracle alone.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1408_5715_gb300 import workloads as W  # noqa: E402
+
+# Algorithmic bytes per cell update of one forward-Euler step: own state read
+# and written once, 6 normal components + 1/V, 3 neighbour ids (neighbour
+# states are counted as cache reuse, not DRAM traffic).
+ALGO_BYTES = {"f32": 16 + 16 + 28 + 12, "f64": 32 + 32 + 56 + 12}
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default="channel_bump_1m",
+                   choices=["channel_bump_1m", "square_16m", "vortex_square_small"])
+    p.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    p.add_argument("--scheme", default="fe", choices=["fe", "rk2"])
+    p.add_argument("--order", default=None, choices=["identity", "shuffle", "rcm", "hilbert"])
+    p.add_argument("--time-steps", type=int, default=None, help="time steps per benchmark step")
+    p.add_argument("--no-extras", action="store_true", help="skip FP64 / 16M / CPU / e2e legs")
+    return p.parse_args()
+
+
+WORKLOADS = {
+    "channel_bump_1m": dict(make=W.channel_bump_1m, init="uniform", mach=0.5, time_steps=10000,
+                            order="rcm", desc="channel 3x1, 10% circular-arc bump, 1250x400 quads, "
+                            "graded 4x, jitter 20%, far field M=0.5, slip walls"),
+    "square_16m": dict(make=W.vortex_square_16m, init="vortex", mach=0.5, time_steps=1000,
+                       order="hilbert", desc="periodic unit square, 4096x2048 quads, jitter 20%, "
+                       "isentropic vortex beta=5 M=0.5"),
+    "vortex_square_small": dict(make=W.vortex_square_small, init="vortex", mach=0.5,
+                                time_steps=100, order="shuffle",
+                                desc="periodic unit square, 64x32 quads, vortex"),
+}
+
+
+def initial_state(spec, mi):
+    if spec["init"] == "uniform":
+        return W.uniform_state(mi.n_tri, W.freestream(spec["mach"]))
+    return W.isentropic_vortex(mi.centroids(), mach=spec["mach"])
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", FALLBACK_HBM_GBS)), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    with open(os.path.join(ROOT, "paper_1408_5715_gb300", "csrc", "kernels.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def profiled_traffic(name):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
+    t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not h or not t or h.group(1) != kernel_source_hash():
+        return None
+    return float(t.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = os.path.join("/tmp", f"fv_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_id), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        rows = [[c.strip() for c in r] for r in rows if len(r) >= 8]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[0]) for r in rows if num(r[0]) is not None]
+        mx = [num(r[1]) for r in rows if num(r[1]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if r[4 + j] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows),
+                "power_w_max": max((num(r[2]) or 0.0) for r in rows)}
+
+
+def gpu_smi_id():
+    import torch
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    uuid = getattr(props, "uuid", None)
+    if uuid is not None:
+        s = str(uuid)
+        return s if s.startswith("GPU-") else "GPU-" + s
+    return os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]
+
+
+# ---------------------------------------------------------------------------
+# our implementation
+# ---------------------------------------------------------------------------
+def make_mesh(B, spec, mi, precision, order):
+    m = B.Mesh.from_input(mi, precision)
+    prim = W.freestream(spec["mach"])
+    m.set_freestream(*prim)
+    perm = m.renumber(order, seed=1)
+    return m, perm
+
+
+def timed_loop(m, U, U0dev, time_steps, steps, warmup, scheme, cfl=0.4, flush=None,
+               dist=None):
+    """Runs warmup + steps benchmark steps; returns per-step device times (s)."""
+    import torch
+    times = []
+    for it in range(warmup + steps):
+        U.copy_(U0dev)
+        if flush is not None:
+            flush.fill_(float(it))  # write > L2 so the step starts cold
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        m.step(U, time_steps, cfl, scheme=scheme, sync=False)
+        m.totals(U)  # FP64 totals; synchronises
+        e1.record()
+        torch.cuda.synchronize()
+        if it >= warmup:
+            times.append(e0.elapsed_time(e1) / 1e3)
+    m.status()  # raises if a bad state appeared
+    return times
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as tdist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+        dist = tdist
+    else:
+        torch.cuda.set_device(0)
+    from paper_1408_5715_gb300 import binding as B
+    from paper_1408_5715_gb300 import build as BLD
+    if local == 0:
+        BLD.build()
+    if dist is not None:
+        dist.barrier()
+    B.load()
+
+    spec = WORKLOADS[args.workload]
+    S = args.time_steps or spec["time_steps"]
+    order = args.order or spec["order"]
+    mi = spec["make"]()
+    U0 = initial_state(spec, mi)
+    n = mi.n_tri
+    prec = args.precision
+    tdt = torch.float32 if prec == "f32" else torch.float64
+    m, perm = make_mesh(B, spec, mi, prec, order)
+    U0p = U0[perm]
+    U0dev = torch.tensor(U0p, dtype=tdt, device="cuda")
+    U = torch.empty_like(U0dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    with ClockSampler(gpu_smi_id()) as clk:
+        times = timed_loop(m, U, U0dev, S, args.steps, args.warmup, args.scheme, flush=flush,
+                           dist=dist)
+    total = sum(times)
+    if dist is not None:
+        t = torch.tensor([total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+    updates = n * S * args.steps * world
+    value = updates / total
+    stages = 2 if args.scheme == "rk2" else 1
+    avg_launch = total / (args.steps * S * stages)  # includes the per-call small kernels
+    peak, peak_kind = measured_peaks()
+    achieved = ALGO_BYTES[prec] * n / avg_launch / 1e9  # GB/s of one step-kernel launch
+    U_final = U.double().cpu().numpy()
+    out = {
+        "metric": "cell updates/s",
+        "value": value,
+        "unit": "cell-updates/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": prec,
+        "data": "synthetic",
+        "config": {"workload": args.workload, "mesh": spec["desc"], "cells": n,
+                   "time_steps_per_step": S, "scheme": args.scheme, "cfl": 0.4, "order": order,
+                   "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "l2": "256 MB written between steps (L2 flushed); state+geometry "
+                         f"{n * (ALGO_BYTES[prec] + 8) / 1e6:.0f} MB"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind,
+                     "bytes_per_update": ALGO_BYTES[prec],
+                     "kernel": f"k_step<{'float' if prec == 'f32' else 'double'},FE>",
+                     "traffic": profiled_traffic(f"step_{prec}_{args.workload}.md")},
+        "gpu_launches": args.steps * (S * stages + 4),
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_extras and world == 1:
+        extras(args, B, spec, mi, U0, U0p, perm, m, S, U_final, out)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def extras(args, B, spec, mi, U0, U0p, perm, m32, S, U32_final, out):
+    import torch
+    n = mi.n_tri
+    # ---- same workload in FP64: throughput, speedup, error of FP32 against it
+    if args.precision == "f32":
+        m64, _ = make_mesh(B, spec, mi, "f64", out["config"]["order"])
+        U0d = torch.tensor(U0p, dtype=torch.float64, device="cuda")
+        U = torch.empty_like(U0d)
+        t64 = timed_loop(m64, U, U0d, S, 1, 1, args.scheme)
+        v64 = n * S / sum(t64)
+        U64 = U.cpu().numpy()
+        err = float(np.linalg.norm(U32_final[:, 0] - U64[:, 0]) / np.linalg.norm(U64[:, 0]))
+        out["fp64"] = {"value": v64, "unit": "cell-updates/s", "time_steps": S,
+                       "speedup_fp32_over_fp64": out["value"] / v64,
+                       "fp32_rel_l2_rho_vs_fp64": err, "tolerance": 1e-5}
+        del U, U0d
+        m64.close()
+    # ---- end to end through the public API with host buffers
+    tdt = torch.float32 if args.precision == "f32" else torch.float64
+    host_in = torch.tensor(U0p, dtype=tdt).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    Ud = torch.empty(host_in.shape, dtype=tdt, device="cuda")
+    times = []
+    for it in range(2):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        Ud.copy_(host_in, non_blocking=True)
+        m32.step(Ud, S, 0.4, scheme=args.scheme, sync=False)
+        tot = m32.totals(Ud)
+        host_out.copy_(Ud, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        if it > 0:
+            times.append(e0.elapsed_time(e1) / 1e3)
+    nb = host_in.numel() * host_in.element_size()
+    out["e2e"] = {"value": n * S / statistics.mean(times), "unit": "cell-updates/s",
+                  "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb + 32,
+                  "api": "fv_step + fv_conserved_totals on host-copied state"}
+    assert np.isfinite(tot).all()
+    # ---- the HBM-bound headline: 16.8M cells
+    if args.workload != "square_16m":
+        spec16 = WORKLOADS["square_16m"]
+        mi16 = spec16["make"]()
+        U16 = initial_state(spec16, mi16)
+        res = {}
+        for prec, steps16 in (("f32", 1000), ("f64", 100)):
+            m16, p16 = make_mesh(B, spec16, mi16, prec, spec16["order"])
+            tdt = torch.float32 if prec == "f32" else torch.float64
+            U0d = torch.tensor(U16[p16], dtype=tdt, device="cuda")
+            U = torch.empty_like(U0d)
+            tt = timed_loop(m16, U, U0d, steps16, 2, 1, "fe")
+            v = mi16.n_tri * steps16 / statistics.mean(tt)
+            gbs = ALGO_BYTES[prec] * v / 1e9
+            peak, _ = measured_peaks()
+            res[prec] = {"value": v, "unit": "cell-updates/s", "time_steps": steps16,
+                         "achieved_gbs": gbs, "frac_of_measured_hbm": gbs / peak,
+                         "traffic": profiled_traffic(f"step_{prec}_square_16m.md")}
+            del U, U0d
+            m16.close()
+        res["cells"] = mi16.n_tri
+        res["order"] = spec16["order"]
+        res["speedup_fp32_over_fp64"] = res["f32"]["value"] / res["f64"]["value"]
+        out["square_16m"] = res
+    # ---- FP64 CPU oracle on one host core, bounded sample of this workload
+    out["cpu_baseline"] = cpu_baseline(spec, mi, U0, budget_s=12.0)
+
+
+def cpu_baseline(spec, mi, U0, budget_s=12.0):
+    import oracle
+    oracle.build()
+    uinf = W.conserved(*W.freestream(spec["mach"]))
+    om = oracle.Mesh(mi.xy, mi.tri, mi.canon, mi.bnd, mi.default_bc, uinf)
+    t0 = time.perf_counter()
+    om.run(U0, 1, 0.4)
+    one = time.perf_counter() - t0
+    nsteps = max(1, int(budget_s / max(one, 1e-6)))
+    t0 = time.perf_counter()
+    _, _, done, _ = om.run(U0, nsteps, 0.4)
+    el = time.perf_counter() - t0
+    return {"value": mi.n_tri * done / el, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"{done} forward-Euler steps of the full {mi.n_tri}-cell mesh, FP64, "
+                      f"single thread ({el:.1f} s)",
+            "cpu": cpu_model()}
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return os.uname().machine
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 oracle as it stands, on the host cores
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    spec = WORKLOADS[args.workload]
+    mi = spec["make"]()
+    U0 = initial_state(spec, mi)
+    uinf = W.conserved(*W.freestream(spec["mach"]))
+    om = oracle.Mesh(mi.xy, mi.tri, mi.canon, mi.bnd, mi.default_bc, uinf)
+    per_step = 2  # time steps per benchmark step: a bounded sample of the workload
+    for _ in range(args.warmup):
+        om.run(U0, 1, 0.4)
+    t0 = time.perf_counter()
+    done = 0
+    for _ in range(args.steps):
+        _, _, d, _ = om.run(U0, per_step, 0.4)
+        done += d
+    el = time.perf_counter() - t0
+    v = mi.n_tri * done / el
+    out = {"metric": "cell updates/s", "value": v, "unit": "cell-updates/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "impl": "reference",
+           "config": {"workload": args.workload, "mesh": spec["desc"], "cells": mi.n_tri,
+                      "time_steps_per_step": per_step, "scheme": "fe", "cfl": 0.4},
+           "cpu_baseline": {"value": v, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+                            "sample": f"{per_step} FP64 forward-Euler steps of the full mesh per "
+                                      "benchmark step, single thread", "cpu": cpu_model()},
+           "e2e": {"value": v, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.warmup < 0 or args.steps < 1:
+        raise SystemExit("need --steps >= 1")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,175 @@
+/*
+ * fv.h -- C ABI of the GB300 library for the explicit cell-centred
+ * finite-volume step of the 2D Euler equations on triangles with the
+ * Lax-Friedrichs flux (Nagy et al., "Accelerating unstructured finite volume
+ * computations on field-programmable gate arrays", Sec. 6 and Sec. 7).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every function returns an int status (FV_OK = 0 or an FV_E* code).  On
+ *   failure fv_last_error() returns a message for the calling thread; nothing
+ *   else is changed unless the function says so.
+ * - Handles (fv_mesh, fv_batch, fv_closure) are opaque and owned by the
+ *   library until their *_destroy call.
+ * - State arrays are caller-owned device memory: n_cells records of four
+ *   values (rho, rho*u, rho*v, E) in the mesh precision (float for FV_F32,
+ *   double for FV_F64), record c at offset 4*c -- the conserved vector U of
+ *   Sec. 6.1.  The library never frees caller memory.
+ * - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *   stream).  Work is queued on it; only functions that return host values
+ *   (totals, time, status) synchronise it.
+ * - A mesh is built on the host; its device arrays are created on first
+ *   device use (or by fv_mesh_upload) on the current CUDA device, so the
+ *   host-side functions work on a machine without a GPU.  Device use of one
+ *   handle from several host threads at once is not supported.
+ * - Cell numbering: after fv_renumber, cell i of the mesh is the cell that
+ *   was number perm[i] before the call; states must be permuted alike.
+ */
+#ifndef FV_H_
+#define FV_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define FV_OK 0
+#define FV_EINVAL 1     /* bad argument or malformed mesh */
+#define FV_ENOMEM 2     /* host or device allocation failed */
+#define FV_ECUDA 3      /* a CUDA runtime call failed (message has the CUDA error) */
+#define FV_ENONFINITE 4 /* a step produced a non-finite state, rho <= 0 or p <= 0 */
+#define FV_ETIMEOUT 5   /* a bounded device wait gave up */
+
+/* ---- precision of a mesh's state and geometry ------------------------------ */
+#define FV_F32 0
+#define FV_F64 1
+
+/* ---- boundary tags of fv_mesh_create's bnd_edges (reading of Sec. 7: "ghost
+ * nodes ... implement inflow, outflow or wall boundary conditions") ---------- */
+#define FV_BC_NONE 0     /* no default: an unmatched edge is an error */
+#define FV_BC_WALL 1     /* slip wall: ghost mirrors the normal momentum */
+#define FV_BC_FARFIELD 2 /* far field: ghost is the free stream of fv_set_freestream */
+#define FV_BC_EXTRAP 3   /* extrapolation: ghost copies the interior state */
+
+/* ---- cell orders of fv_renumber (Sec. 4: renumbering for data locality) --- */
+#define FV_ORDER_IDENTITY 0
+#define FV_ORDER_SHUFFLE 1 /* uniform random permutation from the seed */
+#define FV_ORDER_RCM 2     /* reverse Cuthill-McKee from a pseudo-peripheral cell */
+#define FV_ORDER_HILBERT 3 /* Hilbert curve through the cell centroids */
+
+/* ---- time schemes of fv_step ----------------------------------------------- */
+#define FV_SCHEME_FE 0  /* forward Euler, Eq. 6 and the update equation of Sec. 6.2.2 */
+#define FV_SCHEME_RK2 1 /* two-stage Heun (SSP-RK2) with the same dt; not in the paper */
+
+typedef struct fv_mesh fv_mesh;
+typedef struct fv_batch fv_batch;
+typedef struct fv_closure fv_closure;
+
+/* Message of the last failed call on this thread ("" if none).  The pointer
+ * stays valid until the next failing call on the same thread. */
+const char* fv_last_error(void);
+
+/* ABI version of this header: 1. */
+int32_t fv_abi_version(void);
+
+/* ===========================================================================
+ * Mesh (Sec. 6.2.1 geometry; Sec. 7: each cell has three neighbours, ghost
+ * cells at boundaries; face sizes and normals are precomputed).
+ * ======================================================================== */
+
+/* Builds a mesh on the host.
+ *   xy[2*n_nodes]      node coordinates (x, y), host, read only.
+ *   tri[3*n_tri]       node ids per triangle, host; clockwise triangles are
+ *                      reoriented; face k of a triangle is the edge from its
+ *                      vertex k to vertex k+1 (mod 3) after reorientation.
+ *   node_canon         nullable, [n_nodes]: node -> node it is identified with
+ *                      (periodic domains).  Edges are matched on these ids;
+ *                      each cell's geometry comes from its own coordinates.
+ *   bnd_edges[3*n_bnd] nullable: (node a, node b, FV_BC_* tag) for edges that
+ *                      border no other cell.
+ *   default_bc         FV_BC_* tag for unmatched edges not in bnd_edges.
+ *   precision          FV_F32 or FV_F64.
+ * Errors: FV_EINVAL for a zero-area or non-finite triangle, an edge shared by
+ * more than two cells, an edge collapsed by node_canon, an out-of-range node
+ * id, or an unmatched edge without a tag.  The free stream defaults to
+ * rho = 1, u = v = 0, p = 1.  *out receives the handle. */
+int fv_mesh_create(const double* xy, int64_t n_nodes, const int32_t* tri, int64_t n_tri,
+                   const int32_t* node_canon, const int32_t* bnd_edges, int64_t n_bnd,
+                   int32_t default_bc, int32_t precision, fv_mesh** out);
+
+/* Frees the host and device arrays of the mesh (waits for its device work). */
+int fv_mesh_destroy(fv_mesh* mesh);
+
+/* Number of cells and precision of a mesh. */
+int fv_mesh_info(const fv_mesh* mesh, int64_t* n_cells, int32_t* precision);
+
+/* Free-stream primitive state (rho, u, v, p) used by far-field ghosts.
+ * rho and p must be positive and finite. */
+int fv_set_freestream(fv_mesh* mesh, double rho, double u, double v, double p);
+
+/* Renumbers the cells (Sec. 4) and remaps the neighbour table; each cell keeps
+ * its local face order.  perm_out (nullable, host, [n_cells]) receives the
+ * permutation new -> old relative to the numbering before this call.  seed is
+ * used by FV_ORDER_SHUFFLE only.  Device arrays are refreshed on next use. */
+int fv_renumber(fv_mesh* mesh, int32_t order, uint64_t seed, int32_t* perm_out);
+
+/* Locality diagnostics of the current numbering on the cell graph (Sec. 4.1):
+ * the bandwidth B_f(G) = max |f(u) - f(v)| over neighbouring cells, and the
+ * serial bandwidth S_BW = max_i E(i) - S(i) (nullable outputs). */
+int fv_mesh_diagnostics(const fv_mesh* mesh, int64_t* bandwidth, int64_t* serial_bandwidth);
+
+/* Host copies of the built geometry in the current numbering (nullable):
+ *   nbr[3*n]     neighbour across each face, or -FV_BC_* for a ghost face
+ *   normals[6*n] outward face normal times face length, (x, y) per face
+ *   area[n]      triangle area V_T */
+int fv_mesh_export(const fv_mesh* mesh, int32_t* nbr, double* normals, double* area);
+
+/* Creates or refreshes the device arrays now, on `stream` (otherwise the
+ * first device call does it).  Allocates device memory. */
+int fv_mesh_upload(fv_mesh* mesh, void* stream);
+
+/* ===========================================================================
+ * Time stepping (Eq. 4 semi-discrete form, Eq. 5 flux, Eq. 6 forward Euler).
+ * ======================================================================== */
+
+/* Advances U in place by up to nsteps steps.
+ *   U        device, [4*n_cells] in the mesh precision.
+ *   cfl      > 0: each step uses dt = cfl * min_T 2 V_T / (P_T (|v_T| + c_T))
+ *            on the state at the start of the step (P_T the perimeter; the
+ *            paper does not define dt); < 0: fixed dt = -cfl.
+ *   t_stop   > 0: the time advanced in this call stops at t_stop (the last dt
+ *            is clamped, later steps advance nothing); <= 0: no limit.
+ *   scheme   FV_SCHEME_FE or FV_SCHEME_RK2.
+ *   closure  nullable: learned dissipation scale per face (fv_closure_*).
+ *   t_advanced nullable host pointer: if given, the call synchronises the
+ *            stream, stores the time advanced, and returns FV_ENONFINITE if a
+ *            step produced a bad state.  If NULL nothing is synchronised; use
+ *            fv_mesh_status to collect the outcome later.
+ * The step loop runs as captured CUDA graphs of one fused kernel per step;
+ * the first call with a new (U, scheme, cfl, t_stop, closure) captures them. */
+int fv_step(fv_mesh* mesh, void* U, int64_t nsteps, double cfl, double t_stop, int32_t scheme,
+            const fv_closure* closure, void* stream, double* t_advanced);
+
+/* Waits for the stream and reports the last fv_step: time advanced (nullable)
+ * and FV_ENONFINITE if a bad state was seen. */
+int fv_mesh_status(fv_mesh* mesh, void* stream, double* t_advanced);
+
+/* R = dU/dt = -(1/V_T) sum_f F_f |n_f| (Eq. 4) for the state U; both device
+ * arrays of [4*n_cells] in the mesh precision; R must not alias U. */
+int fv_residual(fv_mesh* mesh, const void* U, void* R, const fv_closure* closure, void* stream);
+
+/* dt of the next step for state U (see fv_step's cfl), written to the host
+ * double *dt; synchronises the stream. */
+int fv_compute_dt(fv_mesh* mesh, const void* U, double cfl, void* stream, double* dt);
+
+/* Conserved totals sum_T V_T U_T (mass, x and y momentum, energy; Eq. 1a-1c)
+ * accumulated in FP64 in a fixed order (bitwise reproducible for a given
+ * numbering), written to host out[4]; synchronises the stream. */
+int fv_conserved_totals(fv_mesh* mesh, const void* U, double* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FV_H_ */

@@ -1,0 +1,47 @@
+// fv_internal.h -- host-side data structures shared by the library's
+// translation units (mesh builder, renumbering, C ABI, kernels).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "fv.h"
+
+namespace fv {
+
+// Error raised inside the library and turned into a status at the C ABI.
+struct Error {
+  int code;
+  std::string msg;
+};
+
+// A mesh as built on the host (Sec. 6.2.1 geometry, Sec. 7 neighbour
+// structure).  Arrays are per cell in the current numbering.
+struct HostMesh {
+  int64_t n = 0;
+  std::vector<int32_t> nbr;     // [3n] neighbour across face k, or -FV_BC_* tag
+  std::vector<double> nrm;      // [6n] outward normal * face length, (x, y) per face
+  std::vector<double> vol;      // [n]  triangle area V_T
+  std::vector<double> inradius; // [n]  2 V_T / P_T (P_T perimeter): CFL length scale
+  std::vector<double> cen;      // [2n] centroid (for the Hilbert order)
+};
+
+// Builds the host mesh; throws fv::Error{FV_EINVAL, ...} for malformed input.
+void build_host_mesh(const double* xy, int64_t n_nodes, const int32_t* tri, int64_t n_tri,
+                     const int32_t* canon, const int32_t* bnd, int64_t n_bnd, int32_t default_bc,
+                     HostMesh& out);
+
+// Cell orders (new -> old) for the current numbering of m (Sec. 4).
+std::vector<int32_t> order_shuffle(int64_t n, uint64_t seed);
+std::vector<int32_t> order_rcm(const HostMesh& m);
+std::vector<int32_t> order_hilbert(const HostMesh& m);
+
+// Renumbers m in place with perm (new -> old), remapping neighbour ids.
+void apply_permutation(HostMesh& m, const std::vector<int32_t>& perm);
+
+// Sec. 4.1 diagnostics on the cell graph of the current numbering.
+int64_t graph_bandwidth(const HostMesh& m);
+int64_t serial_bandwidth(const HostMesh& m);
+
+}  // namespace fv

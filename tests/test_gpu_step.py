@@ -1,0 +1,280 @@
+"""GPU parity of the fused step kernels against the FP64 oracle, through the
+C ABI.  Inputs are seeded and synthetic; the oracle builds its own mesh from
+the same node/triangle arrays and never sees a value produced by the GPU.
+
+Tolerances (written per test):
+  FP64 path vs oracle: 1e-12 relative, max per cell (floor 1e-3 of the
+    component's max magnitude) after the stated steps;
+  FP32 path: 1e-5 relative L2 error in density against the FP64 results.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from conftest import rel_err_max
+from paper_1408_5715_gb300 import binding as B
+from paper_1408_5715_gb300 import build as BLD
+from paper_1408_5715_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    BLD.build()
+    B.load()
+
+
+def shuffled(mi, seed):
+    """The same mesh with its triangle list shuffled (cell numbering by seed)."""
+    p = np.random.default_rng(seed).permutation(mi.n_tri)
+    return W.MeshInput(mi.xy, mi.tri[p], mi.canon, mi.bnd, mi.default_bc, dict(mi.info))
+
+
+def pair(orc, mi, uinf_prim=(1.0, 0.0, 0.0, 1.0)):
+    uinf = W.conserved(*uinf_prim)
+    om = orc.Mesh(mi.xy, mi.tri, mi.canon, mi.bnd, mi.default_bc, uinf)
+    g64 = B.Mesh.from_input(mi, "f64")
+    g32 = B.Mesh.from_input(mi, "f32")
+    for g in (g64, g32):
+        g.set_freestream(*uinf_prim)
+    return om, g64, g32
+
+
+def dev(U, dtype):
+    return torch.tensor(np.ascontiguousarray(U), dtype=dtype, device="cuda")
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def c1(orc):
+    mi = shuffled(W.vortex_square_small(seed=1), seed=11)
+    U0 = W.isentropic_vortex(mi.centroids(), mach=0.5, beta=5.0)
+    return (mi, U0) + pair(orc, mi)
+
+
+def test_c1_fp64_matches_oracle_100_steps(c1):
+    mi, U0, om, g64, _ = c1
+    Uo, to, steps, bad = om.run(U0, 100, 0.4)
+    assert steps == 100 and not bad
+    U = dev(U0, torch.float64)
+    t = g64.step(U, 100, 0.4)
+    assert t == pytest.approx(to, rel=1e-13)
+    assert rel_err_max(U.cpu().numpy(), Uo) <= 1e-12
+
+
+def test_c1_fp32_matches_fp64(c1):
+    mi, U0, om, g64, g32 = c1
+    U64 = dev(U0, torch.float64)
+    U32 = dev(U0, torch.float32)
+    g64.step(U64, 100, 0.4)
+    g32.step(U32, 100, 0.4)
+    a, b = U32.double().cpu().numpy(), U64.cpu().numpy()
+    assert rel_l2(a[:, 0], b[:, 0]) <= 1e-5
+    Uo, *_ = om.run(U0, 100, 0.4)
+    assert rel_l2(a[:, 0], Uo[:, 0]) <= 1e-5
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_residual_dt_totals_match_oracle(orc, prec):
+    mi = shuffled(W.channel_bump(37, 23, seed=5), seed=2)  # 1,702 cells: ragged last block
+    uinf_prim = W.freestream(0.5)
+    om, g64, g32 = pair(orc, mi, uinf_prim)
+    g = g64 if prec == "f64" else g32
+    dt_ = torch.float64 if prec == "f64" else torch.float32
+    U0 = W.random_smooth_state(mi.centroids(), seed=4)
+    U = dev(U0, dt_)
+    R = g.residual(U).double().cpu().numpy()
+    Ro = om.residual(U0 if prec == "f64" else U.double().cpu().numpy())
+    tol = 1e-13 if prec == "f64" else 2e-5
+    assert np.abs(R - Ro).max() <= tol * np.abs(Ro).max()
+    dto = om.dt(U.double().cpu().numpy(), 0.4)
+    assert g.compute_dt(U, 0.4) == pytest.approx(dto, rel=1e-14 if prec == "f64" else 1e-6)
+    assert g.compute_dt(U, -2e-3) == 2e-3
+    To = om.totals(U.double().cpu().numpy())
+    scale = np.abs(U.double().cpu().numpy() * om.vol[:, None]).sum(axis=0)
+    assert (np.abs(g.totals(U) - To) <= 1e-14 * scale).all()
+
+
+def test_channel_walls_farfield_fp64_parity(orc):
+    mi = shuffled(W.channel_bump(60, 25, seed=6), seed=3)
+    uinf_prim = W.freestream(0.5)
+    om, g64, g32 = pair(orc, mi, uinf_prim)
+    U0 = W.uniform_state(mi.n_tri, uinf_prim)
+    Uo, to, _, bad = om.run(U0, 150, 0.4)
+    assert not bad
+    U = dev(U0, torch.float64)
+    t = g64.step(U, 150, 0.4)
+    assert t == pytest.approx(to, rel=1e-13)
+    assert rel_err_max(U.cpu().numpy(), Uo) <= 1e-12
+    # the bump has disturbed the flow
+    assert np.abs(Uo - U0).max() > 1e-3
+    U32 = dev(U0, torch.float32)
+    g32.step(U32, 150, 0.4)
+    assert rel_l2(U32.double().cpu().numpy()[:, 0], Uo[:, 0]) <= 1e-5
+
+
+@pytest.mark.parametrize("scheme", ["fe", "rk2"])
+def test_sod_strip_extrapolation_and_t_stop(orc, scheme):
+    mi = shuffled(W.shock_tube_strip(120, 6, seed=7), seed=4)
+    om, g64, _ = pair(orc, mi)
+    U0 = W.sod_state(mi.centroids())
+    Uo, to, steps, bad = om.run(U0, 10000, 0.4, t_stop=0.05, scheme=1 if scheme == "rk2" else 0)
+    assert not bad and to == pytest.approx(0.05, rel=1e-14)
+    U = dev(U0, torch.float64)
+    t = g64.step(U, steps + 7, 0.4, t_stop=0.05, scheme=scheme)  # extra steps advance nothing
+    assert t == pytest.approx(0.05, rel=1e-14)
+    assert rel_err_max(U.cpu().numpy(), Uo) <= 1e-12
+
+
+def test_rk2_fp64_matches_oracle(c1):
+    mi, U0, om, g64, _ = c1
+    Uo, to, _, _ = om.run(U0, 60, 0.4, scheme=1)
+    U = dev(U0, torch.float64)
+    t = g64.step(U, 60, 0.4, scheme="rk2")
+    assert t == pytest.approx(to, rel=1e-13)
+    assert rel_err_max(U.cpu().numpy(), Uo) <= 1e-12
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_split_calls_equal_one_call(c1, prec):
+    # 197 steps in one call (two captured graphs + a remainder, odd count)
+    # equal 96 + 1 + 100 steps in three calls, bit for bit
+    mi, U0, om, g64, g32 = c1
+    g = g64 if prec == "f64" else g32
+    dt_ = torch.float64 if prec == "f64" else torch.float32
+    A = dev(U0, dt_)
+    Bt = dev(U0, dt_)
+    ta = g.step(A, 197, 0.4)
+    tb = g.step(Bt, 96, 0.4) + g.step(Bt, 1, 0.4) + g.step(Bt, 100, 0.4)
+    assert torch.equal(A, Bt)
+    assert ta == pytest.approx(tb, rel=1e-12)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("order", ["rcm", "hilbert", "shuffle"])
+def test_renumbering_leaves_results_unchanged(c1, prec, order):
+    mi, U0, om, g64, g32 = c1
+    dt_ = torch.float64 if prec == "f64" else torch.float32
+    ref = B.Mesh.from_input(mi, prec)
+    ren = B.Mesh.from_input(mi, prec)
+    perm = ren.renumber(order, seed=9)
+    A = dev(U0, dt_)
+    Bt = dev(U0[perm], dt_)
+    ta = ref.step(A, 120, 0.4)
+    tb = ren.step(Bt, 120, 0.4)
+    assert ta == tb
+    assert torch.equal(Bt, A[torch.as_tensor(perm, device="cuda", dtype=torch.long)])
+
+
+def test_conservation_and_free_stream_on_gpu(c1):
+    mi, U0, om, g64, g32 = c1
+    U = dev(U0, torch.float64)
+    T0 = g64.totals(U)
+    g64.step(U, 300, 0.4)
+    T1 = g64.totals(U)
+    scale = np.abs(U0 * om.vol[:, None]).sum(axis=0)
+    assert (np.abs(T1 - T0) <= 1e-12 * scale).all()
+    prim0 = W.freestream(0.5, angle=0.3)
+    Uf0 = W.uniform_state(mi.n_tri, prim0)
+    Uf = dev(Uf0, torch.float64)
+    g64.step(Uf, 300, 0.4)
+    assert np.abs(Uf.cpu().numpy() - Uf0).max() <= 1e-13
+
+
+def test_bad_state_is_reported(c1):
+    mi, U0, om, g64, g32 = c1
+    Ubad = U0.copy()
+    Ubad[17, 3] = 0.1 * 0.5 * (Ubad[17, 1] ** 2 + Ubad[17, 2] ** 2) / Ubad[17, 0]  # p < 0
+    for g, dt_ in ((g64, torch.float64), (g32, torch.float32)):
+        U = dev(Ubad, dt_)
+        with pytest.raises(B.FVError) as e:
+            g.step(U, 3, 0.4)
+        assert e.value.code == B.FV_ENONFINITE
+        # the mesh stays usable afterwards
+        V = dev(U0, dt_)
+        assert g.step(V, 2, 0.4) > 0
+
+
+def test_small_and_degenerate_sizes(orc):
+    # one triangle with three wall faces stays at rest; empty mesh is a no-op
+    mi = W.MeshInput(np.array([[0.0, 0.0], [1.0, 0.2], [0.3, 0.9]]), np.array([[0, 1, 2]], np.int32),
+                     default_bc=W.TAG_WALL)
+    om, g64, g32 = pair(orc, mi)
+    U0 = W.uniform_state(1, (1.0, 0.0, 0.0, 1.0))
+    for g, dt_ in ((g64, torch.float64), (g32, torch.float32)):
+        U = dev(U0, dt_)
+        g.step(U, 5, 0.4)
+        np.testing.assert_allclose(U.double().cpu().numpy(), U0, rtol=1e-6)
+    e = B.Mesh(np.zeros((0, 2)), np.zeros((0, 3), np.int32), precision="f64")
+    Z = torch.zeros((0, 4), dtype=torch.float64, device="cuda")
+    assert e.step(Z, 10, 0.4) == 0.0
+    assert (e.totals(Z) == 0).all()
+
+
+def test_fixed_dt_mode(c1):
+    mi, U0, om, g64, _ = c1
+    Uo, to, _, _ = om.run(U0, 20, -1e-3)
+    U = dev(U0, torch.float64)
+    assert g64.step(U, 20, -1e-3) == pytest.approx(to, rel=1e-14)
+    assert rel_err_max(U.cpu().numpy(), Uo) <= 1e-12
+
+
+# ---------------------------------------------------------------------------
+# full sizes, in the launch configuration of the benchmark (captured graphs)
+# ---------------------------------------------------------------------------
+def test_channel_1m_fp64_and_fp32_vs_oracle(orc):
+    mi = shuffled(W.channel_bump_1m(), seed=12)
+    uinf_prim = W.freestream(0.5)
+    om, g64, g32 = pair(orc, mi, uinf_prim)
+    g64.renumber("rcm")
+    perm = g32.renumber("rcm")
+    g64b = g64
+    U0 = W.uniform_state(mi.n_tri, uinf_prim)
+    Uo, to, _, bad = om.run(U0, 100, 0.4)
+    assert not bad
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(perm.size)
+    U = dev(U0[perm], torch.float64)
+    t = g64b.step(U, 100, 0.4)
+    assert t == pytest.approx(to, rel=1e-13)
+    assert rel_err_max(U.cpu().numpy()[inv], Uo) <= 1e-12
+    U32 = dev(U0[perm], torch.float32)
+    g32.step(U32, 100, 0.4)
+    assert rel_l2(U32.double().cpu().numpy()[inv][:, 0], Uo[:, 0]) <= 1e-5
+
+
+def test_square_16m_one_step_vs_oracle_and_invariants(orc):
+    mi = W.vortex_square_16m()
+    om = orc.Mesh(mi.xy, mi.tri, mi.canon, None, 0)
+    U0 = W.isentropic_vortex(mi.centroids(), mach=0.5)
+    Uo, to, _, _ = om.run(U0, 2, 0.4)
+    for prec, dt_ in (("f64", torch.float64), ("f32", torch.float32)):
+        g = B.Mesh.from_input(mi, prec)
+        perm = g.renumber("hilbert")
+        inv = np.empty_like(perm)
+        inv[perm] = np.arange(perm.size)
+        U = dev(U0[perm], dt_)
+        t = g.step(U, 2, 0.4)
+        got = U.double().cpu().numpy()[inv]
+        if prec == "f64":
+            assert t == pytest.approx(to, rel=1e-13)
+            assert rel_err_max(got, Uo) <= 1e-12
+        else:
+            assert rel_l2(got[:, 0], Uo[:, 0]) <= 1e-6
+        # 192 more steps through the captured graphs: conservation holds
+        T0 = g.totals(U)
+        g.step(U, 192, 0.4)
+        T1 = g.totals(U)
+        scale = np.abs(U0 * om.vol[:, None]).sum(axis=0)
+        tol = 1e-12 if prec == "f64" else 1e-5
+        assert (np.abs(T1 - T0) <= tol * scale).all()
+        del U
+        g.close()

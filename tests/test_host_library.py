@@ -1,0 +1,164 @@
+"""Host-side logic of the CUDA library, checked without a GPU: exported
+symbols, mesh building against the oracle, malformed meshes, renumbering
+(bijection, neighbour remapping, locality) and the Sec. 4.1 diagnostics
+against the oracle's by-definition implementations."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+from paper_1408_5715_gb300 import binding as B
+from paper_1408_5715_gb300 import build as BLD
+from paper_1408_5715_gb300 import workloads as W
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    BLD.build()
+
+
+def header_functions():
+    txt = open(os.path.join(ROOT, "include", "fv.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(fv_\w+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = B.load()
+    names = header_functions()
+    assert len(names) >= 14
+    for name in names:
+        assert hasattr(lib, name), name
+    assert lib.fv_abi_version() == 1
+
+
+def test_oracle_is_not_linked_into_the_library():
+    # the product library must not depend on the test oracle
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--defined-only", B.library_path()], capture_output=True,
+                         text=True).stdout
+    assert "orc_" not in out
+
+
+@pytest.mark.parametrize("kind", ["periodic", "channel", "strip", "two"])
+def test_mesh_matches_oracle(orc, kind):
+    mi = {"periodic": lambda: W.periodic_square(12, 10, seed=3),
+          "channel": lambda: W.channel_bump(20, 9, seed=4),
+          "strip": lambda: W.shock_tube_strip(15, 3, seed=5),
+          "two": lambda: W.two_cells()}[kind]()
+    m = B.Mesh.from_input(mi, "f64")
+    nbr, nrm, area = m.export()
+    om = orc.Mesh(mi.xy, mi.tri, mi.canon, mi.bnd, mi.default_bc)
+    np.testing.assert_array_equal(nbr, om.nbr)
+    np.testing.assert_array_equal(area, om.vol)
+    # normals: identical except on periodic seams, where the library shares
+    # one copy per face between both sides
+    np.testing.assert_allclose(nrm, om.nrm, rtol=0, atol=1e-15)
+    inner = nbr >= 0
+    c, k = np.nonzero(inner)
+    other = nbr[c, k]
+    # each face's normal is exactly opposite to the one seen from across it
+    back = np.array([np.nonzero(nbr[o] == cc)[0] for cc, o in zip(c, other)], dtype=object)
+    for cc, kk, o, ks in zip(c, k, other, back):
+        assert any((nrm[o, j] == -nrm[cc, kk]).all() for j in ks)
+
+
+def test_malformed_meshes_are_rejected():
+    xy = np.array([[0.0, 0.0], [1.0, 0.0], [2.0, 0.0], [0.0, 1.0]])
+    with pytest.raises(B.FVError, match="zero-area") as e:
+        B.Mesh(xy, [[0, 1, 2]], default_bc=1)
+    assert e.value.code == B.FV_EINVAL
+    xy = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0], [0.0, -1.0], [1.0, 1.0]])
+    with pytest.raises(B.FVError, match="more than two"):
+        B.Mesh(xy, [[0, 1, 2], [0, 3, 1], [1, 0, 4]], default_bc=1)
+    with pytest.raises(B.FVError, match="no boundary tag"):
+        B.Mesh(xy[:3], [[0, 1, 2]], default_bc=0)
+    with pytest.raises(B.FVError, match="out of range"):
+        B.Mesh(xy[:3], [[0, 1, 7]], default_bc=1)
+    with pytest.raises(B.FVError, match="collapsed"):
+        B.Mesh(xy[:3], [[0, 1, 2]], canon=[0, 0, 2], default_bc=1)
+    # clockwise input is reoriented
+    m = B.Mesh(xy[:3], [[0, 2, 1]], default_bc=1)
+    assert m.export()[2][0] == 0.5
+    # empty mesh is valid
+    e = B.Mesh(np.zeros((0, 2)), np.zeros((0, 3), np.int32))
+    assert e.n == 0 and e.diagnostics() == (0, 0)
+
+
+@pytest.mark.parametrize("order", ["identity", "shuffle", "rcm", "hilbert"])
+def test_renumber_is_consistent_permutation(orc, order):
+    mi = W.channel_bump(30, 12, seed=8)
+    m = B.Mesh.from_input(mi, "f32")
+    nbr0, nrm0, area0 = m.export()
+    perm = m.renumber(order, seed=3)
+    assert np.array_equal(np.sort(perm), np.arange(m.n))
+    nbr1, nrm1, area1 = m.export()
+    om = orc.Mesh.from_arrays(nbr0, nrm0, area0, np.zeros(4)).permuted(perm)
+    np.testing.assert_array_equal(nbr1, om.nbr)
+    np.testing.assert_array_equal(nrm1, om.nrm)
+    np.testing.assert_array_equal(area1, om.vol)
+    if order == "identity":
+        assert np.array_equal(perm, np.arange(m.n))
+
+
+def test_rcm_and_hilbert_improve_locality():
+    mi = W.channel_bump(80, 30, seed=9)
+    m = B.Mesh.from_input(mi, "f32")
+    m.renumber("shuffle", seed=1)
+    b_sh, s_sh = m.diagnostics()
+    m.renumber("rcm")
+    b_rcm, s_rcm = m.diagnostics()
+    m.renumber("shuffle", seed=2)
+    m.renumber("hilbert")
+    b_h, s_h = m.diagnostics()
+    assert b_rcm < b_sh / 20 and s_rcm < s_sh / 20
+    # a structured 80x30 quad strip has a natural band of about 2*30 cells
+    assert b_rcm <= 4 * 30
+    # Hilbert order keeps consecutive cells close in space
+    nbr, nrm, area = m.export()
+    cen = None  # centroids are not exported; use the neighbour table instead
+    inner = nbr >= 0
+    gaps = np.abs(nbr - np.arange(m.n)[:, None])[inner]
+    assert np.median(gaps) < 8
+
+
+def test_rcm_on_a_path_has_bandwidth_one():
+    # a strip of triangles one quad high and many long: its cell graph is a path
+    nx = 50
+    xy = np.array([[i, j] for j in range(2) for i in range(nx + 1)], np.float64)
+    tri = []
+    for i in range(nx):
+        a, b, c, d = i, i + 1, nx + 2 + i, nx + 1 + i
+        tri += [[a, b, c], [a, c, d]]
+    m = B.Mesh(xy, tri, default_bc=1)
+    m.renumber("shuffle", seed=4)
+    m.renumber("rcm")
+    assert m.diagnostics()[0] == 1
+
+
+def test_diagnostics_match_definition(orc):
+    rng = np.random.default_rng(5)
+    for seed in range(6):
+        mi = W.periodic_square(int(rng.integers(3, 9)), int(rng.integers(3, 6)), seed=seed)
+        m = B.Mesh.from_input(mi, "f64")
+        m.renumber(["shuffle", "rcm", "hilbert"][seed % 3], seed=seed)
+        nbr, nrm, area = m.export()
+        om = orc.Mesh.from_arrays(nbr, nrm, area, np.zeros(4))
+        assert m.diagnostics() == (om.bandwidth(), om.serial_bandwidth())
+
+
+def test_shuffle_is_seeded():
+    mi = W.periodic_square(10, 10, seed=1)
+    a = B.Mesh.from_input(mi).renumber("shuffle", seed=7)
+    b = B.Mesh.from_input(mi).renumber("shuffle", seed=7)
+    c = B.Mesh.from_input(mi).renumber("shuffle", seed=8)
+    assert np.array_equal(a, b) and not np.array_equal(a, c)
+
+
+def test_freestream_validation():
+    m = B.Mesh.from_input(W.two_cells())
+    with pytest.raises(B.FVError):
+        m.set_freestream(-1.0, 0.0, 0.0, 1.0)
+    m.set_freestream(1.0, 0.5, 0.0, 1.0)
