@@ -85,8 +85,11 @@ int32_t fv_abi_version(void);
  *                      reoriented; face k of a triangle is the edge from its
  *                      vertex k to vertex k+1 (mod 3) after reorientation.
  *   node_canon         nullable, [n_nodes]: node -> node it is identified with
- *                      (periodic domains).  Edges are matched on these ids;
- *                      each cell's geometry comes from its own coordinates.
+ *                      (periodic domains).  Edges are matched on these ids.
+ *                      Each face has one normal (Sec. 7 precomputes face sizes
+ *                      and normals), taken from the coordinates of the cell
+ *                      whose (smaller, larger) node-id pair of that edge is the
+ *                      smaller one; the other cell uses its negation.
  *   bnd_edges[3*n_bnd] nullable: (node a, node b, FV_BC_* tag) for edges that
  *                      border no other cell.
  *   default_bc         FV_BC_* tag for unmatched edges not in bnd_edges.
@@ -125,6 +128,15 @@ int fv_mesh_diagnostics(const fv_mesh* mesh, int64_t* bandwidth, int64_t* serial
  *   normals[6*n] outward face normal times face length, (x, y) per face
  *   area[n]      triangle area V_T */
 int fv_mesh_export(const fv_mesh* mesh, int32_t* nbr, double* normals, double* area);
+
+/* FV_F32 meshes: chooses how fv_step adds each increment to the float state.
+ * enable = 1 (the default): compensated -- the part of every update that the
+ * float state cannot represent is kept in a per-cell bfloat16 remainder
+ * (8 bytes per cell, library-owned, zeroed at the start of every fv_step call)
+ * and added back on the next step, so long runs do not stall when increments
+ * fall below half a float ulp of the state.  enable = 0: plain float update.
+ * Not part of the paper; FV_EINVAL for FV_F64 meshes with enable = 1. */
+int fv_mesh_set_compensation(fv_mesh* mesh, int32_t enable);
 
 /* Creates or refreshes the device arrays now, on `stream` (otherwise the
  * first device call does it).  Allocates device memory. */

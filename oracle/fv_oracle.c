@@ -81,8 +81,13 @@ static double orc_signed_area(const double* xy, int32_t i0, int32_t i1, int32_t 
 
 /* Builds neighbours, outward scaled normals and areas.  Triangles given
  * clockwise are reoriented.  canon (nullable) maps a node to the node it is
- * identified with on a periodic domain; normals always come from the cell's
- * own coordinates. */
+ * identified with on a periodic domain.  Sec. 7 precomputes the size and
+ * normal of every face: each face gets one normal, computed from the
+ * coordinates of one of its two cells, and the other cell uses its negation.
+ * The two copies of a periodic face differ in their node coordinates by
+ * rounding, so the cell that supplies the coordinates is fixed by node ids
+ * alone: the side whose (smaller, larger) raw node-id pair of the edge is the
+ * smaller pair. */
 int orc_build_mesh(int64_t n_nodes, const double* xy, int64_t n_tri, const int32_t* tri,
                    const int32_t* canon, int64_t n_bnd, const int32_t* bnd,
                    int32_t default_bc, int32_t* nbr, double* nrm, double* vol) {
@@ -93,9 +98,11 @@ int orc_build_mesh(int64_t n_nodes, const double* xy, int64_t n_tri, const int32
     if (tri[j] < 0 || tri[j] >= n_nodes) return ORC_E_BADINPUT;
   orc_edge* e = (orc_edge*)malloc(sizeof(orc_edge) * (size_t)(3 * n_tri + 1));
   orc_edge* be = (orc_edge*)malloc(sizeof(orc_edge) * (size_t)(n_bnd + 1));
-  if (!e || !be) {
+  int32_t* vt = (int32_t*)malloc(sizeof(int32_t) * (size_t)(3 * n_tri + 1));
+  if (!e || !be || !vt) {
     free(e);
     free(be);
+    free(vt);
     return ORC_E_NOMEM;
   }
   for (c = 0; c < n_tri; ++c) {
@@ -104,6 +111,7 @@ int orc_build_mesh(int64_t n_nodes, const double* xy, int64_t n_tri, const int32
     if (area == 0.0 || !isfinite(area)) {
       free(e);
       free(be);
+      free(vt);
       return ORC_E_DEGENERATE;
     }
     if (area < 0.0) { /* make the vertex order counter-clockwise */
@@ -113,6 +121,9 @@ int orc_build_mesh(int64_t n_nodes, const double* xy, int64_t n_tri, const int32
       area = -area;
     }
     vol[c] = area;
+    vt[3 * c] = v[0];
+    vt[3 * c + 1] = v[1];
+    vt[3 * c + 2] = v[2];
     for (k = 0; k < 3; ++k) {
       int32_t p = v[k], q = v[(k + 1) % 3];
       /* outward normal of edge p->q on a CCW triangle, scaled by |pq| */
@@ -122,6 +133,7 @@ int orc_build_mesh(int64_t n_nodes, const double* xy, int64_t n_tri, const int32
       if (ca == cb) {
         free(e);
         free(be);
+        free(vt);
         return ORC_E_COLLAPSED;
       }
       e[3 * c + k].a = ca < cb ? ca : cb;
@@ -147,11 +159,22 @@ int orc_build_mesh(int64_t n_nodes, const double* xy, int64_t n_tri, const int32
     if (m - j > 2) {
       free(e);
       free(be);
+      free(vt);
       return ORC_E_NONMANIFOLD;
     }
     if (m - j == 2) {
-      nbr[3 * e[j].cell + e[j].face] = (int32_t)e[j + 1].cell;
-      nbr[3 * e[j + 1].cell + e[j + 1].face] = (int32_t)e[j].cell;
+      int64_t s0 = 3 * e[j].cell + e[j].face, s1 = 3 * e[j + 1].cell + e[j + 1].face;
+      nbr[s0] = (int32_t)e[j + 1].cell;
+      nbr[s1] = (int32_t)e[j].cell;
+      /* one normal per face: the owner side keeps its own, the other negates it */
+      int32_t a0 = vt[s0], b0 = vt[3 * e[j].cell + (e[j].face + 1) % 3];
+      int32_t a1 = vt[s1], b1 = vt[3 * e[j + 1].cell + (e[j + 1].face + 1) % 3];
+      int32_t lo0 = a0 < b0 ? a0 : b0, hi0 = a0 < b0 ? b0 : a0;
+      int32_t lo1 = a1 < b1 ? a1 : b1, hi1 = a1 < b1 ? b1 : a1;
+      int own0 = lo0 < lo1 || (lo0 == lo1 && hi0 <= hi1);
+      int64_t own = own0 ? s0 : s1, other = own0 ? s1 : s0;
+      nrm[2 * other] = -nrm[2 * own];
+      nrm[2 * other + 1] = -nrm[2 * own + 1];
     } else {
       int32_t tag = default_bc;
       int64_t lo = 0, hi = n_bnd; /* binary search of the boundary list */
@@ -166,6 +189,7 @@ int orc_build_mesh(int64_t n_nodes, const double* xy, int64_t n_tri, const int32
       if (tag < 1 || tag > 3) {
         free(e);
         free(be);
+        free(vt);
         return ORC_E_OPEN_EDGE;
       }
       nbr[3 * e[j].cell + e[j].face] = -tag;
@@ -174,6 +198,7 @@ int orc_build_mesh(int64_t n_nodes, const double* xy, int64_t n_tri, const int32
   }
   free(e);
   free(be);
+  free(vt);
   return ORC_OK;
 }
 

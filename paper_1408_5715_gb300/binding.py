@@ -63,6 +63,7 @@ def load():
             "fv_mesh_diagnostics": (ctypes.c_int, [_vp, _P(_i64), _P(_i64)]),
             "fv_mesh_export": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
             "fv_mesh_upload": (ctypes.c_int, [_vp, _vp]),
+            "fv_mesh_set_compensation": (ctypes.c_int, [_vp, _i32]),
             "fv_step": (ctypes.c_int, [_vp, _vp, _i64, _dbl, _dbl, _i32, _vp, _vp, _P(_dbl)]),
             "fv_mesh_status": (ctypes.c_int, [_vp, _vp, _P(_dbl)]),
             "fv_residual": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
@@ -164,6 +165,9 @@ class Mesh:
         area = np.empty(self.n, np.float64)
         _check(load().fv_mesh_export(self._h, _np_ptr(nbr), _np_ptr(nrm), _np_ptr(area)))
         return nbr, nrm, area
+
+    def set_compensation(self, enable: bool):
+        _check(load().fv_mesh_set_compensation(self._h, int(bool(enable))))
 
     # -- device side -----------------------------------------------------------
     def upload(self, stream=None):

@@ -75,6 +75,9 @@ struct fv_mesh {
   void* d_geom = nullptr;
   double* d_vol = nullptr;
   void* d_work = nullptr;  // ping-pong partner of the caller's state / RK2 stage
+  uint2* d_lo = nullptr;        // FP32 compensated update: remainder of the state
+  uint2* d_lo_stage = nullptr;  // ... and of the RK2 stage state
+  bool compensated = true;      // FP32 meshes only
   fv::LoopScalars* d_scal = nullptr;
   double* d_partials = nullptr;
   cudaStream_t cap_stream = nullptr;
@@ -84,11 +87,13 @@ struct fv_mesh {
   int32_t g_scheme = -1;
   double g_cfl = 0.0, g_tstop = 0.0;
   const fv_closure* g_closure = nullptr;
+  bool g_comp = false;
   int last_t_slot = 0;
   bool stepped = false;
 
   bool f64() const { return precision == FV_F64; }
   size_t rec_bytes() const { return f64() ? 32 : 16; }
+  bool use_lo() const { return !f64() && compensated; }
 
   void uinf_conserved(double* U) const {
     const double r = uinf_prim[0], u = uinf_prim[1], v = uinf_prim[2], p = uinf_prim[3];
@@ -110,6 +115,8 @@ struct fv_mesh {
     dev_free(d_geom);
     dev_free(d_vol);
     dev_free(d_work);
+    dev_free(d_lo);
+    dev_free(d_lo_stage);
     dev_free(d_scal);
     dev_free(d_partials);
     if (cap_stream) cudaStreamDestroy(cap_stream);
@@ -136,6 +143,10 @@ void ensure_device(fv_mesh* m, cudaStream_t s) {
     FV_CUDA(cudaMalloc(&m->d_geom, nn * 2 * m->rec_bytes()));
     FV_CUDA(cudaMalloc((void**)&m->d_vol, nn * sizeof(double)));
     FV_CUDA(cudaMalloc(&m->d_work, nn * m->rec_bytes()));
+    if (!m->f64()) {
+      FV_CUDA(cudaMalloc((void**)&m->d_lo, nn * sizeof(uint2)));
+      FV_CUDA(cudaMalloc((void**)&m->d_lo_stage, nn * sizeof(uint2)));
+    }
     FV_CUDA(cudaMalloc((void**)&m->d_scal, sizeof(fv::LoopScalars)));
     FV_CUDA(cudaMalloc((void**)&m->d_partials, fv::kTotalsBlocks * 4 * sizeof(double)));
     FV_CUDA(cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking));
@@ -193,6 +204,10 @@ void enqueue_steps(fv_mesh* m, void* U, int64_t j0, int64_t count, double cfl, d
     a.t_write = &sc->t[(j + 1) % 2];
     a.cfl = cfl;
     a.t_stop = t_stop;
+    if (m->use_lo()) {
+      a.lo = m->d_lo;
+      a.lo_stage = m->d_lo_stage;
+    }
     if (scheme == FV_SCHEME_FE) {
       const bool even = (j % 2) == 0;
       a.U = even ? U : m->d_work;
@@ -231,6 +246,7 @@ void capture_graph(fv_mesh* m, void* U, double cfl, double t_stop, int32_t schem
   m->g_cfl = cfl;
   m->g_tstop = t_stop;
   m->g_closure = cl;
+  m->g_comp = m->use_lo();
 }
 
 void read_status(fv_mesh* m, cudaStream_t s, double* t_adv, bool check) {
@@ -349,6 +365,15 @@ int fv_mesh_export(const fv_mesh* mesh, int32_t* nbr, double* normals, double* a
   });
 }
 
+int fv_mesh_set_compensation(fv_mesh* mesh, int32_t enable) {
+  return guarded([&] {
+    check_mesh(mesh);
+    if (mesh->f64() && enable) invalid("compensated update applies to FV_F32 meshes only");
+    mesh->compensated = enable != 0;
+    mesh->drop_graph();
+  });
+}
+
 int fv_mesh_upload(fv_mesh* mesh, void* stream) {
   return guarded([&] {
     check_mesh(mesh);
@@ -373,13 +398,16 @@ int fv_step(fv_mesh* mesh, void* U, int64_t nsteps, double cfl, double t_stop, i
     mesh->last_t_slot = 0;
     mesh->stepped = true;
     if (n > 0 && nsteps > 0) {
+      if (mesh->use_lo())  // the caller's float state carries no remainder
+        FV_CUDA(cudaMemsetAsync(mesh->d_lo, 0, n * sizeof(uint2), s));
       if (cfl > 0.0)
         FV_CUDA(fv::launch_bound(mesh->f64(), U, mesh->d_geom, n, &mesh->d_scal->bmin[0],
                                  &mesh->d_scal->err, s));
       const int64_t chunks = nsteps / kGraphSteps;
       if (chunks > 0) {
         if (!mesh->graph || mesh->g_U != U || mesh->g_scheme != scheme || mesh->g_cfl != cfl ||
-            mesh->g_tstop != t_stop || mesh->g_closure != closure)
+            mesh->g_tstop != t_stop || mesh->g_closure != closure ||
+            mesh->g_comp != mesh->use_lo())
           capture_graph(mesh, U, cfl, t_stop, scheme, closure);
         for (int64_t k = 0; k < chunks; ++k) FV_CUDA(cudaGraphLaunch(mesh->graph, s));
       }

@@ -20,6 +20,7 @@
 //   U     4 values per cell (rho, rho u, rho v, E), float4 or 32-byte doubles
 //   nbr   int4 per cell: neighbour across faces 0..2, negative = ghost kind
 //   geom  8 values per cell: n0x n0y n1x n1y n2x n2y 1/V 2V/P
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -139,6 +140,31 @@ __device__ __forceinline__ R block_min(R v) {
   return v;
 }
 
+// Error-free sum (Knuth's TwoSum): s + e == a + b exactly, for any a, b.
+__device__ __forceinline__ float two_sum(float a, float b, float& e) {
+  const float s = a + b;
+  const float ap = s - b;
+  const float bp = s - ap;
+  e = (a - ap) + (b - bp);
+  return s;
+}
+
+__device__ __forceinline__ void unpack_lo(uint2 v, float l[4]) {
+  l[0] = __uint_as_float(v.x << 16);
+  l[1] = __uint_as_float(v.x & 0xffff0000u);
+  l[2] = __uint_as_float(v.y << 16);
+  l[3] = __uint_as_float(v.y & 0xffff0000u);
+}
+
+__device__ __forceinline__ unsigned bf16_bits(float x) {
+  return (unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+
+__device__ __forceinline__ uint2 pack_lo(const float l[4]) {
+  return make_uint2(bf16_bits(l[0]) | (bf16_bits(l[1]) << 16),
+                    bf16_bits(l[2]) | (bf16_bits(l[3]) << 16));
+}
+
 // dt of the current step (CFL bound or fixed step, clamped so the loop's time
 // never passes t_stop).  Lane 0 of each warp evaluates it and broadcasts, so
 // the FP64 scalar work is per warp, not per cell.
@@ -158,7 +184,7 @@ __device__ __forceinline__ double step_dt(const StepArgs& a, double& t) {
   return __shfl_sync(0xffffffffu, dt, 0);
 }
 
-template <typename R, int MODE>
+template <typename R, int MODE, bool COMP>
 __global__ void __launch_bounds__(kBlock) k_step(StepArgs a) {
   const rec_t<R>* __restrict__ U = static_cast<const rec_t<R>*>(a.U);
   const rec_t<R>* __restrict__ geom = static_cast<const rec_t<R>*>(a.geom);
@@ -181,6 +207,41 @@ __global__ void __launch_bounds__(kBlock) k_step(StepArgs a) {
     const R invV = g1.z;
     if (MODE == kModeResidual) {
       out[i] = Rec<R>::make(-invV * acc[0], -invV * acc[1], -invV * acc[2], -invV * acc[3]);
+    } else if (COMP) {
+      // float state + bfloat16 remainder: the increment and the remainder are
+      // added with an exact TwoSum, and what the float sum drops becomes the
+      // new remainder (kept only by the stages that produce U^{n+1}).
+      const float f = -(float)dt * (float)invV;
+      float lo[4];
+      unpack_lo(a.lo[i], lo);
+      const float u[4] = {(float)UL.x, (float)UL.y, (float)UL.z, (float)UL.w};
+      float base[4] = {u[0], u[1], u[2], u[3]};
+      float inc[4];
+      if (MODE == kModeRK2b) {
+        // U^{n+1} = U^n + (U* - U^n)/2 + dt R(U*)/2, with U^n = base + lo and
+        // U* = u + lo_stage
+        const rec_t<R> B = static_cast<const rec_t<R>*>(a.Ubase)[i];
+        base[0] = (float)B.x, base[1] = (float)B.y, base[2] = (float)B.z, base[3] = (float)B.w;
+        float ls[4];
+        unpack_lo(a.lo_stage[i], ls);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          inc[q] = 0.5f * (u[q] - base[q]) + 0.5f * ((f * (float)acc[q] + ls[q]) + lo[q]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) inc[q] = f * (float)acc[q] + lo[q];
+      }
+      float s[4], e[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) s[q] = two_sum(base[q], inc[q], e[q]);
+      const rec_t<R> Un = Rec<R>::make(R(s[0]), R(s[1]), R(s[2]), R(s[3]));
+      out[i] = Un;
+      if (MODE == kModeRK2a) {
+        a.lo_stage[i] = pack_lo(e);
+      } else {
+        a.lo[i] = pack_lo(e);
+        bound = cell_bound<R>(Un, g1.w, ok);
+      }
     } else {
       const R f = -R(dt) * invV;
       rec_t<R> Un = Rec<R>::make(UL.x + f * acc[0], UL.y + f * acc[1], UL.z + f * acc[2],
@@ -290,15 +351,15 @@ __global__ void __launch_bounds__(kBlock) k_totals_final(const double* partials,
 
 inline unsigned grid_for(int64_t n) { return (unsigned)((n + kBlock - 1) / kBlock); }
 
-template <typename R>
+template <typename R, bool COMP>
 cudaError_t launch_step_t(int mode, const StepArgs& a, cudaStream_t s) {
   if (a.n <= 0 && mode == kModeResidual) return cudaSuccess;
   const unsigned g = a.n > 0 ? grid_for(a.n) : 1u;  // a time step always runs its scalars
   switch (mode) {
-    case kModeFE: k_step<R, kModeFE><<<g, kBlock, 0, s>>>(a); break;
-    case kModeRK2a: k_step<R, kModeRK2a><<<g, kBlock, 0, s>>>(a); break;
-    case kModeRK2b: k_step<R, kModeRK2b><<<g, kBlock, 0, s>>>(a); break;
-    case kModeResidual: k_step<R, kModeResidual><<<g, kBlock, 0, s>>>(a); break;
+    case kModeFE: k_step<R, kModeFE, COMP><<<g, kBlock, 0, s>>>(a); break;
+    case kModeRK2a: k_step<R, kModeRK2a, COMP><<<g, kBlock, 0, s>>>(a); break;
+    case kModeRK2b: k_step<R, kModeRK2b, COMP><<<g, kBlock, 0, s>>>(a); break;
+    case kModeResidual: k_step<R, kModeResidual, false><<<g, kBlock, 0, s>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -307,7 +368,8 @@ cudaError_t launch_step_t(int mode, const StepArgs& a, cudaStream_t s) {
 }  // namespace
 
 cudaError_t launch_step(bool f64, int mode, const StepArgs& a, cudaStream_t s) {
-  return f64 ? launch_step_t<double>(mode, a, s) : launch_step_t<float>(mode, a, s);
+  if (f64) return launch_step_t<double, false>(mode, a, s);
+  return a.lo ? launch_step_t<float, true>(mode, a, s) : launch_step_t<float, false>(mode, a, s);
 }
 
 cudaError_t launch_init_scalars(LoopScalars* d, cudaStream_t s) {

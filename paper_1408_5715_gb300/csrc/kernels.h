@@ -53,6 +53,13 @@ struct StepArgs {
   double cfl;         // > 0: CFL number; < 0: fixed dt = -cfl
   double t_stop;      // > 0: clamp the time advanced in this loop
   int* err;
+  // FP32 compensated update: per cell, four bfloat16 remainders (8 bytes)
+  // that carry what the float state could not hold; read and rewritten in
+  // place by the cell's own thread.  nullptr = plain float update.
+  uint2* lo;
+  // RK2 with lo: remainder of the stage state U* (written by the first stage,
+  // read by the second).
+  uint2* lo_stage;
 };
 
 // float (FV_F32) or double (FV_F64) instantiations

@@ -34,9 +34,17 @@ def orc():
 
 
 def rel_err_max(a, b, floor_frac=1e-3):
-    """max over cells and components of |a-b| / max(|b|, floor_frac * max_cells |b_comp|)."""
+    """Largest relative error over cells and components of states a against b.
+
+    Each component q is compared as |a - b| / max(|b|, floor_frac * S_q), where
+    S_q is the largest magnitude over cells of the physical quantity q belongs
+    to: density for q = 0, the momentum vector (rho u, rho v) for q = 1, 2 (so
+    a momentum component that is zero everywhere is judged against the flow's
+    momentum, not against its own rounding noise), energy for q = 3.
+    """
     a = np.asarray(a, np.float64).reshape(-1, 4)
     b = np.asarray(b, np.float64).reshape(-1, 4)
-    floor = floor_frac * np.abs(b).max(axis=0)
-    den = np.maximum(np.abs(b), np.maximum(floor, 1e-300))
-    return float((np.abs(a - b) / den).max())
+    mom = np.hypot(b[:, 1], b[:, 2]).max() if b.size else 0.0
+    scale = np.array([np.abs(b[:, 0]).max(), mom, mom, np.abs(b[:, 3]).max()]) if b.size else 0.0
+    den = np.maximum(np.abs(b), np.maximum(floor_frac * scale, 1e-300))
+    return float((np.abs(a - b) / den).max()) if b.size else 0.0
