@@ -181,6 +181,36 @@ int fv_compute_dt(fv_mesh* mesh, const void* U, double cfl, void* stream, double
  * numbering), written to host out[4]; synchronises the stream. */
 int fv_conserved_totals(fv_mesh* mesh, const void* U, double* out, void* stream);
 
+/* ===========================================================================
+ * Allocation-free variant.  The paper has no counterpart: this is a service
+ * entry point for callers that cannot allocate device memory.
+ * ======================================================================== */
+
+/* Conserved totals sum_T V_T U_T, like fv_conserved_totals, for callers that
+ * must not allocate device memory -- for example code that runs inside a
+ * framework whose caching allocator owns the whole device memory budget, or a
+ * latency-critical loop where cudaMalloc's implicit device synchronisation
+ * would stall other streams.  It calls no cudaMalloc, cudaFree or allocating
+ * library routine and needs no fv_mesh.
+ *   U        device, [4*n_cells] states in `precision` (FV_F32 or FV_F64).
+ *   area     device, [n_cells] cell areas V_T (e.g. fv_mesh_export's area,
+ *            copied to the device by the caller), same cell order as U.
+ *   out      device, double[4], written by the call (caller-owned).
+ *   stream   cudaStream_t as void*; nothing is synchronised.
+ * Scratch: per-tile partial sums live in a fixed array inside the library's
+ * device code (4096 tiles of 4096 cells, 128 KiB per GPU, held by every GPU
+ * that loads the library until the process exits).  Hence n_cells may be at
+ * most 16,777,216; larger sizes return FV_EINVAL before any device work.
+ * The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current; make that first call
+ * before any stream capture.  All calls share the one array: calls that
+ * overlap on the GPU (different streams, no ordering) race and give wrong
+ * sums.  Every partial a call reads is written earlier in the same call, so
+ * leftovers of a previous call do not matter.  Results agree with
+ * fv_conserved_totals to rounding (the summation order differs). */
+int fv_conserved_totals_noalloc(const void* U, const double* area, int64_t n_cells,
+                                int32_t precision, double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

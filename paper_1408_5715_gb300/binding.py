@@ -69,6 +69,7 @@ def load():
             "fv_residual": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
             "fv_compute_dt": (ctypes.c_int, [_vp, _vp, _dbl, _vp, _P(_dbl)]),
             "fv_conserved_totals": (ctypes.c_int, [_vp, _vp, _P(_dbl), _vp]),
+            "fv_conserved_totals_noalloc": (ctypes.c_int, [_vp, _vp, _i64, _i32, _vp, _vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -208,3 +209,21 @@ class Mesh:
         _check(load().fv_conserved_totals(self._h, _dev_ptr(U, self.torch_dtype, self.n, "U"),
                                           out, _stream_ptr(stream)))
         return np.array(out[:], np.float64)
+
+def conserved_totals_noalloc(U, area, out, stream=None):
+    """fv_conserved_totals_noalloc: totals of the CUDA state U ((n, 4), float32
+    or float64) weighted by the CUDA cell areas ``area`` ((n,), float64), into
+    the CUDA float64 tensor ``out`` (4 values).  Allocates no device memory
+    and does not synchronise."""
+    import torch
+    if U.dtype not in (torch.float32, torch.float64) or not U.is_cuda or not U.is_contiguous():
+        raise TypeError("U must be a contiguous CUDA float32/float64 tensor")
+    n = U.numel() // 4
+    if U.numel() != 4 * n:
+        raise ValueError("U must have shape (n, 4)")
+    for t, what, cnt in ((area, "area", n), (out, "out", 4)):
+        if not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous() or t.numel() != cnt:
+            raise ValueError(f"{what} must be a contiguous CUDA float64 tensor of {cnt} values")
+    prec = FV_F64 if U.dtype == torch.float64 else FV_F32
+    _check(load().fv_conserved_totals_noalloc(_vp(U.data_ptr()), _vp(area.data_ptr()), n, prec,
+                                              _vp(out.data_ptr()), _stream_ptr(stream)))

@@ -61,6 +61,11 @@ constexpr int64_t kGraphSteps = 96;
 
 }  // namespace
 
+namespace fv {
+// Sets this thread's fv_last_error message (for entry points in other files).
+int record_error(int code, const std::string& msg) { return set_error(code, msg); }
+}  // namespace fv
+
 struct fv_closure;  // defined with the learned closure
 
 struct fv_mesh {
