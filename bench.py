@@ -38,6 +38,8 @@ from paper_1408_5715_gb300 import workloads as W  # noqa: E402
 # and written once, 6 normal components + 1/V, 3 neighbour ids (neighbour
 # states are counted as cache reuse, not DRAM traffic).
 ALGO_BYTES = {"f32": 16 + 16 + 28 + 12, "f64": 32 + 32 + 56 + 12}
+# The compensated FP32 update also reads and writes its 8-byte remainder.
+COMP_BYTES = 8 + 8
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -54,6 +56,8 @@ def parse_args():
     p.add_argument("--order", default=None, choices=["identity", "shuffle", "rcm", "hilbert"])
     p.add_argument("--time-steps", type=int, default=None, help="time steps per benchmark step")
     p.add_argument("--no-extras", action="store_true", help="skip FP64 / 16M / CPU / e2e legs")
+    p.add_argument("--variant", type=int, default=None,
+                   help="force a step-kernel shape instead of autotuning")
     return p.parse_args()
 
 
@@ -180,6 +184,15 @@ def make_mesh(B, spec, mi, precision, order):
     return m, perm
 
 
+def choose_variant(m, U, variant, scheme="fe"):
+    """Autotunes the step-kernel shape (or forces one); returns a report."""
+    if variant is not None:
+        m.set_variant(variant)
+        return {"variant": variant, "autotuned": False}
+    best, us = m.autotune(U, scheme=scheme)
+    return {"variant": best, "autotuned": True, "us_per_step_by_variant": us}
+
+
 def timed_loop(m, U, U0dev, time_steps, steps, warmup, scheme, cfl=0.4, flush=None,
                dist=None):
     """Runs warmup + steps benchmark steps; returns per-step device times (s)."""
@@ -239,6 +252,7 @@ def run_ours(args):
     U0p = U0[perm]
     U0dev = torch.tensor(U0p, dtype=tdt, device="cuda")
     U = torch.empty_like(U0dev)
+    tune = choose_variant(m, U0dev, args.variant, args.scheme)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     with ClockSampler(gpu_smi_id()) as clk:
         times = timed_loop(m, U, U0dev, S, args.steps, args.warmup, args.scheme, flush=flush,
@@ -254,6 +268,7 @@ def run_ours(args):
     avg_launch = total / (args.steps * S * stages)  # includes the per-call small kernels
     peak, peak_kind = measured_peaks()
     achieved = ALGO_BYTES[prec] * n / avg_launch / 1e9  # GB/s of one step-kernel launch
+    kbytes = ALGO_BYTES[prec] + (COMP_BYTES if prec == "f32" else 0)
     U_final = U.double().cpu().numpy()
     out = {
         "metric": "cell updates/s",
@@ -271,12 +286,18 @@ def run_ours(args):
         "config": {"workload": args.workload, "mesh": spec["desc"], "cells": n,
                    "time_steps_per_step": S, "scheme": args.scheme, "cfl": 0.4, "order": order,
                    "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "kernel_shape": tune,
                    "l2": "256 MB written between steps (L2 flushed); state+geometry "
                          f"{n * (ALGO_BYTES[prec] + 8) / 1e6:.0f} MB"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind,
                      "bytes_per_update": ALGO_BYTES[prec],
-                     "kernel": f"k_step<{'float' if prec == 'f32' else 'double'},FE>",
+                     "kernel_bytes_per_update": kbytes,
+                     "frac_with_kernel_bytes": kbytes * n / avg_launch / 1e9 / peak,
+                     "kernel": f"k_step<{'float' if prec == 'f32' else 'double'}, "
+                               f"{'RK2' if stages == 2 else 'FE'}, "
+                               f"{'compensated' if prec == 'f32' else 'plain'}, "
+                               f"variant {tune['variant']}>",
                      "traffic": profiled_traffic(f"step_{prec}_{args.workload}.md")},
         "gpu_launches": args.steps * (S * stages + 4),
         "clocks": clk.summary(),
@@ -298,11 +319,13 @@ def extras(args, B, spec, mi, U0, U0p, perm, m32, S, U32_final, out):
         m64, _ = make_mesh(B, spec, mi, "f64", out["config"]["order"])
         U0d = torch.tensor(U0p, dtype=torch.float64, device="cuda")
         U = torch.empty_like(U0d)
+        tune64 = choose_variant(m64, U0d, None, args.scheme)
         t64 = timed_loop(m64, U, U0d, S, 1, 1, args.scheme)
         v64 = n * S / sum(t64)
         U64 = U.cpu().numpy()
         err = float(np.linalg.norm(U32_final[:, 0] - U64[:, 0]) / np.linalg.norm(U64[:, 0]))
         out["fp64"] = {"value": v64, "unit": "cell-updates/s", "time_steps": S,
+                       "kernel_shape": tune64,
                        "speedup_fp32_over_fp64": out["value"] / v64,
                        "fp32_rel_l2_rho_vs_fp64": err, "tolerance": 1e-5}
         del U, U0d
@@ -342,11 +365,13 @@ def extras(args, B, spec, mi, U0, U0p, perm, m32, S, U32_final, out):
             tdt = torch.float32 if prec == "f32" else torch.float64
             U0d = torch.tensor(U16[p16], dtype=tdt, device="cuda")
             U = torch.empty_like(U0d)
+            t16 = choose_variant(m16, U0d, None)
             tt = timed_loop(m16, U, U0d, steps16, 2, 1, "fe")
             v = mi16.n_tri * steps16 / statistics.mean(tt)
             gbs = ALGO_BYTES[prec] * v / 1e9
             peak, _ = measured_peaks()
             res[prec] = {"value": v, "unit": "cell-updates/s", "time_steps": steps16,
+                         "kernel_shape": t16,
                          "achieved_gbs": gbs, "frac_of_measured_hbm": gbs / peak,
                          "traffic": profiled_traffic(f"step_{prec}_square_16m.md")}
             del U, U0d
@@ -355,8 +380,52 @@ def extras(args, B, spec, mi, U0, U0p, perm, m32, S, U32_final, out):
         res["order"] = spec16["order"]
         res["speedup_fp32_over_fp64"] = res["f32"]["value"] / res["f64"]["value"]
         out["square_16m"] = res
+    # ---- many meshes in one launch per step (256 periodic squares, 5k-200k cells)
+    out["batched"] = batched_leg(B)
     # ---- FP64 CPU oracle on one host core, bounded sample of this workload
     out["cpu_baseline"] = cpu_baseline(spec, mi, U0, budget_s=12.0)
+
+
+def batched_leg(B, time_steps=1000):
+    import torch
+    items = W.vortex_batch()
+    meshes, states = [], []
+    for mi, prim, U0 in items:
+        m = B.Mesh.from_input(mi, "f32")
+        m.set_freestream(*prim)
+        perm = m.renumber("hilbert")
+        meshes.append(m)
+        states.append(U0[perm])
+    batch = B.Batch(meshes)
+    for m in meshes:
+        m.close()
+    flat0 = torch.tensor(batch.pack(states), dtype=torch.float32, device="cuda")
+    U = torch.empty_like(flat0)
+    times = []
+    for it in range(3):
+        U.copy_(flat0)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        batch.step(U, time_steps, 0.4, sync=False)
+        batch.totals(U)
+        e1.record()
+        torch.cuda.synchronize()
+        if it > 0:
+            times.append(e0.elapsed_time(e1) / 1e3)
+    t_adv = batch.step(U, 0, 0.4)  # collects the error flag of the runs above
+    cells = int(sum(batch.sizes))
+    v = cells * time_steps / statistics.mean(times)
+    peak, _ = measured_peaks()
+    gbs = (ALGO_BYTES["f32"] + COMP_BYTES) * v / 1e9
+    res = {"value": v, "unit": "cell-updates/s", "meshes": batch.n_meshes, "cells": cells,
+           "padded_cells": batch.n_padded, "time_steps": time_steps, "dtype": "f32",
+           "order": "hilbert", "kernel": "k_step_batch<float, FE, compensated>",
+           "achieved_gbs_kernel_bytes": gbs, "frac_of_measured_hbm": gbs / peak,
+           "launches_per_step": time_steps + 4}
+    batch.close()
+    return res
 
 
 def cpu_baseline(spec, mi, U0, budget_s=12.0):

@@ -138,6 +138,22 @@ int fv_mesh_export(const fv_mesh* mesh, int32_t* nbr, double* normals, double* a
  * Not part of the paper; FV_EINVAL for FV_F64 meshes with enable = 1. */
 int fv_mesh_set_compensation(fv_mesh* mesh, int32_t enable);
 
+/* Shape of the step kernel: 0 one thread per cell; 1 (default) a persistent
+ * grid of resident blocks that walks the cells and prefetches the next
+ * cell's records; 2 the same limited to 64 registers per thread; 3 and 4 one
+ * thread per cell limited to 40 and 32 registers.  All give bitwise identical
+ * results; only speed differs.  FV_EINVAL outside 0..4. */
+int fv_mesh_set_variant(fv_mesh* mesh, int32_t variant);
+
+/* Times every step-kernel shape on this mesh (a few steps each on a device
+ * copy of U with a negligible fixed dt; U itself is not changed), keeps the
+ * fastest for later fv_step calls and reports it in *best (nullable);
+ * us_per_step (nullable, host, [5]) receives the measured microseconds per
+ * step of each shape.  Allocates and frees one state-sized device buffer and
+ * synchronises the stream.  us_per_step has one entry per shape (5). */
+int fv_mesh_autotune(fv_mesh* mesh, const void* U, int32_t scheme, void* stream, int32_t* best,
+                     double* us_per_step);
+
 /* Creates or refreshes the device arrays now, on `stream` (otherwise the
  * first device call does it).  Allocates device memory. */
 int fv_mesh_upload(fv_mesh* mesh, void* stream);
@@ -154,7 +170,8 @@ int fv_mesh_upload(fv_mesh* mesh, void* stream);
  *   t_stop   > 0: the time advanced in this call stops at t_stop (the last dt
  *            is clamped, later steps advance nothing); <= 0: no limit.
  *   scheme   FV_SCHEME_FE or FV_SCHEME_RK2.
- *   closure  nullable: learned dissipation scale per face (fv_closure_*).
+ *   closure  nullable: learned dissipation scale per face (fv_closure_*);
+ *            FV_F32 meshes only.
  *   t_advanced nullable host pointer: if given, the call synchronises the
  *            stream, stores the time advanced, and returns FV_ENONFINITE if a
  *            step produced a bad state.  If NULL nothing is synchronised; use
@@ -180,6 +197,91 @@ int fv_compute_dt(fv_mesh* mesh, const void* U, double cfl, void* stream, double
  * accumulated in FP64 in a fixed order (bitwise reproducible for a given
  * numbering), written to host out[4]; synchronises the stream. */
 int fv_conserved_totals(fv_mesh* mesh, const void* U, double* out, void* stream);
+
+/* ===========================================================================
+ * Learned dissipation scale (not in the paper).  Per face, an MLP
+ * 8 -> 32 -> 32 -> 1 with ReLU maps eight features of the two states that do
+ * not change when the cells are swapped (|jump of rho| / mean rho,
+ * |jump of u_n| / c-bar, |jump of u_t| / c-bar, |jump of p| / mean p,
+ * |mean u_n| / c-bar, |jump of u_n / c|, min c / c-bar, max c / c-bar) to
+ * s = 0.2 + 1.3 sigmoid(z), which multiplies the dissipation term of Eq. 5.
+ * Hidden-layer weights are bfloat16 (features and hidden activations are
+ * rounded to bfloat16 as tensor-core operands), accumulation is FP32.  Runs
+ * on FV_F32 meshes (FV_EINVAL otherwise).
+ * ======================================================================== */
+
+/* theta: host FP32, 1377 values in the order W1[32][8] (row = hidden unit),
+ * b1[32], W2[32][32], b2[32], w3[32], b3; NULL = all zero.  Allocates device
+ * memory on the current device. */
+int fv_closure_create(const float* theta, fv_closure** out);
+
+int fv_closure_destroy(fv_closure* closure);
+
+/* New parameters (same order); theta is host memory, or device memory when
+ * theta_on_device != 0.  Synchronises the stream.  Captured step graphs keep
+ * using the closure's (updated) parameters. */
+int fv_closure_set(fv_closure* closure, const float* theta, int32_t theta_on_device,
+                   void* stream);
+
+/* The MLP alone: features device FP32 [rows][8] -> scales device FP32 [rows]. */
+int fv_closure_eval(const fv_closure* closure, const float* features, float* scales,
+                    int64_t rows, void* stream);
+
+/* The scale of every face for state U: device FP32 [3 * n_cells], face k of
+ * cell c at 3c + k. */
+int fv_closure_scales(fv_mesh* mesh, const void* U, const fv_closure* closure, float* scales,
+                      void* stream);
+
+/* Training signal of the closure: one forward-Euler step with fixed dt from
+ * U0 (device FP32 [4n]) with the closure, compared with the target Ut:
+ *   L = sum_T V_T sum_q ((U0 + dt R(U0) - Ut)_q / weights[q])^2
+ * weights: host double[4] (> 0).  loss: host double (nullable; if given, the
+ * stream is synchronised).  grad: device FP32 [1377] dL/dtheta in the order of
+ * fv_closure_create (nullable), differentiated through the bfloat16 roundings
+ * as if they were the identity.  Deterministic (fixed reduction order). */
+int fv_closure_loss_grad(fv_mesh* mesh, const void* U0, const void* Ut, double dt,
+                         const double* weights, fv_closure* closure, double* loss, float* grad,
+                         void* stream);
+
+/* One Adam update (Kingma and Ba) of n device FP32 parameters with moments m,
+ * v (device, caller-owned, start at zero); step counts from 1. */
+int fv_adam_step(float* theta, const float* grad, float* m, float* v, int64_t n, double lr,
+                 double beta1, double beta2, double eps, int64_t step, void* stream);
+
+/* ===========================================================================
+ * Batches: many independent meshes of uneven size advanced by one launch per
+ * step (not in the paper).  The meshes' cells are concatenated, each mesh's
+ * range padded to a multiple of 256 cells, so every thread block works on one
+ * mesh; each mesh keeps its own dt (its own CFL minimum), time and free
+ * stream, and advances bit for bit as it would alone in the same precision.
+ * ======================================================================== */
+
+/* Copies the current geometry, numbering and free streams of the meshes
+ * (all of one precision; the meshes may be destroyed afterwards).
+ * FV_EINVAL for no meshes, mixed precisions or more than 2^31 cells. */
+int fv_batch_create(fv_mesh* const* meshes, int32_t n_meshes, fv_batch** out);
+
+int fv_batch_destroy(fv_batch* batch);
+
+/* Padded total number of cells, and offsets[n_meshes + 1] (nullable): mesh k
+ * owns records offsets[k] .. offsets[k] + n_cells(k) - 1 of the batch state;
+ * the records up to offsets[k + 1] are padding, ignored and unspecified. */
+int fv_batch_info(const fv_batch* batch, int64_t* n_cells_padded, int64_t* offsets);
+
+/* Compensated float update for FV_F32 batches (see fv_mesh_set_compensation). */
+int fv_batch_set_compensation(fv_batch* batch, int32_t enable);
+
+/* fv_step for every mesh of the batch: U is device memory of n_cells_padded
+ * records in the batch precision; cfl, t_stop and scheme apply to every mesh,
+ * dt is each mesh's own.  t_advanced (nullable, host, [n_meshes]): if given the
+ * call synchronises, stores each mesh's time advanced and returns
+ * FV_ENONFINITE if any state went bad.  Device arrays are created on first use. */
+int fv_batch_step(fv_batch* batch, void* U, int64_t nsteps, double cfl, double t_stop,
+                  int32_t scheme, void* stream, double* t_advanced);
+
+/* Per-mesh conserved totals, host out[4 * n_meshes], FP64, fixed order;
+ * synchronises the stream. */
+int fv_batch_totals(fv_batch* batch, const void* U, double* out, void* stream);
 
 /* ===========================================================================
  * Allocation-free variant.  The paper has no counterpart: this is a service

@@ -67,6 +67,8 @@ def _load():
             lib.orc_closure_nparam.restype = ctypes.c_int64
             lib.orc_closure_features.restype = None
             lib.orc_closure_features.argtypes = [_d, _d, _d, _d]
+            lib.orc_closure_mlp.restype = ctypes.c_double
+            lib.orc_closure_mlp.argtypes = [_d, ctypes.c_int32, _d]
             lib.orc_closure_scale.restype = ctypes.c_double
             lib.orc_closure_scale.argtypes = [_d, ctypes.c_int32, _d, _d, _d]
             lib.orc_residual.restype = ctypes.c_int
@@ -234,6 +236,11 @@ def closure_features(UL, UR, n):
 def closure_scale(theta, UL, UR, n, bf16_acts=False):
     th, UL, UR, n = _f64(theta), _f64(UL), _f64(UR), _f64(n)
     return _load().orc_closure_scale(_pd(th), int(bf16_acts), _pd(UL), _pd(UR), _pd(n))
+
+
+def closure_mlp(theta, feat, bf16_acts=False):
+    th, f = _f64(theta), _f64(feat)
+    return _load().orc_closure_mlp(_pd(th), int(bf16_acts), _pd(f))
 
 
 def cell_dt_bound(U, nrm_cell, vol):

@@ -385,6 +385,14 @@ static void orc_mlp_backward(const double* th, const orc_mlp_trace* t, double gs
   }
 }
 
+/* The MLP alone on a given feature vector (the features rounded to
+ * bfloat16 first when bf16_acts). */
+double orc_closure_mlp(const double* theta, int32_t bf16_acts, const double* feat) {
+  orc_mlp_trace t;
+  orc_mlp_forward(theta, feat, bf16_acts, &t);
+  return t.s;
+}
+
 double orc_closure_scale(const double* theta, int32_t bf16_acts, const double* UL,
                          const double* UR, const double* n) {
   double f[ORC_NF];

@@ -64,12 +64,29 @@ def load():
             "fv_mesh_export": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
             "fv_mesh_upload": (ctypes.c_int, [_vp, _vp]),
             "fv_mesh_set_compensation": (ctypes.c_int, [_vp, _i32]),
+            "fv_mesh_set_variant": (ctypes.c_int, [_vp, _i32]),
+            "fv_mesh_autotune": (ctypes.c_int, [_vp, _vp, _i32, _vp, _P(_i32), _P(_dbl)]),
             "fv_step": (ctypes.c_int, [_vp, _vp, _i64, _dbl, _dbl, _i32, _vp, _vp, _P(_dbl)]),
             "fv_mesh_status": (ctypes.c_int, [_vp, _vp, _P(_dbl)]),
             "fv_residual": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
             "fv_compute_dt": (ctypes.c_int, [_vp, _vp, _dbl, _vp, _P(_dbl)]),
             "fv_conserved_totals": (ctypes.c_int, [_vp, _vp, _P(_dbl), _vp]),
             "fv_conserved_totals_noalloc": (ctypes.c_int, [_vp, _vp, _i64, _i32, _vp, _vp]),
+            "fv_closure_create": (ctypes.c_int, [_vp, _P(_vp)]),
+            "fv_closure_destroy": (ctypes.c_int, [_vp]),
+            "fv_closure_set": (ctypes.c_int, [_vp, _vp, _i32, _vp]),
+            "fv_closure_eval": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp]),
+            "fv_closure_scales": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+            "fv_closure_loss_grad": (ctypes.c_int, [_vp, _vp, _vp, _dbl, _vp, _vp, _P(_dbl),
+                                                    _vp, _vp]),
+            "fv_adam_step": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, _dbl, _dbl, _dbl, _dbl,
+                                            _i64, _vp]),
+            "fv_batch_create": (ctypes.c_int, [_vp, _i32, _P(_vp)]),
+            "fv_batch_destroy": (ctypes.c_int, [_vp]),
+            "fv_batch_info": (ctypes.c_int, [_vp, _P(_i64), _vp]),
+            "fv_batch_set_compensation": (ctypes.c_int, [_vp, _i32]),
+            "fv_batch_step": (ctypes.c_int, [_vp, _vp, _i64, _dbl, _dbl, _i32, _vp, _vp]),
+            "fv_batch_totals": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -184,6 +201,19 @@ class Mesh:
                               ctypes.byref(t) if sync else None))
         return t.value if sync else None
 
+    def set_variant(self, variant: int):
+        _check(load().fv_mesh_set_variant(self._h, int(variant)))
+
+    def autotune(self, U, scheme="fe", stream=None):
+        """Picks the fastest step-kernel shape for this mesh; returns
+        (best, microseconds per step of each shape)."""
+        best = _i32()
+        us = (_dbl * 5)()
+        _check(load().fv_mesh_autotune(self._h, _dev_ptr(U, self.torch_dtype, self.n, "U"),
+                                       SCHEMES[scheme], _stream_ptr(stream), ctypes.byref(best),
+                                       us))
+        return int(best.value), list(us)
+
     def status(self, stream=None):
         t = _dbl(0.0)
         _check(load().fv_mesh_status(self._h, _stream_ptr(stream), ctypes.byref(t)))
@@ -209,6 +239,153 @@ class Mesh:
         _check(load().fv_conserved_totals(self._h, _dev_ptr(U, self.torch_dtype, self.n, "U"),
                                           out, _stream_ptr(stream)))
         return np.array(out[:], np.float64)
+
+
+CLOSURE_PARAMS = 32 * 8 + 32 + 32 * 32 + 32 + 32 + 1
+
+
+class Closure:
+    """The learned dissipation scale (fv_closure); theta is the flat FP32
+    parameter vector W1[32][8], b1, W2[32][32], b2, w3, b3."""
+
+    def __init__(self, theta=None):
+        lib = load()
+        h = _vp()
+        th = None if theta is None else np.ascontiguousarray(theta, np.float32)
+        if th is not None and th.size != CLOSURE_PARAMS:
+            raise ValueError(f"theta needs {CLOSURE_PARAMS} values")
+        _check(lib.fv_closure_create(_np_ptr(th), ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _check(load().fv_closure_destroy(self._h))
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set(self, theta, stream=None):
+        """New parameters from a host array or a CUDA float32 tensor."""
+        import torch
+        if isinstance(theta, torch.Tensor):
+            if not theta.is_cuda or theta.dtype != torch.float32 or theta.numel() != CLOSURE_PARAMS:
+                raise ValueError("theta tensor must be CUDA float32 with 1377 values")
+            _check(load().fv_closure_set(self._h, _vp(theta.data_ptr()), 1, _stream_ptr(stream)))
+        else:
+            th = np.ascontiguousarray(theta, np.float32)
+            _check(load().fv_closure_set(self._h, _np_ptr(th), 0, _stream_ptr(stream)))
+
+    def eval(self, features, out=None, stream=None):
+        """Scales of the rows of a CUDA float32 (rows, 8) feature tensor."""
+        import torch
+        rows = features.shape[0]
+        if out is None:
+            out = torch.empty(rows, dtype=torch.float32, device=features.device)
+        _check(load().fv_closure_eval(self._h, _vp(features.data_ptr()), _vp(out.data_ptr()),
+                                      rows, _stream_ptr(stream)))
+        return out
+
+    def scales(self, mesh, U, out=None, stream=None):
+        """Per-face scales (n, 3) the step would use for state U."""
+        import torch
+        if out is None:
+            out = torch.empty((mesh.n, 3), dtype=torch.float32, device=U.device)
+        _check(load().fv_closure_scales(mesh._h, _dev_ptr(U, mesh.torch_dtype, mesh.n, "U"),
+                                        self._h, _vp(out.data_ptr()), _stream_ptr(stream)))
+        return out
+
+    def loss_grad(self, mesh, U0, Ut, dt, weights=(1.0, 1.0, 1.0, 1.0), grad=None, stream=None):
+        """One-step training loss (host float) and its gradient (CUDA float32
+        tensor of 1377 values)."""
+        import torch
+        if grad is None:
+            grad = torch.empty(CLOSURE_PARAMS, dtype=torch.float32, device=U0.device)
+        w = np.ascontiguousarray(weights, np.float64)
+        loss = _dbl(0.0)
+        _check(load().fv_closure_loss_grad(mesh._h, _dev_ptr(U0, mesh.torch_dtype, mesh.n, "U0"),
+                                           _dev_ptr(Ut, mesh.torch_dtype, mesh.n, "Ut"),
+                                           float(dt), _np_ptr(w), self._h, ctypes.byref(loss),
+                                           _vp(grad.data_ptr()), _stream_ptr(stream)))
+        return loss.value, grad
+
+
+def adam_step(theta, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    """In-place Adam update of CUDA float32 tensors (fv_adam_step)."""
+    n = theta.numel()
+    _check(load().fv_adam_step(_vp(theta.data_ptr()), _vp(grad.data_ptr()), _vp(m.data_ptr()),
+                               _vp(v.data_ptr()), n, lr, beta1, beta2, eps, int(step),
+                               _stream_ptr(stream)))
+
+
+class Batch:
+    """Many meshes advanced together (fv_batch).  ``offsets[k]`` is the first
+    record of mesh k in the flattened state of ``n_padded`` records."""
+
+    def __init__(self, meshes):
+        lib = load()
+        if not meshes:
+            raise ValueError("need at least one mesh")
+        arr = (_vp * len(meshes))(*[m._h for m in meshes])
+        h = _vp()
+        _check(lib.fv_batch_create(arr, len(meshes), ctypes.byref(h)))
+        self._h = h
+        self.precision = meshes[0].precision
+        self.n_meshes = len(meshes)
+        self.sizes = [m.n for m in meshes]
+        n = _i64()
+        off = np.empty(self.n_meshes + 1, np.int64)
+        _check(lib.fv_batch_info(h, ctypes.byref(n), _np_ptr(off)))
+        self.n_padded = int(n.value)
+        self.offsets = off
+
+    @property
+    def torch_dtype(self):
+        import torch
+        return torch.float64 if self.precision == "f64" else torch.float32
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _check(load().fv_batch_destroy(self._h))
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def pack(self, states):
+        """Host: flattened (n_padded, 4) array from per-mesh (n_k, 4) arrays."""
+        out = np.zeros((self.n_padded, 4), np.float64)
+        for k, U in enumerate(states):
+            out[self.offsets[k]:self.offsets[k] + self.sizes[k]] = U
+        return out
+
+    def unpack(self, flat):
+        return [flat[self.offsets[k]:self.offsets[k] + self.sizes[k]] for k in range(self.n_meshes)]
+
+    def set_compensation(self, enable: bool):
+        _check(load().fv_batch_set_compensation(self._h, int(bool(enable))))
+
+    def step(self, U, nsteps, cfl, t_stop=0.0, scheme="fe", stream=None, sync=True):
+        """Advances the flattened CUDA state U in place; returns each mesh's
+        time advanced (numpy array) when sync is True."""
+        t = np.zeros(self.n_meshes, np.float64) if sync else None
+        _check(load().fv_batch_step(self._h, _dev_ptr(U, self.torch_dtype, self.n_padded, "U"),
+                                    int(nsteps), float(cfl), float(t_stop), SCHEMES[scheme],
+                                    _stream_ptr(stream), _np_ptr(t)))
+        return t
+
+    def totals(self, U, stream=None):
+        out = np.empty((self.n_meshes, 4), np.float64)
+        _check(load().fv_batch_totals(self._h, _dev_ptr(U, self.torch_dtype, self.n_padded, "U"),
+                                      _np_ptr(out), _stream_ptr(stream)))
+        return out
+
 
 def conserved_totals_noalloc(U, area, out, stream=None):
     """fv_conserved_totals_noalloc: totals of the CUDA state U ((n, 4), float32

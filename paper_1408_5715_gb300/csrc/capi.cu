@@ -66,7 +66,32 @@ namespace fv {
 int record_error(int code, const std::string& msg) { return set_error(code, msg); }
 }  // namespace fv
 
-struct fv_closure;  // defined with the learned closure
+// Learned dissipation scale: device copies of the packed parameters.
+struct fv_closure {
+  int device = -1;
+  unsigned* d_w1 = nullptr;  // [32 * 4] bfloat16 pairs
+  unsigned* d_w2 = nullptr;  // [32 * 16] bfloat16 pairs
+  float* d_b = nullptr;      // b1[32] b2[32] w3[32] b3
+  float* d_theta = nullptr;  // FP32 staging of theta (kClosureParams)
+  float b3 = 0.0f;           // host copy: a kernel argument
+  // training scratch: per-block gradient and loss partials, outputs
+  int grad_blocks = 0;
+  float* d_gpart = nullptr;
+  double* d_lpart = nullptr;
+  float* d_grad = nullptr;
+  double* d_loss = nullptr;
+
+  fv::ClosureParams params() const {
+    fv::ClosureParams p;
+    p.w1 = d_w1;
+    p.w2 = d_w2;
+    p.b1 = d_b;
+    p.b2 = d_b + 32;
+    p.w3 = d_b + 64;
+    p.b3 = b3;
+    return p;
+  }
+};
 
 struct fv_mesh {
   fv::HostMesh h;
@@ -76,13 +101,14 @@ struct fv_mesh {
   int device = -1;
   bool dirty = true;
   int64_t dev_n = -1;
-  int4* d_nbr = nullptr;
-  void* d_geom = nullptr;
+  void* d_nbr = nullptr;   // FP64: int4 per cell; FP32: int2 (nbr1, nbr2)
+  void* d_geom = nullptr;  // 8 values per cell (see kernels.h)
   double* d_vol = nullptr;
   void* d_work = nullptr;  // ping-pong partner of the caller's state / RK2 stage
   uint2* d_lo = nullptr;        // FP32 compensated update: remainder of the state
   uint2* d_lo_stage = nullptr;  // ... and of the RK2 stage state
   bool compensated = true;      // FP32 meshes only
+  int variant = 1;              // step-kernel shape (fv_mesh_autotune / fv_mesh_set_variant)
   fv::LoopScalars* d_scal = nullptr;
   double* d_partials = nullptr;
   cudaStream_t cap_stream = nullptr;
@@ -93,6 +119,7 @@ struct fv_mesh {
   double g_cfl = 0.0, g_tstop = 0.0;
   const fv_closure* g_closure = nullptr;
   bool g_comp = false;
+  int g_variant = -1;
   int last_t_slot = 0;
   bool stepped = false;
 
@@ -144,7 +171,7 @@ void ensure_device(fv_mesh* m, cudaStream_t s) {
   if (m->dev_n != n) {
     m->free_device();
     const size_t nn = (size_t)std::max<int64_t>(n, 1);
-    FV_CUDA(cudaMalloc((void**)&m->d_nbr, nn * sizeof(int4)));
+    FV_CUDA(cudaMalloc(&m->d_nbr, nn * (m->f64() ? sizeof(int4) : sizeof(int2))));
     FV_CUDA(cudaMalloc(&m->d_geom, nn * 2 * m->rec_bytes()));
     FV_CUDA(cudaMalloc((void**)&m->d_vol, nn * sizeof(double)));
     FV_CUDA(cudaMalloc(&m->d_work, nn * m->rec_bytes()));
@@ -158,28 +185,15 @@ void ensure_device(fv_mesh* m, cudaStream_t s) {
     m->dev_n = n;
   }
   m->drop_graph();
-  std::vector<int4> nbr(n);
-  for (int64_t c = 0; c < n; ++c)
-    nbr[c] = make_int4(m->h.nbr[3 * c], m->h.nbr[3 * c + 1], m->h.nbr[3 * c + 2], 0);
-  std::vector<double> geom(8 * n);
-  for (int64_t c = 0; c < n; ++c) {
-    for (int k = 0; k < 6; ++k) geom[8 * c + k] = m->h.nrm[6 * c + k];
-    geom[8 * c + 6] = 1.0 / m->h.vol[c];
-    geom[8 * c + 7] = m->h.inradius[c];
-  }
   if (n > 0) {
-    FV_CUDA(cudaMemcpyAsync(m->d_nbr, nbr.data(), n * sizeof(int4), cudaMemcpyHostToDevice, s));
+    fv::DeviceLayout lay = fv::pack_layout(m->h.nbr.data(), m->h.nrm.data(), m->h.vol.data(),
+                                           m->h.inradius.data(), n, 0, m->f64());
+    FV_CUDA(cudaMemcpyAsync(m->d_nbr, lay.nbr.data(), lay.nbr.size(), cudaMemcpyHostToDevice, s));
+    FV_CUDA(cudaMemcpyAsync(m->d_geom, lay.geom.data(), lay.geom.size(), cudaMemcpyHostToDevice,
+                            s));
     FV_CUDA(cudaMemcpyAsync(m->d_vol, m->h.vol.data(), n * sizeof(double), cudaMemcpyHostToDevice,
                             s));
-    if (m->f64()) {
-      FV_CUDA(cudaMemcpyAsync(m->d_geom, geom.data(), 8 * n * sizeof(double),
-                              cudaMemcpyHostToDevice, s));
-    } else {
-      std::vector<float> g32(geom.begin(), geom.end());
-      FV_CUDA(cudaMemcpyAsync(m->d_geom, g32.data(), 8 * n * sizeof(float),
-                              cudaMemcpyHostToDevice, s));
-      FV_CUDA(cudaStreamSynchronize(s));  // g32 is a local staging buffer
-    }
+    FV_CUDA(cudaStreamSynchronize(s));  // lay is a local staging buffer
   }
   FV_CUDA(cudaStreamSynchronize(s));
   m->device = dev;
@@ -196,9 +210,15 @@ fv::StepArgs base_args(const fv_mesh* m) {
   return a;
 }
 
+cudaError_t launch_mode(const fv_mesh* m, int mode, const fv::StepArgs& a, const fv_closure* cl,
+                        cudaStream_t s) {
+  if (cl) return fv::launch_step_closure(mode, a, cl->params(), s);
+  return fv::launch_step(m->f64(), mode, m->variant, a, s);
+}
+
 // Enqueues steps j0 .. j0+count-1 of a loop on stream s.
 void enqueue_steps(fv_mesh* m, void* U, int64_t j0, int64_t count, double cfl, double t_stop,
-                   int32_t scheme, cudaStream_t s) {
+                   int32_t scheme, cudaStream_t s, const fv_closure* cl = nullptr) {
   fv::LoopScalars* sc = m->d_scal;
   for (int64_t j = j0; j < j0 + count; ++j) {
     fv::StepArgs a = base_args(m);
@@ -217,15 +237,15 @@ void enqueue_steps(fv_mesh* m, void* U, int64_t j0, int64_t count, double cfl, d
       const bool even = (j % 2) == 0;
       a.U = even ? U : m->d_work;
       a.out = even ? m->d_work : U;
-      FV_CUDA(fv::launch_step(m->f64(), fv::kModeFE, a, s));
+      FV_CUDA(launch_mode(m, fv::kModeFE, a, cl, s));
     } else {
       a.U = U;
       a.out = m->d_work;
-      FV_CUDA(fv::launch_step(m->f64(), fv::kModeRK2a, a, s));
+      FV_CUDA(launch_mode(m, fv::kModeRK2a, a, cl, s));
       a.U = m->d_work;
       a.Ubase = U;
       a.out = U;
-      FV_CUDA(fv::launch_step(m->f64(), fv::kModeRK2b, a, s));
+      FV_CUDA(launch_mode(m, fv::kModeRK2b, a, cl, s));
     }
   }
 }
@@ -236,7 +256,7 @@ void capture_graph(fv_mesh* m, void* U, double cfl, double t_stop, int32_t schem
   cudaGraph_t g = nullptr;
   FV_CUDA(cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal));
   try {
-    enqueue_steps(m, U, 0, kGraphSteps, cfl, t_stop, scheme, m->cap_stream);
+    enqueue_steps(m, U, 0, kGraphSteps, cfl, t_stop, scheme, m->cap_stream, cl);
   } catch (...) {
     cudaStreamEndCapture(m->cap_stream, &g);
     if (g) cudaGraphDestroy(g);
@@ -252,6 +272,7 @@ void capture_graph(fv_mesh* m, void* U, double cfl, double t_stop, int32_t schem
   m->g_tstop = t_stop;
   m->g_closure = cl;
   m->g_comp = m->use_lo();
+  m->g_variant = m->variant;
 }
 
 void read_status(fv_mesh* m, cudaStream_t s, double* t_adv, bool check) {
@@ -379,6 +400,75 @@ int fv_mesh_set_compensation(fv_mesh* mesh, int32_t enable) {
   });
 }
 
+int fv_mesh_set_variant(fv_mesh* mesh, int32_t variant) {
+  return guarded([&] {
+    check_mesh(mesh);
+    if (variant < 0 || variant >= fv::kStepVariants) invalid("unknown step-kernel variant");
+    mesh->variant = variant;
+    mesh->drop_graph();
+  });
+}
+
+int fv_mesh_autotune(fv_mesh* mesh, const void* U, int32_t scheme, void* stream, int32_t* best,
+                     double* us_per_step) {
+  return guarded([&] {
+    check_mesh(mesh);
+    if (scheme != FV_SCHEME_FE && scheme != FV_SCHEME_RK2) invalid("unknown scheme");
+    const int64_t n = mesh->h.n;
+    if (n == 0) {
+      if (best) *best = mesh->variant;
+      return;
+    }
+    if (!U) invalid("null state");
+    cudaStream_t s = as_stream(stream);
+    ensure_device(mesh, s);
+    void* tmp = nullptr;
+    FV_CUDA(cudaMalloc(&tmp, n * mesh->rec_bytes()));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    double times[fv::kStepVariants];
+    const int keep = mesh->variant;
+    try {
+      FV_CUDA(cudaEventCreate(&e0));
+      FV_CUDA(cudaEventCreate(&e1));
+      // a negligible fixed dt: the kernels do their full work, the state barely moves
+      const double cfl = -1e-30;
+      const int64_t steps = std::max<int64_t>(8, std::min<int64_t>(64, (int64_t)(4e7 / (double)n)));
+      for (int v = 0; v < fv::kStepVariants; ++v) {
+        mesh->variant = v;
+        FV_CUDA(cudaMemcpyAsync(tmp, U, n * mesh->rec_bytes(), cudaMemcpyDeviceToDevice, s));
+        if (mesh->use_lo()) FV_CUDA(cudaMemsetAsync(mesh->d_lo, 0, n * sizeof(uint2), s));
+        FV_CUDA(fv::launch_init_scalars(mesh->d_scal, s));
+        enqueue_steps(mesh, tmp, 0, 2, cfl, 0.0, scheme, s);  // warm-up
+        FV_CUDA(cudaEventRecord(e0, s));
+        enqueue_steps(mesh, tmp, 2, steps, cfl, 0.0, scheme, s);
+        FV_CUDA(cudaEventRecord(e1, s));
+        FV_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        FV_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        times[v] = 1e3 * ms / (double)steps;
+      }
+    } catch (...) {
+      mesh->variant = keep;
+      if (e0) cudaEventDestroy(e0);
+      if (e1) cudaEventDestroy(e1);
+      cudaFree(tmp);
+      throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    FV_CUDA(cudaStreamSynchronize(s));
+    cudaFree(tmp);
+    int b = 0;
+    for (int v = 1; v < fv::kStepVariants; ++v)
+      if (times[v] < times[b]) b = v;
+    mesh->variant = b;
+    mesh->drop_graph();
+    if (best) *best = b;
+    if (us_per_step)
+      for (int v = 0; v < fv::kStepVariants; ++v) us_per_step[v] = times[v];
+  });
+}
+
 int fv_mesh_upload(fv_mesh* mesh, void* stream) {
   return guarded([&] {
     check_mesh(mesh);
@@ -394,7 +484,7 @@ int fv_step(fv_mesh* mesh, void* U, int64_t nsteps, double cfl, double t_stop, i
     if (scheme != FV_SCHEME_FE && scheme != FV_SCHEME_RK2) invalid("unknown scheme");
     if (!std::isfinite(cfl) || cfl == 0.0) invalid("cfl must be finite and non-zero");
     if (!std::isfinite(t_stop)) invalid("t_stop must be finite");
-    if (closure) invalid("learned closure is not available in this build");
+    if (closure && mesh->f64()) invalid("the learned closure runs on FV_F32 meshes only");
     if (!U && nsteps > 0 && mesh->h.n > 0) invalid("null state");
     cudaStream_t s = as_stream(stream);
     ensure_device(mesh, s);
@@ -412,12 +502,12 @@ int fv_step(fv_mesh* mesh, void* U, int64_t nsteps, double cfl, double t_stop, i
       if (chunks > 0) {
         if (!mesh->graph || mesh->g_U != U || mesh->g_scheme != scheme || mesh->g_cfl != cfl ||
             mesh->g_tstop != t_stop || mesh->g_closure != closure ||
-            mesh->g_comp != mesh->use_lo())
+            mesh->g_comp != mesh->use_lo() || mesh->g_variant != mesh->variant)
           capture_graph(mesh, U, cfl, t_stop, scheme, closure);
         for (int64_t k = 0; k < chunks; ++k) FV_CUDA(cudaGraphLaunch(mesh->graph, s));
       }
       const int64_t done = chunks * kGraphSteps;
-      enqueue_steps(mesh, U, done, nsteps - done, cfl, t_stop, scheme, s);
+      enqueue_steps(mesh, U, done, nsteps - done, cfl, t_stop, scheme, s, closure);
       if (scheme == FV_SCHEME_FE && (nsteps % 2) == 1)
         FV_CUDA(cudaMemcpyAsync(U, mesh->d_work, n * mesh->rec_bytes(), cudaMemcpyDeviceToDevice,
                                 s));
@@ -441,7 +531,7 @@ int fv_mesh_status(fv_mesh* mesh, void* stream, double* t_advanced) {
 int fv_residual(fv_mesh* mesh, const void* U, void* R, const fv_closure* closure, void* stream) {
   return guarded([&] {
     check_mesh(mesh);
-    if (closure) invalid("learned closure is not available in this build");
+    if (closure && mesh->f64()) invalid("the learned closure runs on FV_F32 meshes only");
     if (mesh->h.n == 0) return;
     if (!U || !R) invalid("null state or residual");
     if (U == R) invalid("R must not alias U");
@@ -450,7 +540,10 @@ int fv_residual(fv_mesh* mesh, const void* U, void* R, const fv_closure* closure
     fv::StepArgs a = base_args(mesh);
     a.U = U;
     a.out = R;
-    FV_CUDA(fv::launch_step(mesh->f64(), fv::kModeResidual, a, s));
+    if (closure)
+      FV_CUDA(fv::launch_step_closure(fv::kModeResidual, a, closure->params(), s));
+    else
+      FV_CUDA(fv::launch_step(mesh->f64(), fv::kModeResidual, 0, a, s));
   });
 }
 
@@ -495,6 +588,515 @@ int fv_conserved_totals(fv_mesh* mesh, const void* U, double* out, void* stream)
                               sc->totals, s));
     FV_CUDA(cudaMemcpyAsync(out, sc->totals, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
     FV_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Batches of meshes stepped in one launch per step.
+// ===========================================================================
+
+struct fv_batch {
+  int32_t precision = FV_F32;
+  int32_t n_meshes = 0;
+  int64_t n = 0;  // padded total cells
+  std::vector<int64_t> offsets;      // [n_meshes + 1] start of each mesh's cells
+  std::vector<int64_t> mesh_end;     // [n_meshes] one past each mesh's last real cell
+  std::vector<int32_t> block_mesh;   // [n / kBlock]
+  std::vector<int32_t> first_block;  // [n_meshes + 1]
+  std::vector<int32_t> nbr;          // [3n] host staging, global cell ids (-1: padding)
+  std::vector<double> nrm;           // [6n]
+  std::vector<double> inradius;      // [n]
+  std::vector<double> vol;
+  std::vector<double> uinf;          // 4 per mesh (conserved)
+  bool compensated = true;
+  // device
+  int device = -1;
+  bool uploaded = false;
+  void* d_nbr = nullptr;
+  void* d_geom = nullptr;
+  double* d_vol = nullptr;
+  void* d_work = nullptr;
+  uint2* d_lo = nullptr;
+  uint2* d_lo_stage = nullptr;
+  int* d_block_mesh = nullptr;
+  int64_t* d_mesh_end = nullptr;
+  int* d_first_block = nullptr;
+  double* d_uinf = nullptr;
+  unsigned long long* d_bmin = nullptr;
+  double* d_t = nullptr;
+  int* d_err = nullptr;
+  double* d_partials = nullptr;
+  double* d_totals = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  const void* g_U = nullptr;
+  int32_t g_scheme = -1;
+  double g_cfl = 0.0, g_tstop = 0.0;
+  bool g_comp = false;
+  int last_t_slot = 0;
+  bool stepped = false;
+
+  bool f64() const { return precision == FV_F64; }
+  size_t rec_bytes() const { return f64() ? 32 : 16; }
+  bool use_lo() const { return !f64() && compensated; }
+  int64_t n_blocks() const { return n / fv::kBlock; }
+
+  void drop_graph() {
+    if (graph) cudaGraphExecDestroy(graph);
+    graph = nullptr;
+    g_U = nullptr;
+  }
+  void free_device() {
+    drop_graph();
+    dev_free(d_nbr);
+    dev_free(d_geom);
+    dev_free(d_vol);
+    dev_free(d_work);
+    dev_free(d_lo);
+    dev_free(d_lo_stage);
+    dev_free(d_block_mesh);
+    dev_free(d_mesh_end);
+    dev_free(d_first_block);
+    dev_free(d_uinf);
+    dev_free(d_bmin);
+    dev_free(d_t);
+    dev_free(d_err);
+    dev_free(d_partials);
+    dev_free(d_totals);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    cap_stream = nullptr;
+    uploaded = false;
+  }
+};
+
+namespace {
+
+void batch_ensure_device(fv_batch* b, cudaStream_t s) {
+  int dev = 0;
+  FV_CUDA(cudaGetDevice(&dev));
+  if (b->uploaded) {
+    if (dev != b->device) invalid("batch was uploaded to another device");
+    return;
+  }
+  const int64_t n = b->n, nb = b->n_blocks();
+  const int M = b->n_meshes;
+  FV_CUDA(cudaMalloc(&b->d_nbr, n * (b->f64() ? sizeof(int4) : sizeof(int2))));
+  FV_CUDA(cudaMalloc(&b->d_geom, n * 2 * b->rec_bytes()));
+  FV_CUDA(cudaMalloc((void**)&b->d_vol, n * sizeof(double)));
+  FV_CUDA(cudaMalloc(&b->d_work, n * b->rec_bytes()));
+  if (!b->f64()) {
+    FV_CUDA(cudaMalloc((void**)&b->d_lo, n * sizeof(uint2)));
+    FV_CUDA(cudaMalloc((void**)&b->d_lo_stage, n * sizeof(uint2)));
+  }
+  FV_CUDA(cudaMalloc((void**)&b->d_block_mesh, nb * sizeof(int)));
+  FV_CUDA(cudaMalloc((void**)&b->d_mesh_end, M * sizeof(int64_t)));
+  FV_CUDA(cudaMalloc((void**)&b->d_first_block, (M + 1) * sizeof(int)));
+  FV_CUDA(cudaMalloc((void**)&b->d_uinf, 4 * M * sizeof(double)));
+  FV_CUDA(cudaMalloc((void**)&b->d_bmin, 3 * M * sizeof(unsigned long long)));
+  FV_CUDA(cudaMalloc((void**)&b->d_t, 2 * M * sizeof(double)));
+  FV_CUDA(cudaMalloc((void**)&b->d_err, sizeof(int)));
+  FV_CUDA(cudaMalloc((void**)&b->d_partials, nb * 4 * sizeof(double)));
+  FV_CUDA(cudaMalloc((void**)&b->d_totals, 4 * M * sizeof(double)));
+  FV_CUDA(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+  fv::DeviceLayout lay = fv::pack_layout(b->nbr.data(), b->nrm.data(), b->vol.data(),
+                                         b->inradius.data(), n, 0, b->f64());
+  FV_CUDA(cudaMemcpyAsync(b->d_nbr, lay.nbr.data(), lay.nbr.size(), cudaMemcpyHostToDevice, s));
+  FV_CUDA(cudaMemcpyAsync(b->d_geom, lay.geom.data(), lay.geom.size(), cudaMemcpyHostToDevice, s));
+  FV_CUDA(cudaMemcpyAsync(b->d_vol, b->vol.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+  FV_CUDA(cudaMemcpyAsync(b->d_block_mesh, b->block_mesh.data(), nb * sizeof(int),
+                          cudaMemcpyHostToDevice, s));
+  FV_CUDA(cudaMemcpyAsync(b->d_mesh_end, b->mesh_end.data(), M * sizeof(int64_t),
+                          cudaMemcpyHostToDevice, s));
+  FV_CUDA(cudaMemcpyAsync(b->d_first_block, b->first_block.data(), (M + 1) * sizeof(int),
+                          cudaMemcpyHostToDevice, s));
+  FV_CUDA(cudaMemcpyAsync(b->d_uinf, b->uinf.data(), 4 * M * sizeof(double),
+                          cudaMemcpyHostToDevice, s));
+  FV_CUDA(cudaMemsetAsync(b->d_work, 0, n * b->rec_bytes(), s));
+  FV_CUDA(cudaStreamSynchronize(s));
+  b->device = dev;
+  b->uploaded = true;
+}
+
+void batch_enqueue_steps(fv_batch* b, void* U, int64_t j0, int64_t count, double cfl,
+                         double t_stop, int32_t scheme, cudaStream_t s) {
+  for (int64_t j = j0; j < j0 + count; ++j) {
+    fv::BatchArgs a{};
+    a.s.nbr = b->d_nbr;
+    a.s.geom = b->d_geom;
+    a.s.n = b->n;
+    a.s.cfl = cfl;
+    a.s.t_stop = t_stop;
+    a.s.err = b->d_err;
+    if (b->use_lo()) {
+      a.s.lo = b->d_lo;
+      a.s.lo_stage = b->d_lo_stage;
+    }
+    a.block_mesh = b->d_block_mesh;
+    a.mesh_end = b->d_mesh_end;
+    a.uinf = b->d_uinf;
+    a.bmin = b->d_bmin;
+    a.t = b->d_t;
+    a.n_meshes = b->n_meshes;
+    a.slot_read = (int)(j % 3);
+    a.slot_write = (int)((j + 1) % 3);
+    a.slot_reset = (int)((j + 2) % 3);
+    a.t_read = (int)(j % 2);
+    a.t_write = (int)((j + 1) % 2);
+    if (scheme == FV_SCHEME_FE) {
+      const bool even = (j % 2) == 0;
+      a.s.U = even ? U : b->d_work;
+      a.s.out = even ? b->d_work : U;
+      FV_CUDA(fv::launch_batch_step(b->f64(), fv::kModeFE, a, b->n_blocks(), s));
+    } else {
+      a.s.U = U;
+      a.s.out = b->d_work;
+      FV_CUDA(fv::launch_batch_step(b->f64(), fv::kModeRK2a, a, b->n_blocks(), s));
+      a.s.U = b->d_work;
+      a.s.Ubase = U;
+      a.s.out = U;
+      FV_CUDA(fv::launch_batch_step(b->f64(), fv::kModeRK2b, a, b->n_blocks(), s));
+    }
+  }
+}
+
+void check_batch(const fv_batch* b) {
+  if (!b) invalid("null batch");
+}
+
+}  // namespace
+
+extern "C" {
+
+int fv_batch_create(fv_mesh* const* meshes, int32_t n_meshes, fv_batch** out) {
+  return guarded([&] {
+    if (!out) invalid("null out");
+    *out = nullptr;
+    if (n_meshes <= 0 || !meshes) invalid("need at least one mesh");
+    fv_batch* b = new fv_batch();
+    try {
+      b->precision = meshes[0] ? meshes[0]->precision : FV_F32;
+      b->n_meshes = n_meshes;
+      b->offsets.assign(n_meshes + 1, 0);
+      for (int k = 0; k < n_meshes; ++k) {
+        const fv_mesh* m = meshes[k];
+        if (!m) invalid("null mesh in batch");
+        if (m->precision != b->precision) invalid("all meshes of a batch need one precision");
+        const int64_t padded = (m->h.n + fv::kBlock - 1) / fv::kBlock * fv::kBlock;
+        b->offsets[k + 1] = b->offsets[k] + padded;
+      }
+      b->n = b->offsets[n_meshes];
+      if (b->n == 0) invalid("all meshes are empty");
+      if (b->n / fv::kBlock > INT32_MAX || b->n > (int64_t)INT32_MAX)
+        invalid("batch too large for 32-bit cell ids");
+      const int64_t n = b->n;
+      b->nbr.assign(3 * n, -1);
+      b->nrm.assign(6 * n, 0.0);
+      b->inradius.assign(n, 1.0);  // padding: harmless values, never used
+      b->vol.assign(n, 1.0);
+      b->uinf.assign(4 * n_meshes, 0.0);
+      b->mesh_end.assign(n_meshes, 0);
+      b->block_mesh.assign(n / fv::kBlock, 0);
+      b->first_block.assign(n_meshes + 1, 0);
+      for (int k = 0; k < n_meshes; ++k) {
+        const fv_mesh* m = meshes[k];
+        const int64_t off = b->offsets[k];
+        for (int64_t c = 0; c < m->h.n; ++c) {
+          for (int f = 0; f < 3; ++f) {
+            const int32_t x = m->h.nbr[3 * c + f];
+            b->nbr[3 * (off + c) + f] = x >= 0 ? (int32_t)(x + off) : x;
+          }
+          for (int f = 0; f < 6; ++f) b->nrm[6 * (off + c) + f] = m->h.nrm[6 * c + f];
+          b->inradius[off + c] = m->h.inradius[c];
+          b->vol[off + c] = m->h.vol[c];
+        }
+        b->mesh_end[k] = off + m->h.n;
+        m->uinf_conserved(&b->uinf[4 * k]);
+        b->first_block[k] = (int32_t)(off / fv::kBlock);
+        for (int64_t blk = off / fv::kBlock; blk < b->offsets[k + 1] / fv::kBlock; ++blk)
+          b->block_mesh[blk] = k;
+      }
+      b->first_block[n_meshes] = (int32_t)(n / fv::kBlock);
+    } catch (...) {
+      delete b;
+      throw;
+    }
+    *out = b;
+  });
+}
+
+int fv_batch_destroy(fv_batch* batch) {
+  return guarded([&] {
+    if (!batch) return;
+    if (batch->uploaded) {
+      int cur = 0;
+      cudaGetDevice(&cur);
+      cudaSetDevice(batch->device);
+      cudaDeviceSynchronize();
+      batch->free_device();
+      cudaSetDevice(cur);
+    }
+    delete batch;
+  });
+}
+
+int fv_batch_info(const fv_batch* batch, int64_t* n_cells_padded, int64_t* offsets) {
+  return guarded([&] {
+    check_batch(batch);
+    if (n_cells_padded) *n_cells_padded = batch->n;
+    if (offsets)
+      std::memcpy(offsets, batch->offsets.data(), batch->offsets.size() * sizeof(int64_t));
+  });
+}
+
+int fv_batch_set_compensation(fv_batch* batch, int32_t enable) {
+  return guarded([&] {
+    check_batch(batch);
+    if (batch->f64() && enable) invalid("compensated update applies to FV_F32 batches only");
+    batch->compensated = enable != 0;
+    batch->drop_graph();
+  });
+}
+
+int fv_batch_step(fv_batch* batch, void* U, int64_t nsteps, double cfl, double t_stop,
+                  int32_t scheme, void* stream, double* t_advanced) {
+  return guarded([&] {
+    check_batch(batch);
+    if (nsteps < 0) invalid("nsteps < 0");
+    if (scheme != FV_SCHEME_FE && scheme != FV_SCHEME_RK2) invalid("unknown scheme");
+    if (!std::isfinite(cfl) || cfl == 0.0) invalid("cfl must be finite and non-zero");
+    if (!std::isfinite(t_stop)) invalid("t_stop must be finite");
+    if (!U) invalid("null state");
+    cudaStream_t s = as_stream(stream);
+    batch_ensure_device(batch, s);
+    const int M = batch->n_meshes;
+    FV_CUDA(fv::launch_batch_init(batch->d_bmin, batch->d_t, M, batch->d_err, s));
+    batch->last_t_slot = 0;
+    batch->stepped = true;
+    if (nsteps > 0) {
+      if (batch->use_lo())
+        FV_CUDA(cudaMemsetAsync(batch->d_lo, 0, batch->n * sizeof(uint2), s));
+      if (cfl > 0.0)
+        FV_CUDA(fv::launch_batch_bound(batch->f64(), U, batch->d_geom, batch->d_block_mesh,
+                                       batch->d_mesh_end, M, batch->n_blocks(), batch->d_bmin,
+                                       batch->d_err, s));
+      const int64_t chunks = nsteps / kGraphSteps;
+      if (chunks > 0) {
+        if (!batch->graph || batch->g_U != U || batch->g_scheme != scheme ||
+            batch->g_cfl != cfl || batch->g_tstop != t_stop || batch->g_comp != batch->use_lo()) {
+          batch->drop_graph();
+          cudaGraph_t g = nullptr;
+          FV_CUDA(cudaStreamBeginCapture(batch->cap_stream, cudaStreamCaptureModeThreadLocal));
+          try {
+            batch_enqueue_steps(batch, U, 0, kGraphSteps, cfl, t_stop, scheme, batch->cap_stream);
+          } catch (...) {
+            cudaStreamEndCapture(batch->cap_stream, &g);
+            if (g) cudaGraphDestroy(g);
+            throw;
+          }
+          FV_CUDA(cudaStreamEndCapture(batch->cap_stream, &g));
+          cudaError_t e = cudaGraphInstantiate(&batch->graph, g, 0);
+          cudaGraphDestroy(g);
+          FV_CUDA(e);
+          batch->g_U = U;
+          batch->g_scheme = scheme;
+          batch->g_cfl = cfl;
+          batch->g_tstop = t_stop;
+          batch->g_comp = batch->use_lo();
+        }
+        for (int64_t k = 0; k < chunks; ++k) FV_CUDA(cudaGraphLaunch(batch->graph, s));
+      }
+      const int64_t done = chunks * kGraphSteps;
+      batch_enqueue_steps(batch, U, done, nsteps - done, cfl, t_stop, scheme, s);
+      if (scheme == FV_SCHEME_FE && (nsteps % 2) == 1)
+        FV_CUDA(cudaMemcpyAsync(U, batch->d_work, batch->n * batch->rec_bytes(),
+                                cudaMemcpyDeviceToDevice, s));
+      batch->last_t_slot = (int)(nsteps % 2);
+    }
+    if (t_advanced) {
+      std::vector<double> t(2 * M);
+      int err = 0;
+      FV_CUDA(cudaMemcpyAsync(t.data(), batch->d_t, 2 * M * sizeof(double),
+                              cudaMemcpyDeviceToHost, s));
+      FV_CUDA(cudaMemcpyAsync(&err, batch->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+      FV_CUDA(cudaStreamSynchronize(s));
+      for (int k = 0; k < M; ++k) t_advanced[k] = t[batch->last_t_slot * M + k];
+      if (err) throw fv::Error{FV_ENONFINITE, "a step produced a non-finite state or "
+                                              "non-positive density or pressure"};
+    }
+  });
+}
+
+int fv_batch_totals(fv_batch* batch, const void* U, double* out, void* stream) {
+  return guarded([&] {
+    check_batch(batch);
+    if (!U || !out) invalid("null state or out");
+    cudaStream_t s = as_stream(stream);
+    batch_ensure_device(batch, s);
+    FV_CUDA(fv::launch_batch_totals(batch->f64(), U, batch->d_vol, batch->d_block_mesh,
+                                    batch->d_mesh_end, batch->d_first_block, batch->n_meshes,
+                                    batch->n_blocks(), batch->d_partials, batch->d_totals, s));
+    FV_CUDA(cudaMemcpyAsync(out, batch->d_totals, 4 * batch->n_meshes * sizeof(double),
+                            cudaMemcpyDeviceToHost, s));
+    FV_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Learned dissipation scale
+// ===========================================================================
+
+namespace {
+
+void closure_upload(fv_closure* c, const float* theta, bool on_device, cudaStream_t s) {
+  if (theta) {
+    FV_CUDA(cudaMemcpyAsync(c->d_theta, theta, fv::kClosureParams * sizeof(float),
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  } else {
+    FV_CUDA(cudaMemsetAsync(c->d_theta, 0, fv::kClosureParams * sizeof(float), s));
+  }
+  FV_CUDA(fv::launch_pack_closure(c->d_theta, c->d_w1, c->d_w2, c->d_b, s));
+  // b3 is a kernel argument: read it back (a 4-byte copy; synchronises)
+  FV_CUDA(cudaMemcpyAsync(&c->b3, c->d_b + 96, sizeof(float), cudaMemcpyDeviceToHost, s));
+  FV_CUDA(cudaStreamSynchronize(s));
+}
+
+void check_closure(const fv_closure* c) {
+  if (!c) invalid("null closure");
+}
+
+}  // namespace
+
+extern "C" {
+
+int fv_closure_create(const float* theta, fv_closure** out) {
+  return guarded([&] {
+    if (!out) invalid("null out");
+    *out = nullptr;
+    fv_closure* c = new fv_closure();
+    try {
+      FV_CUDA(cudaGetDevice(&c->device));
+      FV_CUDA(cudaMalloc((void**)&c->d_w1, 32 * 4 * sizeof(unsigned)));
+      FV_CUDA(cudaMalloc((void**)&c->d_w2, 32 * 16 * sizeof(unsigned)));
+      FV_CUDA(cudaMalloc((void**)&c->d_b, 97 * sizeof(float)));
+      FV_CUDA(cudaMalloc((void**)&c->d_theta, fv::kClosureParams * sizeof(float)));
+      c->grad_blocks = fv::closure_grad_blocks();
+      FV_CUDA(cudaMalloc((void**)&c->d_gpart,
+                         (size_t)c->grad_blocks * fv::kClosureParams * sizeof(float)));
+      FV_CUDA(cudaMalloc((void**)&c->d_lpart, (size_t)c->grad_blocks * sizeof(double)));
+      FV_CUDA(cudaMalloc((void**)&c->d_grad, fv::kClosureParams * sizeof(float)));
+      FV_CUDA(cudaMalloc((void**)&c->d_loss, sizeof(double)));
+      closure_upload(c, theta, false, nullptr);
+    } catch (...) {
+      cudaFree(c->d_w1);
+      cudaFree(c->d_w2);
+      cudaFree(c->d_b);
+      cudaFree(c->d_theta);
+      cudaFree(c->d_gpart);
+      cudaFree(c->d_lpart);
+      cudaFree(c->d_grad);
+      cudaFree(c->d_loss);
+      delete c;
+      throw;
+    }
+    *out = c;
+  });
+}
+
+int fv_closure_destroy(fv_closure* closure) {
+  return guarded([&] {
+    if (!closure) return;
+    cudaDeviceSynchronize();
+    cudaFree(closure->d_w1);
+    cudaFree(closure->d_w2);
+    cudaFree(closure->d_b);
+    cudaFree(closure->d_theta);
+    cudaFree(closure->d_gpart);
+    cudaFree(closure->d_lpart);
+    cudaFree(closure->d_grad);
+    cudaFree(closure->d_loss);
+    delete closure;
+  });
+}
+
+int fv_closure_set(fv_closure* closure, const float* theta, int32_t theta_on_device,
+                   void* stream) {
+  return guarded([&] {
+    check_closure(closure);
+    if (!theta) invalid("null theta");
+    closure_upload(closure, theta, theta_on_device != 0, as_stream(stream));
+  });
+}
+
+int fv_closure_eval(const fv_closure* closure, const float* features, float* scales,
+                    int64_t rows, void* stream) {
+  return guarded([&] {
+    check_closure(closure);
+    if (rows < 0) invalid("rows < 0");
+    if (rows > 0 && (!features || !scales)) invalid("null features or scales");
+    FV_CUDA(fv::launch_closure_eval(features, scales, rows, closure->params(), as_stream(stream)));
+  });
+}
+
+int fv_closure_scales(fv_mesh* mesh, const void* U, const fv_closure* closure, float* scales,
+                      void* stream) {
+  return guarded([&] {
+    check_mesh(mesh);
+    check_closure(closure);
+    if (mesh->f64()) invalid("the learned closure runs on FV_F32 meshes only");
+    if (mesh->h.n == 0) return;
+    if (!U || !scales) invalid("null state or scales");
+    cudaStream_t s = as_stream(stream);
+    ensure_device(mesh, s);
+    fv::StepArgs a = base_args(mesh);
+    a.U = U;
+    FV_CUDA(fv::launch_closure_scales(a, closure->params(), scales, s));
+  });
+}
+
+int fv_closure_loss_grad(fv_mesh* mesh, const void* U0, const void* Ut, double dt,
+                         const double* weights, fv_closure* closure, double* loss, float* grad,
+                         void* stream) {
+  return guarded([&] {
+    check_mesh(mesh);
+    check_closure(closure);
+    if (mesh->f64()) invalid("the learned closure runs on FV_F32 meshes only");
+    if (!(dt >= 0.0) || !std::isfinite(dt)) invalid("dt must be finite and >= 0");
+    if (!weights) invalid("null loss weights");
+    for (int q = 0; q < 4; ++q)
+      if (!(weights[q] > 0.0) || !std::isfinite(weights[q])) invalid("loss weights must be > 0");
+    if (mesh->h.n > 0 && (!U0 || !Ut)) invalid("null state");
+    cudaStream_t s = as_stream(stream);
+    ensure_device(mesh, s);
+    fv::StepArgs a = base_args(mesh);
+    a.U = U0;
+    FV_CUDA(fv::launch_closure_grad(a, static_cast<const float*>(Ut), dt, weights,
+                                    closure->params(), closure->d_gpart, closure->d_lpart,
+                                    closure->grad_blocks, closure->d_grad, closure->d_loss, s));
+    if (grad)
+      FV_CUDA(cudaMemcpyAsync(grad, closure->d_grad, fv::kClosureParams * sizeof(float),
+                              cudaMemcpyDeviceToDevice, s));
+    if (loss) {
+      FV_CUDA(cudaMemcpyAsync(loss, closure->d_loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+      FV_CUDA(cudaStreamSynchronize(s));
+    }
+  });
+}
+
+int fv_adam_step(float* theta, const float* grad, float* m, float* v, int64_t n, double lr,
+                 double beta1, double beta2, double eps, int64_t step, void* stream) {
+  return guarded([&] {
+    if (n < 0 || n > INT32_MAX) invalid("bad n");
+    if (n > 0 && (!theta || !grad || !m || !v)) invalid("null pointer");
+    if (step < 1) invalid("step counts from 1");
+    if (!(beta1 >= 0.0 && beta1 < 1.0 && beta2 >= 0.0 && beta2 < 1.0 && eps > 0.0))
+      invalid("bad Adam coefficients");
+    if (n == 0) return;
+    FV_CUDA(fv::launch_adam(theta, grad, m, v, (int)n, lr, beta1, beta2, eps, step,
+                            as_stream(stream)));
   });
 }
 

@@ -1,0 +1,716 @@
+// closure.cu -- the learned per-face dissipation scale on tensor cores.
+//
+// Not part of the paper: an MLP 8 -> 32 -> 32 -> 1 (ReLU) maps eight features
+// of a face that do not change when its two cells are swapped to a scale
+// s = 0.2 + 1.3 sigmoid(z) of the Lax-Friedrichs dissipation of Eq. 5.
+// Weights of the two hidden layers are bfloat16, accumulation is FP32.
+//
+// Tensor-core mapping: a warp updates 32 cells; their 3 faces are 96 rows
+// of the MLP, six 16-row tiles.  The features of all 96 rows are written to
+// shared memory as bfloat16; for each tile, layer 1 is one mma.sync
+// m16n8k16 per 8 hidden units (K = 8 features padded to 16), layer 2 two
+// per 8 units (K = 32), with the FP32 accumulators of layer 1 re-packed in
+// registers as the A operand of layer 2; layer 3 (32 -> 1) is an FP32 dot
+// product finished with two quad shuffles.  The scales go back through
+// shared memory to the threads that own the cells.
+//
+// Conservation: the features are computed with explicitly rounded operations
+// that give the same bits from either side of a face (the swap L <-> R,
+// n -> -n), so both cells use the same scale and the face flux stays
+// antisymmetric.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+
+#include "cell_math.cuh"
+#include "kernels.h"
+
+namespace fv {
+
+namespace {
+
+constexpr int kClWarps = 4;
+constexpr int kClThreads = 32 * kClWarps;
+constexpr int kRows = 96;  // 32 cells x 3 faces per warp
+
+struct __align__(16) ClWarpSmem {
+  uint4 feat[kRows];  // 8 bfloat16 features per row
+  float s[kRows];     // scale per row
+};
+
+__device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<unsigned*>(&v);
+}
+
+// D += A (16x16, bf16, row) * B (16x8, bf16, col), FP32 accumulate.
+__device__ __forceinline__ void mma_bf16(float d[4], unsigned a0, unsigned a1, unsigned a2,
+                                         unsigned a3, unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+      "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ float relu(float x) { return x > 0.0f ? x : 0.0f; }
+
+__device__ __forceinline__ float scale_of(float z) {
+  return 0.2f + 1.3f * (1.0f / (1.0f + expf(-z)));
+}
+
+// The eight swap-invariant features of a face.
+__device__ __forceinline__ void face_features(const float4& UL, const Prim<float>& L,
+                                              const float4& UR, const Prim<float>& W, float nx,
+                                              float ny, float len, float f[8]) {
+  const float il = recip<float>(len);
+  const float hx = mul(nx, il), hy = mul(ny, il);
+  const float unL = fma_(L.u, hx, mul(L.v, hy));
+  const float unR = fma_(W.u, hx, mul(W.v, hy));
+  const float utL = fma_(L.v, hx, -mul(L.u, hy));
+  const float utR = fma_(W.v, hx, -mul(W.u, hy));
+  const float cbar = mul(0.5f, add(L.c, W.c));
+  const float icb = recip<float>(cbar);
+  f[0] = mul(fabsf(sub(UR.x, UL.x)), recip<float>(mul(0.5f, add(UL.x, UR.x))));
+  f[1] = mul(fabsf(sub(unR, unL)), icb);
+  f[2] = mul(fabsf(sub(utR, utL)), icb);
+  f[3] = mul(fabsf(sub(W.p, L.p)), recip<float>(mul(0.5f, add(L.p, W.p))));
+  f[4] = mul(fabsf(mul(0.5f, add(unL, unR))), icb);
+  f[5] = fabsf(sub(mul(unR, recip<float>(W.c)), mul(unL, recip<float>(L.c))));
+  f[6] = mul(fminf(L.c, W.c), icb);
+  f[7] = mul(fmaxf(L.c, W.c), icb);
+}
+
+__device__ __forceinline__ uint4 pack_features(const float f[8]) {
+  return make_uint4(pack_bf16(f[0], f[1]), pack_bf16(f[2], f[3]), pack_bf16(f[4], f[5]),
+                    pack_bf16(f[6], f[7]));
+}
+
+// Weights as this thread's mma B fragments (loaded once per kernel).
+struct ClFrag {
+  unsigned w1[4];   // layer 1, per n-tile: W1[n][2c..2c+1] (K rows 8..15 are zero)
+  unsigned w2[16];  // layer 2, per (n-tile, k-slice): two registers
+};
+
+__device__ __forceinline__ void load_frags(const ClosureParams& cp, ClFrag& fr) {
+  const int lane = threadIdx.x & 31, r = lane >> 2, c = lane & 3;
+#pragma unroll
+  for (int nt = 0; nt < 4; ++nt) {
+    fr.w1[nt] = __ldg(cp.w1 + (nt * 8 + r) * 4 + c);
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk) {
+      fr.w2[(nt * 2 + kk) * 2] = __ldg(cp.w2 + (nt * 8 + r) * 16 + kk * 8 + c);
+      fr.w2[(nt * 2 + kk) * 2 + 1] = __ldg(cp.w2 + (nt * 8 + r) * 16 + kk * 8 + 4 + c);
+    }
+  }
+}
+
+// Layer-1 and layer-2 pre-activations of one 16-row tile, in accumulator
+// fragment layout: g[nt][0..1] row r, g[nt][2..3] row r+8, columns
+// nt*8 + 2c, +1.  h1 (bfloat16, as layer-2 A fragments) is returned too.
+__device__ __forceinline__ void tile_forward(const ClWarpSmem& w, int t, const ClFrag& fr,
+                                             const float* b1, const float* b2, float a1[4][4],
+                                             unsigned A2[2][4], float g[4][4]) {
+  const int lane = threadIdx.x & 31, r = lane >> 2, c = lane & 3;
+  const unsigned* row0 = reinterpret_cast<const unsigned*>(&w.feat[16 * t + r]);
+  const unsigned* row1 = reinterpret_cast<const unsigned*>(&w.feat[16 * t + r + 8]);
+  const unsigned x0 = row0[c], x1 = row1[c];
+#pragma unroll
+  for (int nt = 0; nt < 4; ++nt) {
+    a1[nt][0] = a1[nt][1] = a1[nt][2] = a1[nt][3] = 0.0f;
+    mma_bf16(a1[nt], x0, x1, 0u, 0u, fr.w1[nt], 0u);
+    const int col = nt * 8 + 2 * c;
+    a1[nt][0] += b1[col];
+    a1[nt][1] += b1[col + 1];
+    a1[nt][2] += b1[col];
+    a1[nt][3] += b1[col + 1];
+    const unsigned p0 = pack_bf16(relu(a1[nt][0]), relu(a1[nt][1]));
+    const unsigned p1 = pack_bf16(relu(a1[nt][2]), relu(a1[nt][3]));
+    A2[nt >> 1][(nt & 1) ? 2 : 0] = p0;
+    A2[nt >> 1][(nt & 1) ? 3 : 1] = p1;
+  }
+#pragma unroll
+  for (int nt = 0; nt < 4; ++nt) {
+    g[nt][0] = g[nt][1] = g[nt][2] = g[nt][3] = 0.0f;
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk)
+      mma_bf16(g[nt], A2[kk][0], A2[kk][1], A2[kk][2], A2[kk][3], fr.w2[(nt * 2 + kk) * 2],
+               fr.w2[(nt * 2 + kk) * 2 + 1]);
+    const int col = nt * 8 + 2 * c;
+    g[nt][0] += b2[col];
+    g[nt][1] += b2[col + 1];
+    g[nt][2] += b2[col];
+    g[nt][3] += b2[col + 1];
+  }
+}
+
+// z of rows r and r+8 of a tile (all four lanes of a quad get both).
+__device__ __forceinline__ void tile_output(const float g[4][4], const float* w3, float b3,
+                                            float& z0, float& z1) {
+  const int c = threadIdx.x & 3;
+  z0 = 0.0f;
+  z1 = 0.0f;
+#pragma unroll
+  for (int nt = 0; nt < 4; ++nt) {
+    const int col = nt * 8 + 2 * c;
+    z0 += relu(g[nt][0]) * w3[col] + relu(g[nt][1]) * w3[col + 1];
+    z1 += relu(g[nt][2]) * w3[col] + relu(g[nt][3]) * w3[col + 1];
+  }
+  z0 += __shfl_xor_sync(0xffffffffu, z0, 1);
+  z0 += __shfl_xor_sync(0xffffffffu, z0, 2);
+  z1 += __shfl_xor_sync(0xffffffffu, z1, 1);
+  z1 += __shfl_xor_sync(0xffffffffu, z1, 2);
+  z0 += b3;
+  z1 += b3;
+}
+
+// Scales of the warp's 96 rows, from the features in w.feat into w.s.
+__device__ __forceinline__ void warp_mlp(ClWarpSmem& w, const ClFrag& fr, const float* b1,
+                                         const float* b2, const float* w3, float b3) {
+  const int lane = threadIdx.x & 31, r = lane >> 2, c = lane & 3;
+  for (int t = 0; t < kRows / 16; ++t) {
+    float a1[4][4], g[4][4];
+    unsigned A2[2][4];
+    tile_forward(w, t, fr, b1, b2, a1, A2, g);
+    float z0, z1;
+    tile_output(g, w3, b3, z0, z1);
+    if (c == 0) {
+      w.s[16 * t + r] = scale_of(z0);
+      w.s[16 * t + r + 8] = scale_of(z1);
+    }
+  }
+}
+
+struct ClShared {
+  ClWarpSmem warp[kClWarps];
+  float b1[32], b2[32], w3[32];
+};
+
+__device__ __forceinline__ void load_small_params(const ClosureParams& cp, ClShared& sh) {
+  if (threadIdx.x < 32) {
+    sh.b1[threadIdx.x] = cp.b1[threadIdx.x];
+    sh.b2[threadIdx.x] = cp.b2[threadIdx.x];
+    sh.w3[threadIdx.x] = cp.w3[threadIdx.x];
+  }
+  __syncthreads();
+}
+
+// Face normals of a cell in the FP32 layout.
+__device__ __forceinline__ void cell_normals(const CellIn<float>& c, float nx[3], float ny[3]) {
+  nx[0] = c.g0.x, ny[0] = c.g0.y;
+  nx[1] = c.g0.z, ny[1] = c.g0.w;
+  nx[2] = c.g1.x, ny[2] = c.g1.y;
+}
+
+// The fused step with the learned scale (FP32 meshes).  Persistent grid of
+// resident blocks; each warp takes 32 consecutive cells at a time.
+template <int MODE, bool COMP>
+__global__ void __launch_bounds__(kClThreads) k_step_closure(StepArgs a, ClosureParams cp) {
+  __shared__ ClShared sh;
+  load_small_params(cp, sh);
+  ClFrag fr;
+  load_frags(cp, fr);
+  const float4* __restrict__ U = static_cast<const float4*>(a.U);
+  const float4* __restrict__ geom = static_cast<const float4*>(a.geom);
+  float4* out = static_cast<float4*>(a.out);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  ClWarpSmem& w = sh.warp[warp];
+  double t = 0.0, dt = 0.0;
+  if (MODE != kModeResidual) dt = step_dt(a, t);
+  float bmin = INFINITY;
+  bool ok = true;
+  const int64_t wstride = (int64_t)gridDim.x * kClWarps * 32;
+  for (int64_t base = ((int64_t)blockIdx.x * kClWarps + warp) * 32; base < a.n; base += wstride) {
+    const int64_t i = base + lane;
+    const bool valid = i < a.n;
+    CellIn<float> c;
+    float4 UR[3];
+    Prim<float> L, W[3];
+    float nx[3], ny[3], len[3];
+    if (valid) {
+      load_cell<float, MODE, COMP>(a, U, geom, i, c);
+      L = primitive<float>(c.U);
+      cell_normals(c, nx, ny);
+      const int nb[3] = {c.n0, c.n1, c.n2};
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        UR[k] = neighbour_state<float>(c.U, nb[k], nx[k], ny[k], U, a.uinf);
+        W[k] = primitive<float>(UR[k]);
+        len[k] = face_len<float>(nx[k], ny[k]);
+        float f[8];
+        face_features(c.U, L, UR[k], W[k], nx[k], ny[k], len[k], f);
+        w.feat[k * 32 + lane] = pack_features(f);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) w.feat[k * 32 + lane] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    __syncwarp();
+    warp_mlp(w, fr, sh.b1, sh.b2, sh.w3, cp.b3);
+    __syncwarp();
+    if (valid) {
+      float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      float perim = 0.0f;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        face_flux_acc<float, true>(c.U, L, UR[k], W[k], nx[k], ny[k], len[k], w.s[k * 32 + lane],
+                                   acc);
+        perim = add(perim, len[k]);
+      }
+      finish_cell<float, MODE, COMP>(a, out, i, c, acc, perim, (float)dt, bmin, ok);
+    }
+    __syncwarp();
+  }
+  if (MODE == kModeFE || MODE == kModeRK2b) {
+    if (!ok) atomicOr(a.err, 1);
+    const double m = (double)block_min<float>(bmin);
+    if (threadIdx.x == 0) {
+      atomicMin(a.bmin_write, (unsigned long long)__double_as_longlong(m));
+      if (blockIdx.x == 0) {
+        *a.t_write = t + dt;
+        *a.bmin_reset = kInfBits;
+      }
+    }
+  }
+}
+
+// The MLP alone on given FP32 features (rounded to bfloat16 like the step's).
+__global__ void __launch_bounds__(kClThreads) k_closure_eval(const float* feats, float* s_out,
+                                                             int64_t rows, ClosureParams cp) {
+  __shared__ ClShared sh;
+  load_small_params(cp, sh);
+  ClFrag fr;
+  load_frags(cp, fr);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  ClWarpSmem& w = sh.warp[warp];
+  const int64_t wstride = (int64_t)gridDim.x * kClWarps * kRows;
+  for (int64_t base = ((int64_t)blockIdx.x * kClWarps + warp) * kRows; base < rows;
+       base += wstride) {
+    for (int j = lane; j < kRows; j += 32) {
+      float f[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      if (base + j < rows)
+        for (int q = 0; q < 8; ++q) f[q] = feats[(base + j) * 8 + q];
+      w.feat[j] = pack_features(f);
+    }
+    __syncwarp();
+    warp_mlp(w, fr, sh.b1, sh.b2, sh.w3, cp.b3);
+    __syncwarp();
+    for (int j = lane; j < kRows; j += 32)
+      if (base + j < rows) s_out[base + j] = w.s[j];
+    __syncwarp();
+  }
+}
+
+// Per-face scales the step would use for state U (3 per cell, face order).
+__global__ void __launch_bounds__(kClThreads) k_closure_scales(StepArgs a, ClosureParams cp,
+                                                               float* s_out) {
+  __shared__ ClShared sh;
+  load_small_params(cp, sh);
+  ClFrag fr;
+  load_frags(cp, fr);
+  const float4* __restrict__ U = static_cast<const float4*>(a.U);
+  const float4* __restrict__ geom = static_cast<const float4*>(a.geom);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  ClWarpSmem& w = sh.warp[warp];
+  const int64_t wstride = (int64_t)gridDim.x * kClWarps * 32;
+  for (int64_t base = ((int64_t)blockIdx.x * kClWarps + warp) * 32; base < a.n; base += wstride) {
+    const int64_t i = base + lane;
+    if (i < a.n) {
+      CellIn<float> c;
+      load_cell<float, kModeResidual, false>(a, U, geom, i, c);
+      const Prim<float> L = primitive<float>(c.U);
+      float nx[3], ny[3];
+      cell_normals(c, nx, ny);
+      const int nb[3] = {c.n0, c.n1, c.n2};
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float4 UR = neighbour_state<float>(c.U, nb[k], nx[k], ny[k], U, a.uinf);
+        const Prim<float> W = primitive<float>(UR);
+        float f[8];
+        face_features(c.U, L, UR, W, nx[k], ny[k], face_len<float>(nx[k], ny[k]), f);
+        w.feat[k * 32 + lane] = pack_features(f);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) w.feat[k * 32 + lane] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    __syncwarp();
+    warp_mlp(w, fr, sh.b1, sh.b2, sh.w3, cp.b3);
+    __syncwarp();
+    if (i < a.n)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) s_out[3 * i + k] = w.s[k * 32 + lane];
+    __syncwarp();
+  }
+}
+
+template <typename K>
+unsigned cl_resident_blocks(K kernel) {
+  static int cached = 0;
+  if (cached == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kClThreads, 0) !=
+            cudaSuccess ||
+        per_sm < 1)
+      return 512;
+    cached = sms * per_sm;
+  }
+  return (unsigned)cached;
+}
+
+template <typename K>
+unsigned cl_grid(K kernel, int64_t items_per_warp_group, int64_t n) {
+  const int64_t want = std::max<int64_t>(1, (n + items_per_warp_group * kClWarps - 1) /
+                                                (items_per_warp_group * kClWarps));
+  const unsigned cap = cl_resident_blocks(kernel);
+  return (unsigned)std::min<int64_t>(want, cap);
+}
+
+template <int MODE, bool COMP>
+cudaError_t launch_cl(const StepArgs& a, const ClosureParams& cp, cudaStream_t s) {
+  auto kernel = k_step_closure<MODE, COMP>;
+  kernel<<<cl_grid(kernel, 32, a.n), kClThreads, 0, s>>>(a, cp);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Training: one-step loss and its gradient.
+//   U1 = U0 + dt R(U0; theta)   (forward Euler, fixed dt)
+//   L  = sum_T V_T sum_q ((U1 - Ut)_q / w_q)^2
+// dL/ds of a face = sum_q dL/dU1_q (-dt / V) dF_q/ds, where the flux is affine
+// in s with dF/ds = -(|q_L + q_R| + |n| (c_L + c_R)) / 4 (U_R - U_L); then
+// back through the MLP (FP32, straight through the bfloat16 roundings).
+// ---------------------------------------------------------------------------
+constexpr int kGrWarps = 2;
+constexpr int kGrThreads = 32 * kGrWarps;
+
+struct __align__(16) GrWarpSmem {
+  ClWarpSmem f;               // features (bfloat16) and scales
+  unsigned h1[kRows * 16];    // hidden layer 1 after ReLU, bfloat16 pairs
+  float h2[kRows * 32];       // hidden layer 2 after ReLU
+  float sig[kRows];           // sigmoid(z)
+  float gs[kRows];            // dL/ds
+};
+
+struct GrShared {
+  GrWarpSmem warp[kGrWarps];
+  float b1[32], b2[32], w3[32];
+  float W2[32 * 32];          // FP32 copy of the bfloat16 weights, [out][in]
+};
+
+__device__ __forceinline__ float bf16_lo(unsigned v) { return __uint_as_float(v << 16); }
+__device__ __forceinline__ float bf16_hi(unsigned v) { return __uint_as_float(v & 0xffff0000u); }
+
+__global__ void __launch_bounds__(kGrThreads) k_closure_grad(StepArgs a, const float4* Ut,
+                                                             float dt, float4 wq,
+                                                             ClosureParams cp, float* gpart,
+                                                             double* lpart) {
+  __shared__ GrShared sh;
+  if (threadIdx.x < 32) {
+    sh.b1[threadIdx.x] = cp.b1[threadIdx.x];
+    sh.b2[threadIdx.x] = cp.b2[threadIdx.x];
+    sh.w3[threadIdx.x] = cp.w3[threadIdx.x];
+  }
+  for (int j = threadIdx.x; j < 32 * 16; j += blockDim.x) {
+    const unsigned v = cp.w2[j];
+    sh.W2[2 * j] = bf16_lo(v);
+    sh.W2[2 * j + 1] = bf16_hi(v);
+  }
+  __syncthreads();
+  ClFrag fr;
+  load_frags(cp, fr);
+  const float4* __restrict__ U = static_cast<const float4*>(a.U);
+  const float4* __restrict__ geom = static_cast<const float4*>(a.geom);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, r = lane >> 2, cq = lane & 3;
+  GrWarpSmem& w = sh.warp[warp];
+  const float iw2[4] = {1.0f / (wq.x * wq.x), 1.0f / (wq.y * wq.y), 1.0f / (wq.z * wq.z),
+                        1.0f / (wq.w * wq.w)};
+  // per-lane gradient accumulators: lane o owns layer-2 unit o and layer-1 unit o
+  float gW2[32], gW1[8], gb1 = 0.0f, gb2 = 0.0f, gw3 = 0.0f, gb3 = 0.0f;
+#pragma unroll
+  for (int j = 0; j < 32; ++j) gW2[j] = 0.0f;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) gW1[j] = 0.0f;
+  double loss = 0.0;
+  const int64_t wstride = (int64_t)gridDim.x * kGrWarps * 32;
+  for (int64_t base = ((int64_t)blockIdx.x * kGrWarps + warp) * 32; base < a.n; base += wstride) {
+    const int64_t i = base + lane;
+    const bool valid = i < a.n;
+    CellIn<float> c;
+    float4 UR[3];
+    Prim<float> L, W[3];
+    float nx[3], ny[3], len[3];
+    if (valid) {
+      load_cell<float, kModeResidual, false>(a, U, geom, i, c);
+      L = primitive<float>(c.U);
+      cell_normals(c, nx, ny);
+      const int nb[3] = {c.n0, c.n1, c.n2};
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        UR[k] = neighbour_state<float>(c.U, nb[k], nx[k], ny[k], U, a.uinf);
+        W[k] = primitive<float>(UR[k]);
+        len[k] = face_len<float>(nx[k], ny[k]);
+        float f[8];
+        face_features(c.U, L, UR[k], W[k], nx[k], ny[k], len[k], f);
+        w.f.feat[k * 32 + lane] = pack_features(f);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) w.f.feat[k * 32 + lane] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    __syncwarp();
+    // forward, keeping what the backward pass needs
+    for (int t = 0; t < kRows / 16; ++t) {
+      float a1[4][4], g[4][4];
+      unsigned A2[2][4];
+      tile_forward(w.f, t, fr, sh.b1, sh.b2, a1, A2, g);
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        w.h1[(16 * t + r) * 16 + nt * 4 + cq] = A2[nt >> 1][(nt & 1) ? 2 : 0];
+        w.h1[(16 * t + r + 8) * 16 + nt * 4 + cq] = A2[nt >> 1][(nt & 1) ? 3 : 1];
+        const int col = nt * 8 + 2 * cq;
+        w.h2[(16 * t + r) * 32 + col] = relu(g[nt][0]);
+        w.h2[(16 * t + r) * 32 + col + 1] = relu(g[nt][1]);
+        w.h2[(16 * t + r + 8) * 32 + col] = relu(g[nt][2]);
+        w.h2[(16 * t + r + 8) * 32 + col + 1] = relu(g[nt][3]);
+      }
+      float z0, z1;
+      tile_output(g, sh.w3, cp.b3, z0, z1);
+      if (cq == 0) {
+        w.sig[16 * t + r] = 1.0f / (1.0f + expf(-z0));
+        w.sig[16 * t + r + 8] = 1.0f / (1.0f + expf(-z1));
+      }
+    }
+    __syncwarp();
+    // one forward-Euler step of the own cell, its loss and dL/ds per face
+    if (valid) {
+      float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      float dFds[3][4];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float sk = 0.2f + 1.3f * w.sig[k * 32 + lane];
+        face_flux_acc<float, true>(c.U, L, UR[k], W[k], nx[k], ny[k], len[k], sk, acc);
+        const float qL = fma_(L.u, nx[k], mul(L.v, ny[k]));
+        const float qR = fma_(W[k].u, nx[k], mul(W[k].v, ny[k]));
+        const float na = mul(-0.25f, fma_(len[k], add(L.c, W[k].c), fabsf(add(qL, qR))));
+        dFds[k][0] = na * (UR[k].x - c.U.x);
+        dFds[k][1] = na * (UR[k].y - c.U.y);
+        dFds[k][2] = na * (UR[k].z - c.U.z);
+        dFds[k][3] = na * (UR[k].w - c.U.w);
+      }
+      const float invV = c.g1.z;
+      const float f = -dt * invV;
+      const float V = 1.0f / invV;
+      const float4 ut = Ut[i];
+      const float d[4] = {fma_(f, acc[0], c.U.x) - ut.x, fma_(f, acc[1], c.U.y) - ut.y,
+                          fma_(f, acc[2], c.U.z) - ut.z, fma_(f, acc[3], c.U.w) - ut.w};
+      float gU[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        loss += (double)V * (double)d[q] * (double)d[q] * (double)iw2[q];
+        gU[q] = 2.0f * V * d[q] * iw2[q];
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        float gsk = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) gsk += gU[q] * f * dFds[k][q];
+        w.gs[k * 32 + lane] = gsk;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) w.gs[k * 32 + lane] = 0.0f;
+    }
+    __syncwarp();
+    // backward through the MLP, row by row; lane o owns unit o of both layers
+    const int o = lane;
+    for (int row = 0; row < kRows; ++row) {
+      const float sg = w.sig[row];
+      const float dz = w.gs[row] * 1.3f * sg * (1.0f - sg);
+      const float h2o = w.h2[row * 32 + o];
+      gw3 += dz * h2o;
+      gb3 += dz;  // every lane the same; lane 0's copy is used
+      const float da2 = h2o > 0.0f ? dz * sh.w3[o] : 0.0f;
+      gb2 += da2;
+#pragma unroll
+      for (int jj = 0; jj < 16; ++jj) {
+        const unsigned hp = w.h1[row * 16 + jj];
+        gW2[2 * jj] += da2 * bf16_lo(hp);
+        gW2[2 * jj + 1] += da2 * bf16_hi(hp);
+      }
+      // dL/dh1 of unit j = o: sum over the outputs p of W2[p][o] da2_p
+      float dh1 = 0.0f;
+#pragma unroll
+      for (int pp = 0; pp < 32; ++pp) dh1 += sh.W2[pp * 32 + o] * __shfl_sync(0xffffffffu, da2, pp);
+      const unsigned hp = w.h1[row * 16 + (o >> 1)];
+      const float h1o = (o & 1) ? bf16_hi(hp) : bf16_lo(hp);
+      const float da1 = h1o > 0.0f ? dh1 : 0.0f;
+      gb1 += da1;
+      const uint4 xv = w.f.feat[row];
+      const unsigned xs[4] = {xv.x, xv.y, xv.z, xv.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        gW1[2 * q] += da1 * bf16_lo(xs[q]);
+        gW1[2 * q + 1] += da1 * bf16_hi(xs[q]);
+      }
+    }
+    __syncwarp();
+  }
+  // deterministic block reduction: warps in order, through shared memory
+  __syncthreads();
+  float* red = reinterpret_cast<float*>(&sh.warp[0]);  // reuse: kGrWarps x kClosureParams floats
+  {
+    float* mine = red + warp * kClosureParams;
+    const int o = lane;
+    for (int j = 0; j < 8; ++j) mine[o * 8 + j] = gW1[j];           // W1[o][j]
+    mine[256 + o] = gb1;                                            // b1[o]
+    for (int j = 0; j < 32; ++j) mine[288 + o * 32 + j] = gW2[j];   // W2[o][j]
+    mine[1312 + o] = gb2;                                           // b2[o]
+    mine[1344 + o] = gw3;                                           // w3[o]
+    if (o == 0) mine[1376] = gb3;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < kClosureParams; j += blockDim.x) {
+    float sum = 0.0f;
+    for (int wv = 0; wv < kGrWarps; ++wv) sum += red[wv * kClosureParams + j];
+    gpart[(int64_t)blockIdx.x * kClosureParams + j] = sum;
+  }
+  // loss: warp shuffle, then warps in order
+  for (int off = 16; off > 0; off >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, off);
+  __shared__ double lw[kGrWarps];
+  if (lane == 0) lw[warp] = loss;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double l = 0.0;
+    for (int wv = 0; wv < kGrWarps; ++wv) l += lw[wv];
+    lpart[blockIdx.x] = l;
+  }
+}
+
+// Sums the per-block partials in block order (one thread per parameter).
+__global__ void k_closure_grad_final(const float* gpart, const double* lpart, int nblocks,
+                                     float* grad, double* loss) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < kClosureParams) {
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += (double)gpart[(int64_t)b * kClosureParams + j];
+    grad[j] = (float)s;
+  }
+  if (j == 0) {
+    double l = 0.0;
+    for (int b = 0; b < nblocks; ++b) l += lpart[b];
+    *loss = l;
+  }
+}
+
+// Adam (Kingma and Ba, 2015) on FP32 master weights.
+__global__ void k_adam(float* theta, const float* grad, float* m, float* v, int n, float lr,
+                       float b1, float b2, float eps, float c1, float c2) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const float g = grad[j];
+  const float mj = b1 * m[j] + (1.0f - b1) * g;
+  const float vj = b2 * v[j] + (1.0f - b2) * g * g;
+  m[j] = mj;
+  v[j] = vj;
+  theta[j] -= lr * (mj / c1) / (sqrtf(vj / c2) + eps);
+}
+
+__global__ void k_pack_closure(const float* theta, unsigned* w1, unsigned* w2, float* b) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const float* W1 = theta;
+  const float* b1 = W1 + 32 * 8;
+  const float* W2 = b1 + 32;
+  const float* b2 = W2 + 32 * 32;
+  const float* w3 = b2 + 32;
+  const float* b3 = w3 + 32;
+  if (j < 32 * 4) w1[j] = pack_bf16(W1[2 * j], W1[2 * j + 1]);  // row-major pairs
+  if (j < 32 * 16) w2[j] = pack_bf16(W2[2 * j], W2[2 * j + 1]);
+  if (j < 32) {
+    b[j] = b1[j];
+    b[32 + j] = b2[j];
+    b[64 + j] = w3[j];
+  }
+  if (j == 0) b[96] = b3[0];
+}
+
+}  // namespace
+
+cudaError_t launch_pack_closure(const float* theta, unsigned* w1, unsigned* w2, float* b,
+                                cudaStream_t s) {
+  k_pack_closure<<<2, 256, 0, s>>>(theta, w1, w2, b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_closure(int mode, const StepArgs& a, const ClosureParams& cp,
+                                cudaStream_t s) {
+  if (a.n <= 0 && mode == kModeResidual) return cudaSuccess;
+  const bool comp = a.lo != nullptr;
+  switch (mode) {
+    case kModeFE: return comp ? launch_cl<kModeFE, true>(a, cp, s) : launch_cl<kModeFE, false>(a, cp, s);
+    case kModeRK2a:
+      return comp ? launch_cl<kModeRK2a, true>(a, cp, s) : launch_cl<kModeRK2a, false>(a, cp, s);
+    case kModeRK2b:
+      return comp ? launch_cl<kModeRK2b, true>(a, cp, s) : launch_cl<kModeRK2b, false>(a, cp, s);
+    case kModeResidual: return launch_cl<kModeResidual, false>(a, cp, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int closure_grad_blocks() {
+  static int cached = 0;
+  if (cached == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_closure_grad, kGrThreads, 0) !=
+            cudaSuccess ||
+        per_sm < 1)
+      return 256;
+    cached = sms * per_sm;
+  }
+  return cached;
+}
+
+cudaError_t launch_closure_grad(const StepArgs& a, const float* Ut, double dt, const double* w,
+                                const ClosureParams& cp, float* gpart, double* lpart,
+                                int max_blocks, float* grad, double* loss, cudaStream_t s) {
+  const int64_t want = std::max<int64_t>(1, (a.n + 32 * kGrWarps - 1) / (32 * kGrWarps));
+  const int nb = (int)std::min<int64_t>(want, std::min(max_blocks, closure_grad_blocks()));
+  k_closure_grad<<<nb, kGrThreads, 0, s>>>(a, reinterpret_cast<const float4*>(Ut), (float)dt,
+                                           make_float4((float)w[0], (float)w[1], (float)w[2],
+                                                       (float)w[3]),
+                                           cp, gpart, lpart);
+  k_closure_grad_final<<<(kClosureParams + 255) / 256, 256, 0, s>>>(gpart, lpart, nb, grad, loss);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float* theta, const float* grad, float* m, float* v, int n, double lr,
+                        double b1, double b2, double eps, int64_t step, cudaStream_t s) {
+  const double c1 = 1.0 - std::pow(b1, (double)step), c2 = 1.0 - std::pow(b2, (double)step);
+  k_adam<<<(n + 255) / 256, 256, 0, s>>>(theta, grad, m, v, n, (float)lr, (float)b1, (float)b2,
+                                         (float)eps, (float)c1, (float)c2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_closure_eval(const float* feats, float* s_out, int64_t rows,
+                                const ClosureParams& cp, cudaStream_t s) {
+  if (rows <= 0) return cudaSuccess;
+  k_closure_eval<<<cl_grid(k_closure_eval, kRows, rows), kClThreads, 0, s>>>(feats, s_out, rows,
+                                                                              cp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_closure_scales(const StepArgs& a, const ClosureParams& cp, float* s_out,
+                                  cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  k_closure_scales<<<cl_grid(k_closure_scales, 32, a.n), kClThreads, 0, s>>>(a, cp, s_out);
+  return cudaGetLastError();
+}
+
+}  // namespace fv

@@ -40,6 +40,15 @@ std::vector<int32_t> order_hilbert(const HostMesh& m);
 // Renumbers m in place with perm (new -> old), remapping neighbour ids.
 void apply_permutation(HostMesh& m, const std::vector<int32_t>& perm);
 
+// Device records of a cell range (byte buffers ready to copy):
+//   FP64: nbr int4 (nbr0, nbr1, nbr2, 0); geom doubles n0x n0y n1x n1y n2x n2y 1/V 2V/P
+//   FP32: nbr int2 (nbr1, nbr2); geom floats n0x n0y n1x n1y n2x n2y 1/V nbr0-bits
+struct DeviceLayout {
+  std::vector<unsigned char> nbr, geom;
+};
+DeviceLayout pack_layout(const int32_t* nbr, const double* nrm, const double* vol,
+                         const double* inradius, int64_t n, int32_t meta, bool f64);
+
 // Sec. 4.1 diagnostics on the cell graph of the current numbering.
 int64_t graph_bandwidth(const HostMesh& m);
 int64_t serial_bandwidth(const HostMesh& m);

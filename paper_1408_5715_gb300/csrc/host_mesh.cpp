@@ -142,4 +142,37 @@ void build_host_mesh(const double* xy, int64_t n_nodes, const int32_t* tri, int6
   }
 }
 
+DeviceLayout pack_layout(const int32_t* nbr, const double* nrm, const double* vol,
+                         const double* inradius, int64_t n, int32_t meta, bool f64) {
+  DeviceLayout d;
+  if (f64) {
+    d.nbr.resize(n * 4 * sizeof(int32_t));
+    d.geom.resize(n * 8 * sizeof(double));
+    int32_t* nb = reinterpret_cast<int32_t*>(d.nbr.data());
+    double* g = reinterpret_cast<double*>(d.geom.data());
+    for (int64_t c = 0; c < n; ++c) {
+      nb[4 * c] = nbr[3 * c];
+      nb[4 * c + 1] = nbr[3 * c + 1];
+      nb[4 * c + 2] = nbr[3 * c + 2];
+      nb[4 * c + 3] = meta;
+      for (int k = 0; k < 6; ++k) g[8 * c + k] = nrm[6 * c + k];
+      g[8 * c + 6] = 1.0 / vol[c];
+      g[8 * c + 7] = inradius[c];
+    }
+  } else {
+    d.nbr.resize(n * 2 * sizeof(int32_t));
+    d.geom.resize(n * 8 * sizeof(float));
+    int32_t* nb = reinterpret_cast<int32_t*>(d.nbr.data());
+    float* g = reinterpret_cast<float*>(d.geom.data());
+    for (int64_t c = 0; c < n; ++c) {
+      nb[2 * c] = nbr[3 * c + 1];
+      nb[2 * c + 1] = nbr[3 * c + 2];
+      for (int k = 0; k < 6; ++k) g[8 * c + k] = (float)nrm[6 * c + k];
+      g[8 * c + 6] = (float)(1.0 / vol[c]);
+      std::memcpy(&g[8 * c + 7], &nbr[3 * c], sizeof(int32_t));
+    }
+  }
+  return d;
+}
+
 }  // namespace fv

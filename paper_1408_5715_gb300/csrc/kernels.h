@@ -41,8 +41,11 @@ struct StepArgs {
   const void* U;      // state whose fluxes are evaluated (neighbours and own cell)
   const void* Ubase;  // RK2 second stage: U^n of the own cell (may equal out)
   void* out;          // new state, or the residual in kModeResidual
-  const int4* nbr;    // {nbr0, nbr1, nbr2, unused}; negative = -FV_BC_* ghost
-  const void* geom;   // 8 values per cell: n0x n0y n1x n1y n2x n2y 1/V 2V/P
+  // Neighbours (negative = -FV_BC_* ghost) and geometry, by precision:
+  //   FP64: nbr int4 (nbr0, nbr1, nbr2, -); geom 8 doubles n0x n0y n1x n1y n2x n2y 1/V 2V/P
+  //   FP32: nbr int2 (nbr1, nbr2); geom 8 floats n0x n0y n1x n1y n2x n2y 1/V nbr0-bits
+  const void* nbr;
+  const void* geom;
   int64_t n;
   double uinf[4];     // far-field conserved state
   const unsigned long long* bmin_read;
@@ -53,23 +56,86 @@ struct StepArgs {
   double cfl;         // > 0: CFL number; < 0: fixed dt = -cfl
   double t_stop;      // > 0: clamp the time advanced in this loop
   int* err;
-  // FP32 compensated update: per cell, four bfloat16 remainders (8 bytes)
-  // that carry what the float state could not hold; read and rewritten in
-  // place by the cell's own thread.  nullptr = plain float update.
+  // FP32 compensated update: per cell, four bfloat16 values (8 bytes) holding
+  // what the float state could not; read and rewritten in place by the cell's
+  // own thread.  nullptr = plain float update.
   uint2* lo;
   // RK2 with lo: remainder of the stage state U* (written by the first stage,
   // read by the second).
   uint2* lo_stage;
 };
 
+// Arguments of the batched step kernel: many meshes concatenated into one
+// cell range, each padded to a multiple of kBlock cells.
+struct BatchArgs {
+  StepArgs s;               // arrays over the whole range (n = padded total)
+  const int* block_mesh;    // [n / kBlock] mesh of each block
+  const int64_t* mesh_end;  // [n_meshes] one past the last real cell of each mesh
+  const double* uinf;       // [4 * n_meshes] far-field conserved states
+  unsigned long long* bmin; // [3 * n_meshes] CFL minima, slot-major
+  double* t;                // [2 * n_meshes] time advanced, slot-major
+  int n_meshes;
+  int slot_read, slot_write, slot_reset;
+  int t_read, t_write;
+};
+
+// Learned dissipation scale (closure.cu): MLP 8 -> 32 -> 32 -> 1 with
+// bfloat16 hidden-layer weights.  Flat parameter order of theta (FP32, 1377
+// values): W1[32][8], b1[32], W2[32][32], b2[32], w3[32], b3.
+constexpr int kClosureParams = 32 * 8 + 32 + 32 * 32 + 32 + 32 + 1;
+
+struct ClosureParams {
+  const unsigned* w1;  // [32][4]: bfloat16 pairs (W1[n][2c], W1[n][2c+1])
+  const unsigned* w2;  // [32][16]: bfloat16 pairs (W2[n][2c], W2[n][2c+1])
+  const float* b1;     // [32]
+  const float* b2;     // [32]
+  const float* w3;     // [32]
+  float b3;
+};
+
+cudaError_t launch_step_closure(int mode, const StepArgs& a, const ClosureParams& cp,
+                                cudaStream_t s);
+cudaError_t launch_closure_eval(const float* feats, float* s_out, int64_t rows,
+                                const ClosureParams& cp, cudaStream_t s);
+cudaError_t launch_closure_scales(const StepArgs& a, const ClosureParams& cp, float* s_out,
+                                  cudaStream_t s);
+// Blocks the gradient kernel launches at most on this device.
+int closure_grad_blocks();
+// One-step loss and gradient; gpart [max_blocks * kClosureParams], lpart
+// [max_blocks] scratch; grad [kClosureParams] and loss [1] device outputs.
+cudaError_t launch_closure_grad(const StepArgs& a, const float* Ut, double dt, const double* w,
+                                const ClosureParams& cp, float* gpart, double* lpart,
+                                int max_blocks, float* grad, double* loss, cudaStream_t s);
+cudaError_t launch_adam(float* theta, const float* grad, float* m, float* v, int n, double lr,
+                        double b1, double b2, double eps, int64_t step, cudaStream_t s);
+// theta (device, FP32, kClosureParams) -> w1, w2 (bfloat16 pairs), b (b1 b2 w3 b3)
+cudaError_t launch_pack_closure(const float* theta, unsigned* w1, unsigned* w2, float* b,
+                                cudaStream_t s);
+
+// Shape variants of the step kernel (see k_step): 0 one thread per cell,
+// 1 persistent grid with next-cell prefetch, 2 the same capped at 64
+// registers, 3 and 4 one thread per cell capped at 40 and 32 registers.
+constexpr int kStepVariants = 5;
+
 // float (FV_F32) or double (FV_F64) instantiations
-cudaError_t launch_step(bool f64, int mode, const StepArgs& a, cudaStream_t s);
+cudaError_t launch_step(bool f64, int mode, int variant, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_init_scalars(LoopScalars* d, cudaStream_t s);
 cudaError_t launch_bound(bool f64, const void* U, const void* geom, int64_t n,
                          unsigned long long* bmin, int* err, cudaStream_t s);
 cudaError_t launch_totals(bool f64, const void* U, const double* vol, int64_t n,
                           double* partials /*[kTotalsBlocks*4]*/, double* out /*[4]*/,
                           cudaStream_t s);
+cudaError_t launch_batch_step(bool f64, int mode, const BatchArgs& b, int64_t n_blocks,
+                              cudaStream_t s);
+cudaError_t launch_batch_init(unsigned long long* bmin, double* t, int n_meshes, int* err,
+                              cudaStream_t s);
+cudaError_t launch_batch_bound(bool f64, const void* U, const void* geom, const int* block_mesh,
+                               const int64_t* mesh_end, int n_meshes, int64_t n_blocks,
+                               unsigned long long* bmin, int* err, cudaStream_t s);
+cudaError_t launch_batch_totals(bool f64, const void* U, const double* vol, const int* block_mesh,
+                                const int64_t* mesh_end, const int* mesh_first_block,
+                                int n_meshes, int64_t n_blocks, double* partials, double* out,
+                                cudaStream_t s);
 // *bmin = +inf bits, *flag = 0 (flag nullable)
 cudaError_t launch_reset_min(unsigned long long* bmin, int* flag, cudaStream_t s);
 cudaError_t launch_dt_from_bound(const unsigned long long* bmin, double cfl, double* dt_out,

@@ -285,3 +285,62 @@ def batch_lattices(n_meshes: int = 256, lo: int = 5000, hi: int = 200000, seed: 
     n = np.exp(rng.uniform(math.log(lo), math.log(hi), size=n_meshes))
     ny = np.maximum(np.rint(np.sqrt(n / 4.0)).astype(int), 2)
     return [(2 * int(a), int(a)) for a in ny]
+
+
+def vortex_batch(n_meshes: int = 256, lo: int = 5000, hi: int = 200000, seed: int = 3):
+    """A batch of periodic jittered squares with triangle counts log-uniform in
+    [lo, hi]; each mesh gets a free-stream Mach number U(0.3, 0.8) and, by a
+    seeded coin, a vortex or a uniform initial state.  Returns a list of
+    (MeshInput, primitive free stream, initial state)."""
+    rng = np.random.default_rng(seed + 7919)
+    out = []
+    for k, (nx, ny) in enumerate(batch_lattices(n_meshes, lo, hi, seed)):
+        mi = periodic_square(nx, ny, seed=1000 * seed + k)
+        mach = float(rng.uniform(0.3, 0.8))
+        prim = freestream(mach)
+        if rng.integers(0, 2):
+            U0 = isentropic_vortex(mi.centroids(), mach=mach)
+        else:
+            U0 = uniform_state(mi.n_tri, prim)
+        out.append((mi, prim, U0))
+    return out
+
+
+def refine_midpoint(mi: MeshInput, levels: int = 2):
+    """Splits every triangle into four through its edge midpoints, ``levels``
+    times (16 children per triangle for two levels).  New nodes on boundary
+    edges stay on the straight edge, so the children tile their parent
+    exactly.  Returns (fine MeshInput, parent) where parent[f] is the coarse
+    triangle of fine triangle f; the children of coarse triangle c are the
+    consecutive fine triangles 4**levels * c ... 4**levels * (c + 1) - 1.
+    Periodic meshes are not supported."""
+    if mi.canon is not None:
+        raise ValueError("refinement of periodic meshes is not supported")
+    xy, tri = mi.xy, mi.tri.astype(np.int64)
+    bnd = None if mi.bnd is None else mi.bnd.astype(np.int64)
+    parent = np.arange(tri.shape[0], dtype=np.int64)
+    for _ in range(levels):
+        nn = xy.shape[0]
+        e = np.concatenate([tri[:, [0, 1]], tri[:, [1, 2]], tri[:, [2, 0]]])
+        key = np.sort(e, axis=1)
+        uniq, inv = np.unique(key[:, 0] * nn + key[:, 1], return_inverse=True)
+        a, b = uniq // nn, uniq % nn
+        mid_xy = 0.5 * (xy[a] + xy[b])
+        mid = nn + inv.reshape(3, -1)  # midpoint node of edges 01, 12, 20 per triangle
+        m01, m12, m20 = mid[0], mid[1], mid[2]
+        v0, v1, v2 = tri[:, 0], tri[:, 1], tri[:, 2]
+        kids = np.stack([np.stack([v0, m01, m20], -1), np.stack([m01, v1, m12], -1),
+                         np.stack([m20, m12, v2], -1), np.stack([m01, m12, m20], -1)], axis=1)
+        tri = kids.reshape(-1, 3)
+        parent = np.repeat(parent, 4)
+        if bnd is not None:
+            bk = np.sort(bnd[:, :2], axis=1)
+            pos = np.searchsorted(uniq, bk[:, 0] * nn + bk[:, 1])
+            m = nn + pos
+            bnd = np.concatenate([np.stack([bnd[:, 0], m, bnd[:, 2]], -1),
+                                  np.stack([m, bnd[:, 1], bnd[:, 2]], -1)])
+        xy = np.concatenate([xy, mid_xy])
+    fine = MeshInput(xy, tri.astype(np.int32), None,
+                     None if bnd is None else bnd.astype(np.int32), mi.default_bc,
+                     dict(mi.info, refined=levels))
+    return fine, parent

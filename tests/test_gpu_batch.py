@@ -1,0 +1,107 @@
+"""Batched many-mesh stepping on the GPU: every mesh of a batch advances bit
+for bit as it does alone, with its own dt, time, free stream and totals."""
+import numpy as np
+import pytest
+
+from paper_1408_5715_gb300 import binding as B
+from paper_1408_5715_gb300 import build as BLD
+from paper_1408_5715_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    BLD.build()
+    B.load()
+
+
+def make_set(seed, n_meshes=7):
+    """Uneven meshes: periodic squares of several sizes and a channel with
+    walls and far field, each with its own initial state and free stream."""
+    rng = np.random.default_rng(seed)
+    items = []
+    for k in range(n_meshes):
+        if k == 3:
+            mi = W.channel_bump(40, 17, seed=k)
+            prim = W.freestream(0.55)
+            U0 = W.uniform_state(mi.n_tri, prim)
+        else:
+            ny = int(rng.integers(3, 40))
+            mi = W.periodic_square(2 * ny + int(rng.integers(0, 3)), ny, seed=100 + k)
+            mach = float(rng.uniform(0.3, 0.8))
+            prim = W.freestream(mach)
+            U0 = (W.isentropic_vortex(mi.centroids(), mach=mach) if rng.integers(0, 2)
+                  else W.uniform_state(mi.n_tri, prim))
+        items.append((mi, prim, U0))
+    return items
+
+
+def solo_and_batch(items, prec, nsteps, scheme, t_stop=0.0, comp=True):
+    dt_ = torch.float64 if prec == "f64" else torch.float32
+    meshes, solo = [], []
+    for mi, prim, U0 in items:
+        m = B.Mesh.from_input(mi, prec)
+        m.set_freestream(*prim)
+        m.renumber("rcm")
+        meshes.append(m)
+    # states in each mesh's (renumbered) order: renumber is deterministic
+    perms = []
+    for (mi, prim, U0), m in zip(items, meshes):
+        probe = B.Mesh.from_input(mi, prec)
+        perms.append(probe.renumber("rcm"))
+    for (mi, prim, U0), m, p in zip(items, meshes, perms):
+        if prec == "f32":
+            m.set_compensation(comp)
+        U = torch.tensor(U0[p], dtype=dt_, device="cuda")
+        t = m.step(U, nsteps, 0.4, t_stop=t_stop, scheme=scheme)
+        solo.append((U.cpu().numpy(), t, m.totals(U)))
+    batch = B.Batch(meshes)
+    if prec == "f32":
+        batch.set_compensation(comp)
+    flat = torch.tensor(batch.pack([U0[p] for (mi, prim, U0), p in zip(items, perms)]),
+                        dtype=dt_, device="cuda")
+    tb = batch.step(flat, nsteps, 0.4, t_stop=t_stop, scheme=scheme)
+    return solo, batch, flat, tb
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("scheme", ["fe", "rk2"])
+def test_batch_equals_solo_bitwise(prec, scheme):
+    items = make_set(5)
+    solo, batch, flat, tb = solo_and_batch(items, prec, 131, scheme)
+    got = batch.unpack(flat.cpu().numpy())
+    tot = batch.totals(flat)
+    for k, (Us, ts, Ts) in enumerate(solo):
+        assert np.array_equal(got[k], Us), k
+        assert tb[k] == ts, k
+        scale = np.abs(Us).sum(axis=0) + 1e-300
+        assert (np.abs(tot[k] - Ts) <= 1e-13 * np.abs(Ts).max() + 1e-300).all(), k
+    # the meshes really have different time steps
+    assert len(set(np.round(tb, 12))) > 1
+
+
+def test_batch_t_stop_and_bad_state():
+    items = make_set(6, n_meshes=4)
+    solo, batch, flat, tb = solo_and_batch(items, "f64", 500, "fe", t_stop=0.01)
+    assert np.allclose(tb, 0.01, rtol=1e-14)
+    for k, (Us, ts, _) in enumerate(solo):
+        assert np.array_equal(batch.unpack(flat.cpu().numpy())[k], Us)
+    # a bad state in one mesh is reported for the batch
+    bad = flat.clone()
+    k = 2
+    i = int(batch.offsets[k]) + 5
+    bad[i, 3] = 0.01 * 0.5 * (bad[i, 1] ** 2 + bad[i, 2] ** 2) / bad[i, 0]
+    with pytest.raises(B.FVError) as e:
+        batch.step(bad, 3, 0.4)
+    assert e.value.code == B.FV_ENONFINITE
+
+
+def test_batch_rejects_mixed_precision():
+    a = B.Mesh.from_input(W.periodic_square(4, 4, seed=1), "f32")
+    b = B.Mesh.from_input(W.periodic_square(4, 4, seed=1), "f64")
+    with pytest.raises(B.FVError):
+        B.Batch([a, b])

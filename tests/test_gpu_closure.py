@@ -1,0 +1,221 @@
+"""The learned dissipation scale on the GPU (tensor-core MLP fused into the
+flux) against the FP64 oracle's MLP with the same bfloat16 weights and the
+same bfloat16 rounding of layer inputs.
+
+Tolerances: the GPU computes features in FP32 and accumulates in FP32, the
+oracle in FP64, so a feature or hidden activation that lies within FP32
+rounding of a bfloat16 rounding boundary can round to the neighbouring
+bfloat16 value (a relative change of 2^-8 in one input).  Scales therefore
+agree to 1e-5 for almost all rows and to a few 1e-3 for the rest.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1408_5715_gb300 import binding as B
+from paper_1408_5715_gb300 import build as BLD
+from paper_1408_5715_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+NP = B.CLOSURE_PARAMS
+W1 = slice(0, 256)
+W2 = slice(288, 288 + 1024)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    BLD.build()
+    B.load()
+
+
+def bf16(x):
+    return torch.tensor(np.asarray(x, np.float32)).to(torch.bfloat16).float().numpy()
+
+
+def make_theta(seed, scale=0.5):
+    """FP32 parameters for the GPU and the FP64 values the GPU really uses
+    (hidden-layer weights rounded to bfloat16) for the oracle."""
+    rng = np.random.default_rng(seed)
+    th = (rng.normal(size=NP) * scale).astype(np.float32)
+    th[-1] = 0.3
+    th64 = th.astype(np.float64)
+    th64[W1] = bf16(th[W1])
+    th64[W2] = bf16(th[W2])
+    return th, th64
+
+
+def test_mlp_alone_matches_oracle(orc):
+    th, th64 = make_theta(1)
+    cl = B.Closure(th)
+    rng = np.random.default_rng(2)
+    rows = 5000
+    f = np.abs(rng.normal(size=(rows, 8))) * np.array([0.3, 0.3, 0.3, 0.3, 0.5, 0.3, 1.0, 1.0])
+    f = bf16(f).astype(np.float64)  # bfloat16-exact inputs: no rounding ambiguity at layer 1
+    s_gpu = cl.eval(torch.tensor(f, dtype=torch.float32, device="cuda")).cpu().numpy()
+    s_orc = np.array([orc.closure_mlp(th64, f[i], bf16_acts=True) for i in range(rows)])
+    d = np.abs(s_gpu - s_orc)
+    assert (s_gpu >= 0.2).all() and (s_gpu <= 1.5).all()
+    assert np.quantile(d, 0.99) <= 1e-5, np.quantile(d, [0.5, 0.99, 1.0])
+    assert d.max() <= 5e-3
+    # the scales really vary with the features
+    assert s_gpu.std() > 0.05
+
+
+@pytest.fixture(scope="module")
+def vortex_case():
+    mi = W.periodic_square(40, 24, seed=9)
+    U0 = W.isentropic_vortex(mi.centroids(), mach=0.6, radius=0.15)
+    U0 = U0.astype(np.float32).astype(np.float64)  # float-exact states
+    return mi, U0
+
+
+def test_face_scales_match_oracle_and_are_swap_invariant(orc, vortex_case):
+    mi, U0 = vortex_case
+    th, th64 = make_theta(3)
+    cl = B.Closure(th)
+    g = B.Mesh.from_input(mi, "f32")
+    U = torch.tensor(U0, dtype=torch.float32, device="cuda")
+    s = cl.scales(g, U).cpu().numpy()
+    om = orc.Mesh(mi.xy, mi.tri, mi.canon, None, 0)
+    _, so = om.residual(U0, theta=th64, bf16_acts=True, return_scales=True)
+    d = np.abs(s - so)
+    assert np.quantile(d, 0.99) <= 1e-4, np.quantile(d, [0.5, 0.99, 1.0])
+    assert d.max() <= 2e-2
+    # both cells of every face use the same scale, bit for bit
+    nbr, nrm, _ = g.export()
+    for c in range(mi.n_tri):
+        for k in range(3):
+            m = nbr[c, k]
+            ks = [j for j in range(3) if nbr[m, j] == c and (nrm[m, j] == -nrm[c, k]).all()]
+            assert ks and s[m, ks[0]] == s[c, k]
+
+
+def test_closure_step_matches_oracle_and_conserves(orc, vortex_case):
+    mi, U0 = vortex_case
+    th, th64 = make_theta(4, scale=0.3)
+    cl = B.Closure(th)
+    g = B.Mesh.from_input(mi, "f32")
+    U = torch.tensor(U0, dtype=torch.float32, device="cuda")
+    T0 = g.totals(U)
+    t = g.step(U, 120, 0.4, closure=cl)
+    om = orc.Mesh(mi.xy, mi.tri, mi.canon, None, 0)
+    Uo, to, _, bad = om.run(U0, 120, 0.4, theta=th64, bf16_acts=True)
+    assert not bad and t == pytest.approx(to, rel=1e-5)
+    got = U.double().cpu().numpy()
+    assert np.linalg.norm(got[:, 0] - Uo[:, 0]) / np.linalg.norm(Uo[:, 0]) <= 1e-5
+    # the closure changed the solution compared with the plain flux
+    Up, *_ = om.run(U0, 120, 0.4)
+    assert np.linalg.norm(Up[:, 0] - Uo[:, 0]) / np.linalg.norm(Uo[:, 0]) > 1e-4
+    T1 = g.totals(U)
+    scale = np.abs(U0 * om.vol[:, None]).sum(axis=0)
+    assert (np.abs(T1 - T0) <= 1e-6 * scale).all()
+
+
+@pytest.mark.parametrize("scheme", ["fe", "rk2"])
+def test_unit_scale_reproduces_plain_flux(vortex_case, scheme):
+    mi, U0 = vortex_case
+    th = np.zeros(NP, np.float32)
+    th[-1] = math.log((0.8 / 1.3) / (1.0 - 0.8 / 1.3))  # s = 0.2 + 1.3 sigmoid(b3) ~ 1
+    cl = B.Closure(th)
+    g = B.Mesh.from_input(mi, "f32")
+    A = torch.tensor(U0, dtype=torch.float32, device="cuda")
+    Bt = A.clone()
+    g.step(A, 200, 0.4, scheme=scheme)
+    g.step(Bt, 200, 0.4, scheme=scheme, closure=cl)
+    a, b = A.double().cpu().numpy(), Bt.double().cpu().numpy()
+    assert np.abs(a - b).max() <= 1e-5 * np.abs(a).max()
+    s = cl.scales(g, A).cpu().numpy()
+    assert np.abs(s - 1.0).max() <= 2e-7
+
+
+def test_closure_residual_and_errors(vortex_case):
+    mi, U0 = vortex_case
+    th, _ = make_theta(5)
+    cl = B.Closure(th)
+    g = B.Mesh.from_input(mi, "f32")
+    U = torch.tensor(U0, dtype=torch.float32, device="cuda")
+    R1 = g.residual(U, closure=cl)
+    R0 = g.residual(U)
+    assert torch.isfinite(R1).all() and not torch.equal(R0, R1)
+    g64 = B.Mesh.from_input(mi, "f64")
+    with pytest.raises(B.FVError):
+        g64.step(torch.tensor(U0, device="cuda"), 1, 0.4, closure=cl)
+
+
+def test_closure_gradient_matches_oracle(orc):
+    # channel with walls and far field: ghost faces take part too
+    mi = W.channel_bump(36, 14, seed=12)
+    prim = W.freestream(0.5)
+    uinf = W.conserved(*prim)
+    U0 = W.random_smooth_state(mi.centroids(), seed=6).astype(np.float32).astype(np.float64)
+    rng = np.random.default_rng(7)
+    Ut = (U0 + 0.02 * rng.normal(size=U0.shape)).astype(np.float32).astype(np.float64)
+    th, th64 = make_theta(8, scale=0.4)
+    dt, w = 2e-3, np.array([1.0, 0.5, 0.5, 2.0])
+    g = B.Mesh.from_input(mi, "f32")
+    g.set_freestream(*prim)
+    cl = B.Closure(th)
+    Ud = torch.tensor(U0, dtype=torch.float32, device="cuda")
+    Utd = torch.tensor(Ut, dtype=torch.float32, device="cuda")
+    loss, grad = cl.loss_grad(g, Ud, Utd, dt, w)
+    grad = grad.cpu().numpy().astype(np.float64)
+    om = orc.Mesh(mi.xy, mi.tri, None, mi.bnd, 0, uinf)
+    lo, go = om.closure_loss_grad(U0, Ut, dt, w, th64, bf16_acts=True)
+    assert loss == pytest.approx(lo, rel=1e-4)
+    err = np.linalg.norm(grad - go) / np.linalg.norm(go)
+    assert err <= 3e-3, err
+    # layer by layer, each block of parameters on its own
+    for sl in (slice(0, 256), slice(256, 288), slice(288, 1312), slice(1312, 1344),
+               slice(1344, 1376), slice(1376, 1377)):
+        e = np.linalg.norm(grad[sl] - go[sl]) / (np.linalg.norm(go[sl]) + 1e-30)
+        assert e <= 1e-2, (sl, e)
+    # deterministic
+    loss2, grad2 = cl.loss_grad(g, Ud, Utd, dt, w)
+    assert loss2 == loss and np.array_equal(grad2.cpu().numpy().astype(np.float64), grad)
+
+
+def test_adam_matches_reference_update():
+    rng = np.random.default_rng(9)
+    n = 1377
+    th = rng.normal(size=n).astype(np.float32)
+    m = np.zeros(n, np.float32)
+    v = np.zeros(n, np.float32)
+    t_th, t_m, t_v = (torch.tensor(x, device="cuda") for x in (th, m, v))
+    for step in range(1, 4):
+        gr = rng.normal(size=n).astype(np.float32)
+        B.adam_step(t_th, torch.tensor(gr, device="cuda"), t_m, t_v, step, lr=1e-2)
+        m = 0.9 * m + 0.1 * gr
+        v = 0.999 * v + 0.001 * gr * gr
+        th = th - 1e-2 * (m / (1 - 0.9 ** step)) / (np.sqrt(v / (1 - 0.999 ** step)) + 1e-8)
+    np.testing.assert_allclose(t_th.cpu().numpy(), th, rtol=1e-5, atol=1e-6)
+
+
+def test_training_lowers_one_step_loss(vortex_case):
+    # target: one plain step with the dissipation halved everywhere (reachable
+    # through b3 alone); a few Adam steps on the GPU must lower the loss
+    mi, U0 = vortex_case
+    g = B.Mesh.from_input(mi, "f32")
+    U = torch.tensor(U0, dtype=torch.float32, device="cuda")
+    th_t = np.zeros(NP, np.float32)
+    th_t[-1] = math.log((0.3 / 1.3) / (1.0 - 0.3 / 1.3))  # s = 0.5
+    target = B.Closure(th_t)
+    dt = 0.4 * g.compute_dt(U, 1.0)
+    Ut = U.clone()
+    g.step(Ut, 1, -dt, closure=target)
+    theta = torch.tensor(make_theta(10, scale=0.1)[0], device="cuda")
+    m = torch.zeros_like(theta)
+    v = torch.zeros_like(theta)
+    cl = B.Closure(theta.cpu().numpy())
+    w = (1e-3, 1e-3, 1e-3, 1e-3)
+    first = None
+    for step in range(1, 61):
+        loss, grad = cl.loss_grad(g, U, Ut, dt, w)
+        first = loss if first is None else first
+        B.adam_step(theta, grad, m, v, step, lr=3e-2)
+        cl.set(theta)
+    assert loss < 0.2 * first, (first, loss)

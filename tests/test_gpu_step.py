@@ -201,6 +201,45 @@ def test_compensated_fp32_tracks_fp64_over_long_runs(scheme):
     assert e_plain > 10 * e_comp, (e_plain, e_comp)
 
 
+@pytest.fixture(scope="module")
+def big_square():
+    # 240,000 cells: more than two sweeps of every persistent grid
+    mi = W.periodic_square(400, 300, seed=31)
+    return mi, W.isentropic_vortex(mi.centroids(), mach=0.6)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("scheme", ["fe", "rk2"])
+def test_kernel_shapes_give_identical_results(big_square, prec, scheme):
+    mi, U0 = big_square
+    dt_ = torch.float64 if prec == "f64" else torch.float32
+    outs, ts = [], []
+    for v in range(5):
+        g = B.Mesh.from_input(mi, prec)
+        g.renumber("hilbert")
+        g.set_variant(v)
+        U = dev(U0, dt_)
+        ts.append(g.step(U, 30, 0.4, scheme=scheme))
+        outs.append(U)
+        g.close()
+    for v in range(1, 5):
+        assert ts[v] == ts[0]
+        assert torch.equal(outs[v], outs[0]), v
+
+
+def test_autotune_picks_a_shape_and_leaves_state(big_square):
+    mi, U0 = big_square
+    g = B.Mesh.from_input(mi, "f32")
+    U = dev(U0, torch.float32)
+    before = U.clone()
+    best, us = g.autotune(U)
+    assert 0 <= best < 5 and len(us) == 5 and all(x > 0 for x in us)
+    assert us[best] == min(us)
+    assert torch.equal(U, before)
+    with pytest.raises(B.FVError):
+        g.set_variant(7)
+
+
 def test_conservation_and_free_stream_on_gpu(c1):
     mi, U0, om, g64, g32 = c1
     U = dev(U0, torch.float64)
