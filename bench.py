@@ -90,8 +90,12 @@ def measured_peaks():
 
 
 def kernel_source_hash():
-    with open(os.path.join(ROOT, "paper_1408_5715_gb300", "csrc", "kernels.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    """Hash of the sources of the step kernels (ties a profile to a kernel)."""
+    h = hashlib.sha256()
+    for name in ("cell_math.cuh", "kernels.cu", "kernels.h"):
+        with open(os.path.join(ROOT, "paper_1408_5715_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def profiled_traffic(name):
@@ -382,6 +386,8 @@ def extras(args, B, spec, mi, U0, U0p, perm, m32, S, U32_final, out):
         out["square_16m"] = res
     # ---- many meshes in one launch per step (256 periodic squares, 5k-200k cells)
     out["batched"] = batched_leg(B)
+    # ---- learned dissipation scale: cost per step on the 250k-cell coarse channel
+    out["learned"] = learned_leg(B)
     # ---- FP64 CPU oracle on one host core, bounded sample of this workload
     out["cpu_baseline"] = cpu_baseline(spec, mi, U0, budget_s=12.0)
 
@@ -425,6 +431,30 @@ def batched_leg(B, time_steps=1000):
            "achieved_gbs_kernel_bytes": gbs, "frac_of_measured_hbm": gbs / peak,
            "launches_per_step": time_steps + 4}
     batch.close()
+    return res
+
+
+def learned_leg(B, time_steps=2000):
+    import torch
+    from paper_1408_5715_gb300 import closure_training as CT
+    mi = W.channel_bump(625, 200, seed=5)
+    m = B.Mesh.from_input(mi, "f32")
+    m.set_freestream(*W.freestream(0.5))
+    m.renumber("rcm")
+    cl = B.Closure(CT.initial_theta(1, 0.3))
+    cost = CT.step_cost(m, cl, steps=time_steps)
+    n = mi.n_tri
+    # tensor-core work per face evaluation: layer 1 (K padded 8 -> 16) and layer 2
+    mma_flops = 2 * (16 * 32 + 32 * 32)
+    res = {"cells": n, "time_steps": time_steps, "us_per_step_plain": cost["plain"],
+           "us_per_step_learned": cost["learned"],
+           "value": n / (cost["learned"] * 1e-6), "unit": "cell-updates/s",
+           "overhead": cost["learned"] / cost["plain"],
+           "mma_flops_per_cell": 3 * mma_flops,
+           "mma_tflops": 3 * mma_flops * n / (cost["learned"] * 1e-6) / 1e12,
+           "kernel": "k_step_closure<FE, compensated> (mma.sync m16n8k16 bf16)"}
+    m.close()
+    cl.close()
     return res
 
 

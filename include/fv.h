@@ -58,6 +58,7 @@ extern "C" {
 #define FV_ORDER_SHUFFLE 1 /* uniform random permutation from the seed */
 #define FV_ORDER_RCM 2     /* reverse Cuthill-McKee from a pseudo-peripheral cell */
 #define FV_ORDER_HILBERT 3 /* Hilbert curve through the cell centroids */
+#define FV_ORDER_AM1 4     /* Amoeba1, the paper's serial-bandwidth heuristic (Sec. 4.2) */
 
 /* ---- time schemes of fv_step ----------------------------------------------- */
 #define FV_SCHEME_FE 0  /* forward Euler, Eq. 6 and the update equation of Sec. 6.2.2 */
@@ -141,18 +142,49 @@ int fv_mesh_set_compensation(fv_mesh* mesh, int32_t enable);
 /* Shape of the step kernel: 0 one thread per cell; 1 (default) a persistent
  * grid of resident blocks that walks the cells and prefetches the next
  * cell's records; 2 the same limited to 64 registers per thread; 3 and 4 one
- * thread per cell limited to 40 and 32 registers.  All give bitwise identical
- * results; only speed differs.  FV_EINVAL outside 0..4. */
+ * thread per cell limited to 40 and 32 registers; 5 a persistent grid whose
+ * cell records are staged in shared memory by bulk (TMA) copies.  All give
+ * bitwise identical results; only speed differs.  FV_EINVAL outside 0..5. */
 int fv_mesh_set_variant(fv_mesh* mesh, int32_t variant);
 
 /* Times every step-kernel shape on this mesh (a few steps each on a device
  * copy of U with a negligible fixed dt; U itself is not changed), keeps the
  * fastest for later fv_step calls and reports it in *best (nullable);
- * us_per_step (nullable, host, [5]) receives the measured microseconds per
+ * us_per_step (nullable, host, [6]) receives the measured microseconds per
  * step of each shape.  Allocates and frees one state-sized device buffer and
- * synchronises the stream.  us_per_step has one entry per shape (5). */
+ * synchronises the stream.  us_per_step has one entry per shape (6). */
 int fv_mesh_autotune(fv_mesh* mesh, const void* U, int32_t scheme, void* stream, int32_t* best,
                      double* us_per_step);
+
+/* Polls of a device-side wait before it gives up (shape 5 waits for its bulk
+ * copies on mbarriers).  A wait that gives up makes the kernel stop, drain its
+ * own copies in flight (with the default limit) and set an error bit, and
+ * fv_step / fv_mesh_status return FV_ETIMEOUT; the state is then not valid.
+ * Default 2^24.  A limit of 0 forces the timeout path (for tests). */
+int fv_mesh_set_wait_limit(fv_mesh* mesh, uint32_t polls);
+
+/* ===========================================================================
+ * Partitioning for several processes (host only).  Part p of nparts owns the
+ * contiguous range [p*n/nparts, (p+1)*n/nparts) of the current numbering
+ * (renumber first: RCM or Hilbert ranges are compact).  Its local numbering is
+ * the owned cells in global order followed by its halo: every other cell that
+ * an owned cell has as a neighbour, in ascending global id.  Stepping a part
+ * needs the halo states from their owners after every stage and the minimum
+ * of the CFL bound over all parts (the paper's design is one FPGA; several
+ * FPGAs are its future work, Sec. 8).
+ * ======================================================================== */
+
+/* Sizes of part `part`: owned cells and halo cells. */
+int fv_partition_sizes(const fv_mesh* mesh, int32_t nparts, int32_t part, int64_t* n_owned,
+                       int64_t* n_halo);
+
+/* Host arrays of part `part` (all nullable):
+ *   global_ids[n_owned + n_halo]  local -> global cell id
+ *   halo_owner[n_halo]            part that owns each halo cell
+ *   nbr[3 * n_owned]              neighbours in local ids (ghost codes < 0)
+ *   normals[6 * n_owned], area[n_owned]  geometry of the owned cells */
+int fv_partition_local(const fv_mesh* mesh, int32_t nparts, int32_t part, int64_t* global_ids,
+                       int32_t* halo_owner, int32_t* nbr, double* normals, double* area);
 
 /* Creates or refreshes the device arrays now, on `stream` (otherwise the
  * first device call does it).  Allocates device memory. */

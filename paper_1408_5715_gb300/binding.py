@@ -18,7 +18,7 @@ from . import build as _build
 FV_OK, FV_EINVAL, FV_ENOMEM, FV_ECUDA, FV_ENONFINITE, FV_ETIMEOUT = range(6)
 FV_F32, FV_F64 = 0, 1
 FV_BC_NONE, FV_BC_WALL, FV_BC_FARFIELD, FV_BC_EXTRAP = 0, 1, 2, 3
-ORDERS = {"identity": 0, "shuffle": 1, "rcm": 2, "hilbert": 3}
+ORDERS = {"identity": 0, "shuffle": 1, "rcm": 2, "hilbert": 3, "am1": 4}
 SCHEMES = {"fe": 0, "rk2": 1}
 
 _lock = threading.Lock()
@@ -63,8 +63,11 @@ def load():
             "fv_mesh_diagnostics": (ctypes.c_int, [_vp, _P(_i64), _P(_i64)]),
             "fv_mesh_export": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
             "fv_mesh_upload": (ctypes.c_int, [_vp, _vp]),
+            "fv_partition_sizes": (ctypes.c_int, [_vp, _i32, _i32, _P(_i64), _P(_i64)]),
+            "fv_partition_local": (ctypes.c_int, [_vp, _i32, _i32, _vp, _vp, _vp, _vp, _vp]),
             "fv_mesh_set_compensation": (ctypes.c_int, [_vp, _i32]),
             "fv_mesh_set_variant": (ctypes.c_int, [_vp, _i32]),
+            "fv_mesh_set_wait_limit": (ctypes.c_int, [_vp, ctypes.c_uint32]),
             "fv_mesh_autotune": (ctypes.c_int, [_vp, _vp, _i32, _vp, _P(_i32), _P(_dbl)]),
             "fv_step": (ctypes.c_int, [_vp, _vp, _i64, _dbl, _dbl, _i32, _vp, _vp, _P(_dbl)]),
             "fv_mesh_status": (ctypes.c_int, [_vp, _vp, _P(_dbl)]),
@@ -187,6 +190,23 @@ class Mesh:
     def set_compensation(self, enable: bool):
         _check(load().fv_mesh_set_compensation(self._h, int(bool(enable))))
 
+    def partition(self, nparts, part):
+        """Local view of one part: dict with global_ids, halo_owner, nbr,
+        normals, area, n_owned (host numpy arrays)."""
+        lib = load()
+        no, nh = _i64(), _i64()
+        _check(lib.fv_partition_sizes(self._h, nparts, part, ctypes.byref(no), ctypes.byref(nh)))
+        no, nh = int(no.value), int(nh.value)
+        gid = np.empty(no + nh, np.int64)
+        owner = np.empty(nh, np.int32)
+        nbr = np.empty((no, 3), np.int32)
+        nrm = np.empty((no, 3, 2), np.float64)
+        area = np.empty(no, np.float64)
+        _check(lib.fv_partition_local(self._h, nparts, part, _np_ptr(gid), _np_ptr(owner),
+                                      _np_ptr(nbr), _np_ptr(nrm), _np_ptr(area)))
+        return dict(n_owned=no, global_ids=gid, halo_owner=owner, nbr=nbr, normals=nrm,
+                    area=area)
+
     # -- device side -----------------------------------------------------------
     def upload(self, stream=None):
         _check(load().fv_mesh_upload(self._h, _stream_ptr(stream)))
@@ -204,11 +224,14 @@ class Mesh:
     def set_variant(self, variant: int):
         _check(load().fv_mesh_set_variant(self._h, int(variant)))
 
+    def set_wait_limit(self, polls: int):
+        _check(load().fv_mesh_set_wait_limit(self._h, int(polls)))
+
     def autotune(self, U, scheme="fe", stream=None):
         """Picks the fastest step-kernel shape for this mesh; returns
         (best, microseconds per step of each shape)."""
         best = _i32()
-        us = (_dbl * 5)()
+        us = (_dbl * 6)()
         _check(load().fv_mesh_autotune(self._h, _dev_ptr(U, self.torch_dtype, self.n, "U"),
                                        SCHEMES[scheme], _stream_ptr(stream), ctypes.byref(best),
                                        us))

@@ -109,6 +109,7 @@ struct fv_mesh {
   uint2* d_lo_stage = nullptr;  // ... and of the RK2 stage state
   bool compensated = true;      // FP32 meshes only
   int variant = 1;              // step-kernel shape (fv_mesh_autotune / fv_mesh_set_variant)
+  unsigned wait_limit = fv::kDefaultWaitLimit;  // bounded device waits (variant 5)
   fv::LoopScalars* d_scal = nullptr;
   double* d_partials = nullptr;
   cudaStream_t cap_stream = nullptr;
@@ -170,7 +171,9 @@ void ensure_device(fv_mesh* m, cudaStream_t s) {
   const int64_t n = m->h.n;
   if (m->dev_n != n) {
     m->free_device();
-    const size_t nn = (size_t)std::max<int64_t>(n, 1);
+    // whole tiles: the TMA-staged step copies whole tiles of these arrays
+    const size_t nn = (size_t)((std::max<int64_t>(n, 1) + fv::kPadCells - 1) / fv::kPadCells *
+                               fv::kPadCells);
     FV_CUDA(cudaMalloc(&m->d_nbr, nn * (m->f64() ? sizeof(int4) : sizeof(int2))));
     FV_CUDA(cudaMalloc(&m->d_geom, nn * 2 * m->rec_bytes()));
     FV_CUDA(cudaMalloc((void**)&m->d_vol, nn * sizeof(double)));
@@ -207,6 +210,8 @@ fv::StepArgs base_args(const fv_mesh* m) {
   a.n = m->h.n;
   m->uinf_conserved(a.uinf);
   a.err = &m->d_scal->err;
+  a.wait_limit = m->wait_limit;
+  a.drain_limit = fv::kDefaultWaitLimit;
   return a;
 }
 
@@ -280,6 +285,8 @@ void read_status(fv_mesh* m, cudaStream_t s, double* t_adv, bool check) {
   FV_CUDA(cudaMemcpyAsync(&h, m->d_scal, sizeof h, cudaMemcpyDeviceToHost, s));
   FV_CUDA(cudaStreamSynchronize(s));
   if (t_adv) *t_adv = h.t[m->last_t_slot];
+  if (check && (h.err & 2))
+    throw fv::Error{FV_ETIMEOUT, "a bounded device wait gave up; the state is not valid"};
   if (check && h.err) throw fv::Error{FV_ENONFINITE, "a step produced a non-finite state or "
                                                      "non-positive density or pressure"};
 }
@@ -364,6 +371,7 @@ int fv_renumber(fv_mesh* mesh, int32_t order, uint64_t seed, int32_t* perm_out) 
       case FV_ORDER_SHUFFLE: perm = fv::order_shuffle(mesh->h.n, seed); break;
       case FV_ORDER_RCM: perm = fv::order_rcm(mesh->h); break;
       case FV_ORDER_HILBERT: perm = fv::order_hilbert(mesh->h); break;
+      case FV_ORDER_AM1: perm = fv::order_am1(mesh->h); break;
       default: invalid("unknown order");
     }
     fv::apply_permutation(mesh->h, perm);
@@ -405,6 +413,14 @@ int fv_mesh_set_variant(fv_mesh* mesh, int32_t variant) {
     check_mesh(mesh);
     if (variant < 0 || variant >= fv::kStepVariants) invalid("unknown step-kernel variant");
     mesh->variant = variant;
+    mesh->drop_graph();
+  });
+}
+
+int fv_mesh_set_wait_limit(fv_mesh* mesh, uint32_t polls) {
+  return guarded([&] {
+    check_mesh(mesh);
+    mesh->wait_limit = polls;
     mesh->drop_graph();
   });
 }
@@ -466,6 +482,30 @@ int fv_mesh_autotune(fv_mesh* mesh, const void* U, int32_t scheme, void* stream,
     if (best) *best = b;
     if (us_per_step)
       for (int v = 0; v < fv::kStepVariants; ++v) us_per_step[v] = times[v];
+  });
+}
+
+int fv_partition_sizes(const fv_mesh* mesh, int32_t nparts, int32_t part, int64_t* n_owned,
+                       int64_t* n_halo) {
+  return guarded([&] {
+    check_mesh(mesh);
+    const fv::LocalPart lp = fv::build_local_part(mesh->h, nparts, part);
+    if (n_owned) *n_owned = lp.n_owned;
+    if (n_halo) *n_halo = (int64_t)lp.global.size() - lp.n_owned;
+  });
+}
+
+int fv_partition_local(const fv_mesh* mesh, int32_t nparts, int32_t part, int64_t* global_ids,
+                       int32_t* halo_owner, int32_t* nbr, double* normals, double* area) {
+  return guarded([&] {
+    check_mesh(mesh);
+    const fv::LocalPart lp = fv::build_local_part(mesh->h, nparts, part);
+    const int64_t nh = (int64_t)lp.global.size() - lp.n_owned;
+    if (global_ids) std::memcpy(global_ids, lp.global.data(), lp.global.size() * sizeof(int64_t));
+    if (halo_owner) std::memcpy(halo_owner, lp.halo_owner.data(), nh * sizeof(int32_t));
+    if (nbr) std::memcpy(nbr, lp.nbr.data(), lp.nbr.size() * sizeof(int32_t));
+    if (normals) std::memcpy(normals, lp.nrm.data(), lp.nrm.size() * sizeof(double));
+    if (area) std::memcpy(area, lp.vol.data(), lp.vol.size() * sizeof(double));
   });
 }
 

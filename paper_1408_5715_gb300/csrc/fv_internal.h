@@ -36,6 +36,7 @@ void build_host_mesh(const double* xy, int64_t n_nodes, const int32_t* tri, int6
 std::vector<int32_t> order_shuffle(int64_t n, uint64_t seed);
 std::vector<int32_t> order_rcm(const HostMesh& m);
 std::vector<int32_t> order_hilbert(const HostMesh& m);
+std::vector<int32_t> order_am1(const HostMesh& m);
 
 // Renumbers m in place with perm (new -> old), remapping neighbour ids.
 void apply_permutation(HostMesh& m, const std::vector<int32_t>& perm);
@@ -48,6 +49,21 @@ struct DeviceLayout {
 };
 DeviceLayout pack_layout(const int32_t* nbr, const double* nrm, const double* vol,
                          const double* inradius, int64_t n, int32_t meta, bool f64);
+
+// Partitioning into contiguous ranges of the current numbering (partition.cpp).
+struct PartRange {
+  int64_t begin = 0, end = 0;
+};
+struct LocalPart {
+  int64_t n_owned = 0;
+  std::vector<int64_t> global;      // [n_owned + n_halo] local -> global cell id
+  std::vector<int32_t> halo_owner;  // [n_halo] part owning each halo cell
+  std::vector<int32_t> nbr;         // [3 n_owned] local neighbour ids / ghost codes
+  std::vector<double> nrm;          // [6 n_owned]
+  std::vector<double> vol;          // [n_owned]
+};
+PartRange part_range(int64_t n, int32_t nparts, int32_t part);
+LocalPart build_local_part(const HostMesh& m, int32_t nparts, int32_t part);
 
 // Sec. 4.1 diagnostics on the cell graph of the current numbering.
 int64_t graph_bandwidth(const HostMesh& m);

@@ -372,6 +372,8 @@ cudaError_t launch_step_t(int mode, int var, const StepArgs& a, cudaStream_t s) 
 }  // namespace
 
 cudaError_t launch_step(bool f64, int mode, int variant, const StepArgs& a, cudaStream_t s) {
+  if (variant == 5 && mode != kModeResidual && a.n > 0) return launch_step_tma(f64, mode, a, s);
+  if (variant == 5) variant = 0;
   if (f64) return launch_step_t<double, false>(mode, variant, a, s);
   return a.lo ? launch_step_t<float, true>(mode, variant, a, s)
               : launch_step_t<float, false>(mode, variant, a, s);

@@ -63,6 +63,10 @@ struct StepArgs {
   // RK2 with lo: remainder of the stage state U* (written by the first stage,
   // read by the second).
   uint2* lo_stage;
+  // Bounded waits of the TMA-staged variant: polls of an mbarrier before a
+  // wait gives up (error bit 2), and polls allowed to drain copies in flight.
+  unsigned wait_limit;
+  unsigned drain_limit;
 };
 
 // Arguments of the batched step kernel: many meshes concatenated into one
@@ -114,8 +118,15 @@ cudaError_t launch_pack_closure(const float* theta, unsigned* w1, unsigned* w2, 
 
 // Shape variants of the step kernel (see k_step): 0 one thread per cell,
 // 1 persistent grid with next-cell prefetch, 2 the same capped at 64
-// registers, 3 and 4 one thread per cell capped at 40 and 32 registers.
-constexpr int kStepVariants = 5;
+// registers, 3 and 4 one thread per cell capped at 40 and 32 registers,
+// 5 persistent grid with TMA-staged cell records (tma_step.cu).
+constexpr int kStepVariants = 6;
+// Library-owned per-cell arrays are allocated in whole tiles of this many
+// cells (the TMA-staged variant copies whole tiles of them).
+constexpr int64_t kPadCells = 256;
+constexpr unsigned kDefaultWaitLimit = 1u << 24;
+
+cudaError_t launch_step_tma(bool f64, int mode, const StepArgs& a, cudaStream_t s);
 
 // float (FV_F32) or double (FV_F64) instantiations
 cudaError_t launch_step(bool f64, int mode, int variant, const StepArgs& a, cudaStream_t s);

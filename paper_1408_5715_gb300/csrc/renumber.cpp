@@ -8,6 +8,7 @@
 //     cites in Sec. 4.2), neighbours visited by ascending degree, then index;
 //   - a Hilbert space-filling curve through the cell centroids (16 bits per
 //     axis of the bounding box), stable in the old index;
+//   - Amoeba1, the paper's own constructive serial-bandwidth heuristic;
 //   - a uniform shuffle (Fisher-Yates driven by SplitMix64) as the worst case.
 // Diagnostics: bandwidth B_f(G) and serial bandwidth S_BW (Sec. 4.1).
 #include <algorithm>
@@ -144,6 +145,84 @@ std::vector<int32_t> order_rcm(const HostMesh& m) {
     }
   }
   std::reverse(order.begin(), order.end());
+  return order;
+}
+
+// Amoeba1 (Sec. 4.2): a constructive, breadth-first-like labelling aimed at a
+// small serial bandwidth.  The labelled part P grows one node at a time.  For
+// a labelled node i: s(i) is the largest label distance to a labelled
+// neighbour below it, u(i) its unlabelled neighbours, and with n = |P| its
+// importance is imp(i) = (n - i) + |u(i)| + s(i) (zero once u(i) is empty).
+// I is the first label whose u() is not empty.  Among the nodes of u(I) the
+// next label goes to the one with a labelled neighbour (other than I) of
+// largest importance; ties keep the first candidate (the smallest node id
+// of u(I), standing in for the paper's random choice).  Each component starts
+// from a pseudo-peripheral node, as GPS finds one (Sec. 4.2).
+std::vector<int32_t> order_am1(const HostMesh& m) {
+  const int64_t n = m.n;
+  Adjacency a = adjacency(m);
+  std::vector<int32_t> order;  // label -> node
+  order.reserve(n);
+  std::vector<int64_t> label(n, -1), s(n, 0);
+  std::vector<int8_t> uncovered(n, 0);  // |u(i)|
+  for (int64_t c = 0; c < n; ++c) uncovered[c] = a.deg[c];
+  std::vector<int32_t> mark(n, -1), queue, last;
+  int32_t stamp = 0;
+  auto add = [&](int32_t v) {
+    const int64_t lv = (int64_t)order.size();
+    label[v] = lv;
+    order.push_back(v);
+    for (int k = 0; k < a.deg[v]; ++k) {
+      const int32_t x = a.nb[3 * v + k];
+      if (label[x] >= 0) {
+        s[v] = std::max<int64_t>(s[v], lv - label[x]);
+        --uncovered[x];  // v is no longer uncovered for x
+        --uncovered[v];
+      }
+    }
+  };
+  auto imp = [&](int32_t v) -> int64_t {
+    if (uncovered[v] == 0) return 0;
+    return ((int64_t)order.size() - label[v]) + uncovered[v] + s[v];
+  };
+  int64_t I = 0;  // label of the first node with uncovered neighbours
+  for (int64_t seed = 0; seed < n; ++seed) {
+    if (label[seed] >= 0) continue;
+    int32_t root = (int32_t)seed;
+    int depth = bfs_last_level(a, root, mark, stamp++, queue, last);
+    for (int iter = 0; iter < 64; ++iter) {
+      int32_t cand = last[0];
+      for (int32_t x : last)
+        if (a.deg[x] < a.deg[cand] || (a.deg[x] == a.deg[cand] && x < cand)) cand = x;
+      int d2 = bfs_last_level(a, cand, mark, stamp++, queue, last);
+      if (d2 <= depth) break;
+      root = cand;
+      depth = d2;
+    }
+    add(root);
+    for (;;) {
+      while (I < (int64_t)order.size() && uncovered[order[I]] == 0) ++I;
+      if (I >= (int64_t)order.size()) break;  // component done
+      const int32_t nodeI = order[I];
+      int32_t first = -1, cand = -1;
+      int64_t best = 0;
+      for (int k = 0; k < a.deg[nodeI]; ++k) {
+        const int32_t x = a.nb[3 * nodeI + k];
+        if (label[x] >= 0) continue;
+        if (first < 0 || x < first) first = x;
+        int64_t local = 0;
+        for (int j = 0; j < a.deg[x]; ++j) {
+          const int32_t l = a.nb[3 * x + j];
+          if (label[l] >= 0 && l != nodeI) local = std::max(local, imp(l));
+        }
+        if (local > best) {
+          best = local;
+          cand = x;
+        }
+      }
+      add(best > 0 ? cand : first);
+    }
+  }
   return order;
 }
 

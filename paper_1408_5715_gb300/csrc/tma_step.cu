@@ -1,0 +1,282 @@
+// tma_step.cu -- the fused step with its per-cell records staged through
+// shared memory by the Tensor Memory Accelerator (shape variant 5).
+//
+// A persistent block owns tiles of kTile consecutive cells (tile = block,
+// block + grid, ...).  For each tile one thread issues 1D bulk copies
+// (cp.async.bulk) of the tile's slices of the state, geometry, neighbour ids
+// and remainders into one of two shared-memory stages; the copies complete on
+// that stage's mbarrier.  While the block computes tile k from one stage, the
+// copies of tile k+1 are in flight into the other, so the loads stay in
+// flight without holding registers.  A neighbour that lies in the current
+// tile is read from shared memory; others come through L1/L2.
+//
+// Every wait on an mbarrier is bounded by a_.wait_limit polls.  When a wait
+// gives up, the kernel sets bit 2 of the error word (the host reports
+// FV_ETIMEOUT), stops computing, waits (bounded again) for its own copies
+// still in flight and returns.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "cell_math.cuh"
+#include "kernels.h"
+
+namespace fv {
+
+namespace {
+
+constexpr int kTile = kBlock;  // cells per tile = threads per block
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// 1D bulk copy global -> shared, completing `bytes` on the mbarrier.
+// Both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned bytes,
+                                          uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Polls the barrier at most `limit` times; false if it did not complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsigned limit) {
+  for (unsigned it = 0; it < limit; ++it)
+    if (mbar_test(bar, parity)) return true;
+  return false;
+}
+
+template <typename R>
+struct TileLayout {
+  // byte sizes of one cell's records
+  static constexpr unsigned kU = sizeof(rec_t<R>);
+  static constexpr unsigned kGeom = 2 * sizeof(rec_t<R>);
+  static constexpr unsigned kNbr = sizeof(R) == 8 ? 16 : 8;
+  static constexpr unsigned kLo = 8;
+};
+
+template <typename R, int MODE, bool COMP>
+struct __align__(128) TileStage {
+  rec_t<R> U[kTile];
+  rec_t<R> geom[2 * kTile];
+  unsigned char nbr[kTile * TileLayout<R>::kNbr];
+  rec_t<R> base[MODE == kModeRK2b ? kTile : 1];
+  uint2 lo[COMP ? kTile : 1];
+  uint2 lo_stage[(COMP && MODE == kModeRK2b) ? kTile : 1];
+};
+
+// Issues the copies of tile `t` into stage `st`; the tile holds `cnt` cells.
+// Library-owned arrays are padded to whole tiles, so their slices are always
+// whole multiples of 16 bytes; the caller's state is 16 or 32 bytes a cell.
+template <typename R, int MODE, bool COMP>
+__device__ __forceinline__ void issue_tile(const StepArgs& a, TileStage<R, MODE, COMP>& st,
+                                           uint64_t* bar, int64_t t, unsigned cnt) {
+  using L = TileLayout<R>;
+  const int64_t c0 = t * kTile;
+  const unsigned full = kTile;
+  unsigned bytes = cnt * L::kU + full * (L::kGeom + L::kNbr);
+  if (MODE == kModeRK2b) bytes += cnt * L::kU;
+  if (COMP) bytes += full * L::kLo;
+  if (COMP && MODE == kModeRK2b) bytes += full * L::kLo;
+  mbar_expect_tx(bar, bytes);
+  bulk_copy(st.U, static_cast<const rec_t<R>*>(a.U) + c0, cnt * L::kU, bar);
+  bulk_copy(st.geom, static_cast<const rec_t<R>*>(a.geom) + 2 * c0, full * L::kGeom, bar);
+  bulk_copy(st.nbr, static_cast<const unsigned char*>(a.nbr) + c0 * L::kNbr, full * L::kNbr, bar);
+  if (MODE == kModeRK2b)
+    bulk_copy(st.base, static_cast<const rec_t<R>*>(a.Ubase) + c0, cnt * L::kU, bar);
+  if (COMP) bulk_copy(st.lo, a.lo + c0, full * L::kLo, bar);
+  if (COMP && MODE == kModeRK2b) bulk_copy(st.lo_stage, a.lo_stage + c0, full * L::kLo, bar);
+}
+
+template <typename R, int MODE, bool COMP>
+__global__ void __launch_bounds__(kBlock) k_step_tma(StepArgs a) {
+  using Stage = TileStage<R, MODE, COMP>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  Stage* stages = reinterpret_cast<Stage*>(smem_raw);
+  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ int abort_flag;
+  const rec_t<R>* __restrict__ U = static_cast<const rec_t<R>*>(a.U);
+  rec_t<R>* out = static_cast<rec_t<R>*>(a.out);
+  const int tid = threadIdx.x;
+  const int64_t ntiles = (a.n + kTile - 1) / kTile;
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    abort_flag = 0;
+  }
+  __syncthreads();
+  double t = 0.0, dt = 0.0;
+  dt = step_dt(a, t);
+  const R dtR = R(dt);
+  R bmin = R(INFINITY);
+  bool ok = true;
+  auto tile_count = [&](int64_t tt) {
+    const int64_t rem = a.n - tt * kTile;
+    return (unsigned)(rem < kTile ? rem : kTile);
+  };
+  // prologue: the first two tiles of this block
+  int64_t tile = blockIdx.x;
+  if (tid == 0) {
+    for (int s = 0; s < 2; ++s) {
+      const int64_t tt = tile + (int64_t)s * gridDim.x;
+      if (tt < ntiles) issue_tile<R, MODE, COMP>(a, stages[s], &bars[s], tt, tile_count(tt));
+    }
+  }
+  unsigned phase[2] = {0u, 0u};
+  int issued_not_waited[2] = {0, 0};
+  for (int s = 0; s < 2; ++s) issued_not_waited[s] = (tile + (int64_t)s * gridDim.x) < ntiles;
+  for (int k = 0; tile < ntiles; ++k, tile += gridDim.x) {
+    const int s = k & 1;
+    Stage& st = stages[s];
+    // every thread waits for the stage (bounded)
+    const bool arrived = mbar_wait(&bars[s], phase[s], a.wait_limit);
+    if (!arrived) atomicExch(&abort_flag, 1);
+    __syncthreads();
+    if (abort_flag) break;
+    phase[s] ^= 1u;
+    issued_not_waited[s] = 0;
+    const int64_t i = tile * kTile + tid;
+    if (i < a.n) {
+      CellIn<R> c;
+      c.g0 = st.geom[2 * tid];
+      c.g1 = st.geom[2 * tid + 1];
+      if constexpr (sizeof(R) == 8) {
+        const int4 nb = reinterpret_cast<const int4*>(st.nbr)[tid];
+        c.n0 = nb.x, c.n1 = nb.y, c.n2 = nb.z;
+      } else {
+        const int2 nb = reinterpret_cast<const int2*>(st.nbr)[tid];
+        c.n0 = __float_as_int(c.g1.w), c.n1 = nb.x, c.n2 = nb.y;
+      }
+      c.U = st.U[tid];
+      if (MODE == kModeRK2b) c.base = st.base[tid];
+      if (COMP) c.lo = st.lo[tid];
+      if (COMP && MODE == kModeRK2b) c.lo_stage = st.lo_stage[tid];
+      const Prim<R> L = primitive<R>(c.U);
+      R acc[4] = {R(0), R(0), R(0), R(0)};
+      const int nb[3] = {c.n0, c.n1, c.n2};
+      const R nx[3] = {c.g0.x, c.g0.z, c.g1.x};
+      const R ny[3] = {c.g0.y, c.g0.w, c.g1.y};
+      const int64_t t0 = tile * kTile;
+      R perim = R(0);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        rec_t<R> UR;
+        if (nb[q] >= 0) {
+          const int64_t local = (int64_t)nb[q] - t0;
+          UR = (local >= 0 && local < kTile && (int64_t)nb[q] < a.n) ? st.U[local]
+                                                                      : Rec<R>::ld(U + nb[q]);
+        } else {
+          UR = ghost<R>(nb[q], c.U, nx[q], ny[q], a.uinf);
+        }
+        const Prim<R> W = primitive<R>(UR);
+        const R len = face_len<R>(nx[q], ny[q]);
+        face_flux_acc<R, false>(c.U, L, UR, W, nx[q], ny[q], len, R(1), acc);
+        perim = q == 0 ? len : add(perim, len);
+      }
+      finish_cell<R, MODE, COMP>(a, out, i, c, acc, perim, dtR, bmin, ok);
+    }
+    __syncthreads();  // the stage is free again
+    if (tid == 0) {
+      const int64_t nt = tile + 2 * (int64_t)gridDim.x;
+      if (nt < ntiles) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue_tile<R, MODE, COMP>(a, st, &bars[s], nt, tile_count(nt));
+        issued_not_waited[s] = 1;
+      }
+    }
+  }
+  if (abort_flag) {
+    // record the timeout, then drain this block's copies still in flight
+    if (tid == 0) {
+      atomicOr(a.err, 2);
+      for (int s = 0; s < 2; ++s)
+        if (issued_not_waited[s]) mbar_wait(&bars[s], phase[s], a.drain_limit);
+    }
+    __syncthreads();
+    return;
+  }
+  if (MODE == kModeFE || MODE == kModeRK2b) {
+    if (!ok) atomicOr(a.err, 1);
+    const double m = (double)block_min<R>(bmin);
+    if (tid == 0) {
+      atomicMin(a.bmin_write, (unsigned long long)__double_as_longlong(m));
+      if (blockIdx.x == 0) {
+        *a.t_write = t + dt;
+        *a.bmin_reset = kInfBits;
+      }
+    }
+  }
+}
+
+template <typename R, int MODE, bool COMP>
+cudaError_t launch_tma_t(const StepArgs& a, cudaStream_t s) {
+  auto kernel = k_step_tma<R, MODE, COMP>;
+  const size_t smem = 2 * sizeof(TileStage<R, MODE, COMP>);
+  static int cap = 0;
+  if (cap == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, smem) !=
+            cudaSuccess ||
+        per_sm < 1)
+      return cudaErrorInvalidConfiguration;
+    cap = sms * per_sm;
+  }
+  const int64_t ntiles = a.n > 0 ? (a.n + kTile - 1) / kTile : 1;
+  const unsigned g = (unsigned)(ntiles < cap ? ntiles : cap);
+  kernel<<<g, kBlock, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_step_tma(bool f64, int mode, const StepArgs& a, cudaStream_t s) {
+  const bool comp = !f64 && a.lo != nullptr;
+#define FV_TMA_CASES(R, C)                                               \
+  switch (mode) {                                                        \
+    case kModeFE: return launch_tma_t<R, kModeFE, C>(a, s);              \
+    case kModeRK2a: return launch_tma_t<R, kModeRK2a, C>(a, s);          \
+    case kModeRK2b: return launch_tma_t<R, kModeRK2b, C>(a, s);          \
+    default: return cudaErrorInvalidValue;                               \
+  }
+  if (f64) {
+    FV_TMA_CASES(double, false)
+  } else if (comp) {
+    FV_TMA_CASES(float, true)
+  } else {
+    FV_TMA_CASES(float, false)
+  }
+#undef FV_TMA_CASES
+}
+
+}  // namespace fv

@@ -214,7 +214,7 @@ def test_kernel_shapes_give_identical_results(big_square, prec, scheme):
     mi, U0 = big_square
     dt_ = torch.float64 if prec == "f64" else torch.float32
     outs, ts = [], []
-    for v in range(5):
+    for v in range(6):
         g = B.Mesh.from_input(mi, prec)
         g.renumber("hilbert")
         g.set_variant(v)
@@ -222,7 +222,7 @@ def test_kernel_shapes_give_identical_results(big_square, prec, scheme):
         ts.append(g.step(U, 30, 0.4, scheme=scheme))
         outs.append(U)
         g.close()
-    for v in range(1, 5):
+    for v in range(1, 6):
         assert ts[v] == ts[0]
         assert torch.equal(outs[v], outs[0]), v
 
@@ -233,11 +233,35 @@ def test_autotune_picks_a_shape_and_leaves_state(big_square):
     U = dev(U0, torch.float32)
     before = U.clone()
     best, us = g.autotune(U)
-    assert 0 <= best < 5 and len(us) == 5 and all(x > 0 for x in us)
+    assert 0 <= best < 6 and len(us) == 6 and all(x > 0 for x in us)
     assert us[best] == min(us)
     assert torch.equal(U, before)
     with pytest.raises(B.FVError):
         g.set_variant(7)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_bounded_wait_gives_timeout_not_a_hang(big_square, prec):
+    # the TMA-staged shape waits for its bulk copies on mbarriers with a poll
+    # limit; a limit of 0 makes every wait give up at once: the kernel drains
+    # its own copies, sets the timeout bit and returns, and the call reports
+    # FV_ETIMEOUT
+    mi, U0 = big_square
+    dt_ = torch.float64 if prec == "f64" else torch.float32
+    g = B.Mesh.from_input(mi, prec)
+    g.set_variant(5)
+    g.set_wait_limit(0)
+    U = dev(U0, dt_)
+    with pytest.raises(B.FVError) as e:
+        g.step(U, 3, 0.4)
+    assert e.value.code == B.FV_ETIMEOUT
+    # the mesh and the device stay usable
+    g.set_wait_limit(1 << 24)
+    V = dev(U0, dt_)
+    ref = B.Mesh.from_input(mi, prec)
+    W_ = dev(U0, dt_)
+    assert g.step(V, 5, 0.4) == ref.step(W_, 5, 0.4)
+    assert torch.equal(V, W_)
 
 
 def test_conservation_and_free_stream_on_gpu(c1):

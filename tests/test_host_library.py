@@ -87,7 +87,7 @@ def test_malformed_meshes_are_rejected():
     assert e.n == 0 and e.diagnostics() == (0, 0)
 
 
-@pytest.mark.parametrize("order", ["identity", "shuffle", "rcm", "hilbert"])
+@pytest.mark.parametrize("order", ["identity", "shuffle", "rcm", "hilbert", "am1"])
 def test_renumber_is_consistent_permutation(orc, order):
     mi = W.channel_bump(30, 12, seed=8)
     m = B.Mesh.from_input(mi, "f32")
@@ -162,3 +162,32 @@ def test_freestream_validation():
     with pytest.raises(B.FVError):
         m.set_freestream(-1.0, 0.0, 0.0, 1.0)
     m.set_freestream(1.0, 0.5, 0.0, 1.0)
+
+
+def test_am1_matches_rcm_quality_on_degree_three_meshes():
+    # Sec. 4.2: on the cell graphs of 2D triangulations (degree <= 3) AM1 gives
+    # serial bandwidths close to GPS; here against RCM from the same kind of
+    # pseudo-peripheral start
+    for mi in (W.channel_bump(120, 40, seed=1), W.periodic_square(64, 40, seed=2)):
+        m = B.Mesh.from_input(mi, "f32")
+        m.renumber("shuffle", seed=3)
+        b0, s0 = m.diagnostics()
+        m.renumber("rcm")
+        b_rcm, s_rcm = m.diagnostics()
+        m.renumber("shuffle", seed=4)
+        m.renumber("am1")
+        b_am1, s_am1 = m.diagnostics()
+        assert s_am1 < s0 / 10 and s_am1 <= 1.25 * s_rcm and b_am1 <= 1.25 * b_rcm
+
+
+def test_am1_on_a_path_has_bandwidth_one():
+    nx = 40
+    xy = np.array([[i, j] for j in range(2) for i in range(nx + 1)], np.float64)
+    tri = []
+    for i in range(nx):
+        a, b, c, d = i, i + 1, nx + 2 + i, nx + 1 + i
+        tri += [[a, b, c], [a, c, d]]
+    m = B.Mesh(xy, tri, default_bc=1)
+    m.renumber("shuffle", seed=4)
+    m.renumber("am1")
+    assert m.diagnostics() == (1, 2)
