@@ -53,7 +53,7 @@ def parse_args():
                    choices=["channel_bump_1m", "square_16m", "vortex_square_small"])
     p.add_argument("--precision", default="f32", choices=["f32", "f64"])
     p.add_argument("--scheme", default="fe", choices=["fe", "rk2"])
-    p.add_argument("--order", default=None, choices=["identity", "shuffle", "rcm", "hilbert"])
+    p.add_argument("--order", default=None, choices=["identity", "shuffle", "rcm", "hilbert", "am1"])
     p.add_argument("--time-steps", type=int, default=None, help="time steps per benchmark step")
     p.add_argument("--no-extras", action="store_true", help="skip FP64 / 16M / CPU / e2e legs")
     p.add_argument("--variant", type=int, default=None,
@@ -274,6 +274,7 @@ def run_ours(args):
     achieved = ALGO_BYTES[prec] * n / avg_launch / 1e9  # GB/s of one step-kernel launch
     kbytes = ALGO_BYTES[prec] + (COMP_BYTES if prec == "f32" else 0)
     U_final = U.double().cpu().numpy()
+    e2e = e2e_leg(args, m, U0p, n, S, dist)
     out = {
         "metric": "cell updates/s",
         "value": value,
@@ -303,6 +304,7 @@ def run_ours(args):
                                f"{'compensated' if prec == 'f32' else 'plain'}, "
                                f"variant {tune['variant']}>",
                      "traffic": profiled_traffic(f"step_{prec}_{args.workload}.md")},
+        "e2e": e2e,
         "gpu_launches": args.steps * (S * stages + 4),
         "clocks": clk.summary(),
     }
@@ -313,6 +315,45 @@ def run_ours(args):
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def e2e_leg(args, m, U0p, n, S, dist=None):
+    """The same metric end to end through the public API: every step copies
+    the state in from pinned host memory, steps, reads the totals and copies
+    the state back."""
+    import torch
+    tdt = torch.float32 if args.precision == "f32" else torch.float64
+    host_in = torch.tensor(U0p, dtype=tdt).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    Ud = torch.empty(host_in.shape, dtype=tdt, device="cuda")
+    times = []
+    for it in range(2):
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        Ud.copy_(host_in, non_blocking=True)
+        m.step(Ud, S, 0.4, scheme=args.scheme, sync=False)
+        tot = m.totals(Ud)
+        host_out.copy_(Ud, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        if it > 0:
+            times.append(e0.elapsed_time(e1) / 1e3)
+    assert np.isfinite(tot).all()
+    t = statistics.mean(times)
+    world = 1
+    if dist is not None:
+        world = dist.get_world_size()
+        tt = torch.tensor([t], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    nb = host_in.numel() * host_in.element_size()
+    return {"value": world * n * S / t, "unit": "cell-updates/s",
+            "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb + 32,
+            "api": "fv_step + fv_conserved_totals on host-copied state"}
 
 
 def extras(args, B, spec, mi, U0, U0p, perm, m32, S, U32_final, out):
@@ -334,30 +375,6 @@ def extras(args, B, spec, mi, U0, U0p, perm, m32, S, U32_final, out):
                        "fp32_rel_l2_rho_vs_fp64": err, "tolerance": 1e-5}
         del U, U0d
         m64.close()
-    # ---- end to end through the public API with host buffers
-    tdt = torch.float32 if args.precision == "f32" else torch.float64
-    host_in = torch.tensor(U0p, dtype=tdt).pin_memory()
-    host_out = torch.empty_like(host_in).pin_memory()
-    Ud = torch.empty(host_in.shape, dtype=tdt, device="cuda")
-    times = []
-    for it in range(2):
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        Ud.copy_(host_in, non_blocking=True)
-        m32.step(Ud, S, 0.4, scheme=args.scheme, sync=False)
-        tot = m32.totals(Ud)
-        host_out.copy_(Ud, non_blocking=True)
-        e1.record()
-        torch.cuda.synchronize()
-        if it > 0:
-            times.append(e0.elapsed_time(e1) / 1e3)
-    nb = host_in.numel() * host_in.element_size()
-    out["e2e"] = {"value": n * S / statistics.mean(times), "unit": "cell-updates/s",
-                  "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb + 32,
-                  "api": "fv_step + fv_conserved_totals on host-copied state"}
-    assert np.isfinite(tot).all()
     # ---- the HBM-bound headline: 16.8M cells
     if args.workload != "square_16m":
         spec16 = WORKLOADS["square_16m"]
@@ -388,6 +405,8 @@ def extras(args, B, spec, mi, U0, U0p, perm, m32, S, U32_final, out):
     out["batched"] = batched_leg(B)
     # ---- learned dissipation scale: cost per step on the 250k-cell coarse channel
     out["learned"] = learned_leg(B)
+    # ---- the paper's own case: Mach 3 forward-facing step to t = 4
+    out["forward_step"] = forward_step_leg(B)
     # ---- FP64 CPU oracle on one host core, bounded sample of this workload
     out["cpu_baseline"] = cpu_baseline(spec, mi, U0, budget_s=12.0)
 
@@ -432,6 +451,37 @@ def batched_leg(B, time_steps=1000):
            "launches_per_step": time_steps + 4}
     batch.close()
     return res
+
+
+def forward_step_leg(B, t_end=4.0):
+    """Mach 3 over a forward-facing step (Sec. 7.1) on a 410k-triangle mesh
+    refined 12.5x toward the corner: wall time to simulate t_end, FP32."""
+    import torch
+    mi = W.forward_step_394k()
+    prim = W.mach3_inflow()
+    m = B.Mesh.from_input(mi, "f32")
+    m.set_freestream(*prim)
+    perm = m.renumber("rcm")
+    U0 = torch.tensor(W.uniform_state(mi.n_tri, prim)[perm], dtype=torch.float32, device="cuda")
+    U = U0.clone()
+    choose_variant(m, U0, None)
+    m.step(U, 200, 0.4)  # warm-up (graph capture)
+    U.copy_(U0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    t, steps = 0.0, 0
+    while t < t_end - 1e-12:
+        dt = m.compute_dt(U, 0.4)
+        n = int(math.ceil((t_end - t) / (0.9 * dt))) + 2
+        t += m.step(U, n, 0.4, t_stop=t_end - t)
+        steps += n
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    rho = U[:, 0].double()
+    return {"cells": mi.n_tri, "t_end": t, "steps_launched": steps, "wall_s": wall,
+            "value": mi.n_tri * steps / wall, "unit": "cell-updates/s", "dtype": "f32",
+            "rho_max_over_inflow": float(rho.max()) / prim[0],
+            "rho_min_over_inflow": float(rho.min()) / prim[0]}
 
 
 def learned_leg(B, time_steps=2000):

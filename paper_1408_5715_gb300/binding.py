@@ -88,6 +88,7 @@ def load():
             "fv_batch_destroy": (ctypes.c_int, [_vp]),
             "fv_batch_info": (ctypes.c_int, [_vp, _P(_i64), _vp]),
             "fv_batch_set_compensation": (ctypes.c_int, [_vp, _i32]),
+            "fv_batch_set_variant": (ctypes.c_int, [_vp, _i32]),
             "fv_batch_step": (ctypes.c_int, [_vp, _vp, _i64, _dbl, _dbl, _i32, _vp, _vp]),
             "fv_batch_totals": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
         }
@@ -393,6 +394,9 @@ class Batch:
 
     def set_compensation(self, enable: bool):
         _check(load().fv_batch_set_compensation(self._h, int(bool(enable))))
+
+    def set_variant(self, variant: int):
+        _check(load().fv_batch_set_variant(self._h, int(variant)))
 
     def step(self, U, nsteps, cfl, t_stop=0.0, scheme="fe", stream=None, sync=True):
         """Advances the flattened CUDA state U in place; returns each mesh's

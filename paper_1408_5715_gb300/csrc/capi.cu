@@ -651,6 +651,7 @@ struct fv_batch {
   std::vector<double> vol;
   std::vector<double> uinf;          // 4 per mesh (conserved)
   bool compensated = true;
+  int variant = 5;                   // 0: one thread per cell; 5: TMA-staged tiles
   // device
   int device = -1;
   bool uploaded = false;
@@ -759,6 +760,11 @@ void batch_ensure_device(fv_batch* b, cudaStream_t s) {
   b->uploaded = true;
 }
 
+cudaError_t batch_launch(const fv_batch* b, int mode, const fv::BatchArgs& a, cudaStream_t s) {
+  if (b->variant == 5) return fv::launch_batch_step_tma(b->f64(), mode, a, s);
+  return fv::launch_batch_step(b->f64(), mode, a, b->n_blocks(), s);
+}
+
 void batch_enqueue_steps(fv_batch* b, void* U, int64_t j0, int64_t count, double cfl,
                          double t_stop, int32_t scheme, cudaStream_t s) {
   for (int64_t j = j0; j < j0 + count; ++j) {
@@ -769,6 +775,8 @@ void batch_enqueue_steps(fv_batch* b, void* U, int64_t j0, int64_t count, double
     a.s.cfl = cfl;
     a.s.t_stop = t_stop;
     a.s.err = b->d_err;
+    a.s.wait_limit = fv::kDefaultWaitLimit;
+    a.s.drain_limit = fv::kDefaultWaitLimit;
     if (b->use_lo()) {
       a.s.lo = b->d_lo;
       a.s.lo_stage = b->d_lo_stage;
@@ -788,15 +796,15 @@ void batch_enqueue_steps(fv_batch* b, void* U, int64_t j0, int64_t count, double
       const bool even = (j % 2) == 0;
       a.s.U = even ? U : b->d_work;
       a.s.out = even ? b->d_work : U;
-      FV_CUDA(fv::launch_batch_step(b->f64(), fv::kModeFE, a, b->n_blocks(), s));
+      FV_CUDA(batch_launch(b, fv::kModeFE, a, s));
     } else {
       a.s.U = U;
       a.s.out = b->d_work;
-      FV_CUDA(fv::launch_batch_step(b->f64(), fv::kModeRK2a, a, b->n_blocks(), s));
+      FV_CUDA(batch_launch(b, fv::kModeRK2a, a, s));
       a.s.U = b->d_work;
       a.s.Ubase = U;
       a.s.out = U;
-      FV_CUDA(fv::launch_batch_step(b->f64(), fv::kModeRK2b, a, b->n_blocks(), s));
+      FV_CUDA(batch_launch(b, fv::kModeRK2b, a, s));
     }
   }
 }
@@ -887,6 +895,15 @@ int fv_batch_info(const fv_batch* batch, int64_t* n_cells_padded, int64_t* offse
     if (n_cells_padded) *n_cells_padded = batch->n;
     if (offsets)
       std::memcpy(offsets, batch->offsets.data(), batch->offsets.size() * sizeof(int64_t));
+  });
+}
+
+int fv_batch_set_variant(fv_batch* batch, int32_t variant) {
+  return guarded([&] {
+    check_batch(batch);
+    if (variant != 0 && variant != 5) invalid("batch kernel shape must be 0 or 5");
+    batch->variant = variant;
+    batch->drop_graph();
   });
 }
 

@@ -124,7 +124,7 @@ __device__ __forceinline__ double batch_step_dt(const BatchArgs& b, int m, doubl
 }
 
 template <typename R, int MODE, bool COMP>
-__global__ void __launch_bounds__(kBlock) k_step_batch(BatchArgs b) {
+__global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 6 : 1) k_step_batch(BatchArgs b) {
   const StepArgs& a = b.s;
   const rec_t<R>* __restrict__ U = static_cast<const rec_t<R>*>(a.U);
   const rec_t<R>* __restrict__ geom = static_cast<const rec_t<R>*>(a.geom);

@@ -127,6 +127,9 @@ constexpr int64_t kPadCells = 256;
 constexpr unsigned kDefaultWaitLimit = 1u << 24;
 
 cudaError_t launch_step_tma(bool f64, int mode, const StepArgs& a, cudaStream_t s);
+// the same for a batch (tiles = the batch's 256-cell blocks); needs the
+// batch's library arrays padded to whole tiles, as fv_batch allocates them
+cudaError_t launch_batch_step_tma(bool f64, int mode, const BatchArgs& b, cudaStream_t s);
 
 // float (FV_F32) or double (FV_F64) instantiations
 cudaError_t launch_step(bool f64, int mode, int variant, const StepArgs& a, cudaStream_t s);

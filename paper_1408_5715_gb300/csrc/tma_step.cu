@@ -113,8 +113,29 @@ __device__ __forceinline__ void issue_tile(const StepArgs& a, TileStage<R, MODE,
   if (COMP && MODE == kModeRK2b) bulk_copy(st.lo_stage, a.lo_stage + c0, full * L::kLo, bar);
 }
 
-template <typename R, int MODE, bool COMP>
-__global__ void __launch_bounds__(kBlock) k_step_tma(StepArgs a) {
+// dt and time of mesh m in a batch (lane 0 of each warp reads, then broadcast)
+__device__ __forceinline__ double tma_batch_dt(const BatchArgs& b, int m, double& t) {
+  double dt = 0.0;
+  t = 0.0;
+  if ((threadIdx.x & 31) == 0) {
+    t = b.t[b.t_read * b.n_meshes + m];
+    const unsigned long long bits = b.bmin[b.slot_read * b.n_meshes + m];
+    dt = b.s.cfl > 0.0 ? b.s.cfl * __longlong_as_double((long long)bits) : -b.s.cfl;
+    if (b.s.t_stop > 0.0) {
+      const double rem = b.s.t_stop - t;
+      if (rem < dt) dt = rem;
+      if (!(dt > 0.0)) dt = 0.0;
+    }
+  }
+  t = __shfl_sync(0xffffffffu, t, 0);
+  return __shfl_sync(0xffffffffu, dt, 0);
+}
+
+// BATCH: the tiles are the 256-cell blocks of a batch; each tile uses its
+// mesh's dt, time, free stream and CFL-minimum slot (see BatchArgs).
+template <typename R, int MODE, bool COMP, bool BATCH>
+__global__ void __launch_bounds__(kBlock) k_step_tma(BatchArgs b) {
+  const StepArgs& a = b.s;
   using Stage = TileStage<R, MODE, COMP>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   Stage* stages = reinterpret_cast<Stage*>(smem_raw);
@@ -132,8 +153,7 @@ __global__ void __launch_bounds__(kBlock) k_step_tma(StepArgs a) {
   }
   __syncthreads();
   double t = 0.0, dt = 0.0;
-  dt = step_dt(a, t);
-  const R dtR = R(dt);
+  if (!BATCH) dt = step_dt(a, t);
   R bmin = R(INFINITY);
   bool ok = true;
   auto tile_count = [&](int64_t tt) {
@@ -162,7 +182,18 @@ __global__ void __launch_bounds__(kBlock) k_step_tma(StepArgs a) {
     phase[s] ^= 1u;
     issued_not_waited[s] = 0;
     const int64_t i = tile * kTile + tid;
-    if (i < a.n) {
+    int m = 0;
+    int64_t end = a.n;
+    const double* uinf = a.uinf;
+    if (BATCH) {
+      m = __ldg(b.block_mesh + tile);
+      end = __ldg(b.mesh_end + m);
+      uinf = b.uinf + 4 * m;
+      dt = tma_batch_dt(b, m, t);
+      bmin = R(INFINITY);
+    }
+    const R dtR = R(dt);
+    if (i < end) {
       CellIn<R> c;
       c.g0 = st.geom[2 * tid];
       c.g1 = st.geom[2 * tid + 1];
@@ -189,10 +220,10 @@ __global__ void __launch_bounds__(kBlock) k_step_tma(StepArgs a) {
         rec_t<R> UR;
         if (nb[q] >= 0) {
           const int64_t local = (int64_t)nb[q] - t0;
-          UR = (local >= 0 && local < kTile && (int64_t)nb[q] < a.n) ? st.U[local]
+          UR = (local >= 0 && local < kTile && (int64_t)nb[q] < end) ? st.U[local]
                                                                       : Rec<R>::ld(U + nb[q]);
         } else {
-          UR = ghost<R>(nb[q], c.U, nx[q], ny[q], a.uinf);
+          UR = ghost<R>(nb[q], c.U, nx[q], ny[q], uinf);
         }
         const Prim<R> W = primitive<R>(UR);
         const R len = face_len<R>(nx[q], ny[q]);
@@ -200,6 +231,18 @@ __global__ void __launch_bounds__(kBlock) k_step_tma(StepArgs a) {
         perim = q == 0 ? len : add(perim, len);
       }
       finish_cell<R, MODE, COMP>(a, out, i, c, acc, perim, dtR, bmin, ok);
+    }
+    if (BATCH && (MODE == kModeFE || MODE == kModeRK2b)) {
+      // this tile's mesh: its minimum, and (first tile of the mesh) its time
+      const double mn = (double)block_min<R>(bmin);
+      if (tid == 0) {
+        atomicMin(&b.bmin[b.slot_write * b.n_meshes + m],
+                  (unsigned long long)__double_as_longlong(mn));
+        if (tile == 0 || __ldg(b.block_mesh + tile - 1) != m) {
+          b.t[b.t_write * b.n_meshes + m] = t + dt;
+          b.bmin[b.slot_reset * b.n_meshes + m] = kInfBits;
+        }
+      }
     }
     __syncthreads();  // the stage is free again
     if (tid == 0) {
@@ -223,20 +266,23 @@ __global__ void __launch_bounds__(kBlock) k_step_tma(StepArgs a) {
   }
   if (MODE == kModeFE || MODE == kModeRK2b) {
     if (!ok) atomicOr(a.err, 1);
-    const double m = (double)block_min<R>(bmin);
-    if (tid == 0) {
-      atomicMin(a.bmin_write, (unsigned long long)__double_as_longlong(m));
-      if (blockIdx.x == 0) {
-        *a.t_write = t + dt;
-        *a.bmin_reset = kInfBits;
+    if (!BATCH) {
+      const double mn = (double)block_min<R>(bmin);
+      if (tid == 0) {
+        atomicMin(a.bmin_write, (unsigned long long)__double_as_longlong(mn));
+        if (blockIdx.x == 0) {
+          *a.t_write = t + dt;
+          *a.bmin_reset = kInfBits;
+        }
       }
     }
   }
 }
 
-template <typename R, int MODE, bool COMP>
-cudaError_t launch_tma_t(const StepArgs& a, cudaStream_t s) {
-  auto kernel = k_step_tma<R, MODE, COMP>;
+template <typename R, int MODE, bool COMP, bool BATCH>
+cudaError_t launch_tma_t(const BatchArgs& ba, cudaStream_t s) {
+  const StepArgs& a = ba.s;
+  auto kernel = k_step_tma<R, MODE, COMP, BATCH>;
   const size_t smem = 2 * sizeof(TileStage<R, MODE, COMP>);
   static int cap = 0;
   if (cap == 0) {
@@ -254,20 +300,21 @@ cudaError_t launch_tma_t(const StepArgs& a, cudaStream_t s) {
   }
   const int64_t ntiles = a.n > 0 ? (a.n + kTile - 1) / kTile : 1;
   const unsigned g = (unsigned)(ntiles < cap ? ntiles : cap);
-  kernel<<<g, kBlock, smem, s>>>(a);
+  kernel<<<g, kBlock, smem, s>>>(ba);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_step_tma(bool f64, int mode, const StepArgs& a, cudaStream_t s) {
-  const bool comp = !f64 && a.lo != nullptr;
-#define FV_TMA_CASES(R, C)                                               \
-  switch (mode) {                                                        \
-    case kModeFE: return launch_tma_t<R, kModeFE, C>(a, s);              \
-    case kModeRK2a: return launch_tma_t<R, kModeRK2a, C>(a, s);          \
-    case kModeRK2b: return launch_tma_t<R, kModeRK2b, C>(a, s);          \
-    default: return cudaErrorInvalidValue;                               \
+template <bool BATCH>
+cudaError_t launch_tma_any(bool f64, int mode, const BatchArgs& b, cudaStream_t s) {
+  const bool comp = !f64 && b.s.lo != nullptr;
+#define FV_TMA_CASES(R, C)                                                   \
+  switch (mode) {                                                            \
+    case kModeFE: return launch_tma_t<R, kModeFE, C, BATCH>(b, s);           \
+    case kModeRK2a: return launch_tma_t<R, kModeRK2a, C, BATCH>(b, s);       \
+    case kModeRK2b: return launch_tma_t<R, kModeRK2b, C, BATCH>(b, s);       \
+    default: return cudaErrorInvalidValue;                                   \
   }
   if (f64) {
     FV_TMA_CASES(double, false)
@@ -277,6 +324,16 @@ cudaError_t launch_step_tma(bool f64, int mode, const StepArgs& a, cudaStream_t 
     FV_TMA_CASES(float, false)
   }
 #undef FV_TMA_CASES
+}
+
+cudaError_t launch_step_tma(bool f64, int mode, const StepArgs& a, cudaStream_t s) {
+  BatchArgs b{};
+  b.s = a;
+  return launch_tma_any<false>(f64, mode, b, s);
+}
+
+cudaError_t launch_batch_step_tma(bool f64, int mode, const BatchArgs& b, cudaStream_t s) {
+  return launch_tma_any<true>(f64, mode, b, s);
 }
 
 }  // namespace fv

@@ -344,3 +344,92 @@ def refine_midpoint(mi: MeshInput, levels: int = 2):
                      None if bnd is None else bnd.astype(np.int32), mi.default_bc,
                      dict(mi.info, refined=levels))
     return fine, parent
+
+
+def _graded_toward(n: int, lo: float, hi: float, at_hi: bool, ratio: float) -> np.ndarray:
+    """n+1 points on [lo, hi] whose spacing shrinks geometrically by `ratio`
+    toward one end (the hi end if at_hi)."""
+    if n < 1:
+        raise ValueError("need at least one interval")
+    q = ratio ** (1.0 / max(n - 1, 1))  # growth factor between neighbouring intervals
+    w = q ** np.arange(n)
+    w = w[::-1] if at_hi else w  # large intervals away from the refined end
+    x = lo + (hi - lo) * np.concatenate([[0.0], np.cumsum(w)]) / w.sum()
+    x[0], x[-1] = lo, hi
+    return x
+
+
+def forward_step(nx1: int, nx2: int, ny1: int, ny2: int, seed: int, jitter: float = 0.2,
+                 length: float = 3.0, height: float = 1.0, step_x: float = 0.6,
+                 step_h: float = 0.2, corner_refine: float = 12.5) -> MeshInput:
+    """Channel [0, length] x [0, height] with a forward-facing step occupying
+    x > step_x, y < step_h (these dimensions are this generator's choice).
+    Grid lines run through the step corner; the spacing shrinks toward the
+    corner by `corner_refine` (Sec. 7.1 refines the characteristic length
+    near the corner by 12.5).  Interior nodes are jittered.  Tags: inflow at
+    x = 0 far field (2), outflow at x = length extrapolation (3), all walls
+    slip (1)."""
+    rng = np.random.default_rng(seed)
+    xs = np.concatenate([_graded_toward(nx1, 0.0, step_x, True, corner_refine),
+                         _graded_toward(nx2, step_x, length, False, corner_refine)[1:]])
+    ys = np.concatenate([_graded_toward(ny1, 0.0, step_h, True, corner_refine),
+                         _graded_toward(ny2, step_h, height, False, corner_refine)[1:]])
+    nx, ny = nx1 + nx2, ny1 + ny2
+    dx = np.diff(xs)
+    hx = np.minimum(np.concatenate([[dx[0]], dx]), np.concatenate([dx, [dx[-1]]]))
+    dy = np.diff(ys)
+    hy = np.minimum(np.concatenate([[dy[0]], dy]), np.concatenate([dy, [dy[-1]]]))
+    X, Y = np.meshgrid(xs, ys, indexing="xy")  # (ny+1, nx+1)
+    ii, jj = np.meshgrid(np.arange(nx + 1), np.arange(ny + 1), indexing="xy")
+    # nodes on a boundary (outer walls, inflow, outflow, step faces) stay put
+    on_bnd = (ii == 0) | (ii == nx) | (jj == 0) | (jj == ny) | \
+             ((ii == nx1) & (jj <= ny1)) | ((jj == ny1) & (ii >= nx1))
+    inside_step = (ii > nx1) & (jj < ny1)
+    move = ~on_bnd & ~inside_step
+    X = np.where(move, X + rng.uniform(-jitter, jitter, X.shape) * hx[None, :], X)
+    Y = np.where(move, Y + rng.uniform(-jitter, jitter, Y.shape) * hy[:, None], Y)
+    node_id = lambda i, j: j * (nx + 1) + i  # noqa: E731
+    coin = rng.integers(0, 2, size=nx * ny)
+    tri = _quad_split(nx, ny, node_id, coin).reshape(ny, nx, 2, 3)
+    qi, qj = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
+    keep = ~((qi >= nx1) & (qj < ny1))  # quads inside the step are removed
+    tri = tri[keep].reshape(-1, 3)
+    xy = np.stack([X, Y], -1).reshape(-1, 2).astype(np.float64)
+    segs = []
+
+    def add(i0, j0, i1, j1, tag):
+        if i0 == i1:
+            j = np.arange(min(j0, j1), max(j0, j1))
+            segs.append(np.stack([node_id(i0, j), node_id(i0, j + 1), np.full(j.size, tag)], -1))
+        else:
+            i = np.arange(min(i0, i1), max(i0, i1))
+            segs.append(np.stack([node_id(i, j0), node_id(i + 1, j0), np.full(i.size, tag)], -1))
+
+    add(0, 0, 0, ny, TAG_FARFIELD)          # inflow
+    add(nx, ny1, nx, ny, TAG_EXTRAP)        # outflow
+    add(0, 0, nx1, 0, TAG_WALL)             # floor before the step
+    add(nx1, 0, nx1, ny1, TAG_WALL)         # step face
+    add(nx1, ny1, nx, ny1, TAG_WALL)        # step top
+    add(0, ny, nx, ny, TAG_WALL)            # ceiling
+    bnd = np.concatenate(segs).astype(np.int32)
+    # drop nodes no triangle uses (the inside of the step)
+    used = np.unique(tri)
+    remap = -np.ones(xy.shape[0], np.int64)
+    remap[used] = np.arange(used.size)
+    tri = remap[tri].astype(np.int32)
+    bnd[:, :2] = remap[bnd[:, :2]]
+    xy = xy[used]
+    assert _signed_areas(xy, tri).min() > 0.0
+    return MeshInput(xy, tri, canon=None, bnd=bnd, default_bc=0,
+                     info=dict(kind="forward_step", nx1=nx1, nx2=nx2, ny1=ny1, ny2=ny2, seed=seed,
+                               step_x=step_x, step_h=step_h, corner_refine=corner_refine))
+
+
+def forward_step_394k(seed: int = 7) -> MeshInput:
+    """About 394,000 triangles, the size of the paper's largest step mesh."""
+    return forward_step(120, 420, 90, 360, seed)
+
+
+def mach3_inflow() -> tuple:
+    """Primitive inflow state of the forward-facing step: Mach 3 with c = 1."""
+    return freestream(3.0, rho=GAMMA, p=1.0)

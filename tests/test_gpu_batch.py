@@ -40,7 +40,7 @@ def make_set(seed, n_meshes=7):
     return items
 
 
-def solo_and_batch(items, prec, nsteps, scheme, t_stop=0.0, comp=True):
+def solo_and_batch(items, prec, nsteps, scheme, t_stop=0.0, comp=True, variant=5):
     dt_ = torch.float64 if prec == "f64" else torch.float32
     meshes, solo = [], []
     for mi, prim, U0 in items:
@@ -60,6 +60,7 @@ def solo_and_batch(items, prec, nsteps, scheme, t_stop=0.0, comp=True):
         t = m.step(U, nsteps, 0.4, t_stop=t_stop, scheme=scheme)
         solo.append((U.cpu().numpy(), t, m.totals(U)))
     batch = B.Batch(meshes)
+    batch.set_variant(variant)
     if prec == "f32":
         batch.set_compensation(comp)
     flat = torch.tensor(batch.pack([U0[p] for (mi, prim, U0), p in zip(items, perms)]),
@@ -70,9 +71,10 @@ def solo_and_batch(items, prec, nsteps, scheme, t_stop=0.0, comp=True):
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 @pytest.mark.parametrize("scheme", ["fe", "rk2"])
-def test_batch_equals_solo_bitwise(prec, scheme):
+@pytest.mark.parametrize("variant", [5, 0])
+def test_batch_equals_solo_bitwise(prec, scheme, variant):
     items = make_set(5)
-    solo, batch, flat, tb = solo_and_batch(items, prec, 131, scheme)
+    solo, batch, flat, tb = solo_and_batch(items, prec, 131, scheme, variant=variant)
     got = batch.unpack(flat.cpu().numpy())
     tot = batch.totals(flat)
     for k, (Us, ts, Ts) in enumerate(solo):
