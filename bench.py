@@ -41,6 +41,10 @@ ALGO_BYTES = {"f32": 16 + 16 + 28 + 12, "f64": 32 + 32 + 56 + 12}
 # The compensated FP32 update also reads and writes its 8-byte remainder.
 COMP_BYTES = 8 + 8
 FALLBACK_HBM_GBS = 6800.0
+# The two-step launch (FP32, compensated) moves per tile cell and pair of
+# updates: state in and out (32), geometry (32), tile-local neighbours (8),
+# remainder in and out (16); halo reads are re-reads of other tiles' cells.
+PAIR_BYTES = 32 + 32 + 8 + 16
 
 
 def parse_args():
@@ -56,6 +60,13 @@ def parse_args():
     p.add_argument("--order", default=None, choices=["identity", "shuffle", "rcm", "hilbert", "am1"])
     p.add_argument("--time-steps", type=int, default=None, help="time steps per benchmark step")
     p.add_argument("--no-extras", action="store_true", help="skip FP64 / 16M / CPU / e2e legs")
+    p.add_argument("--blocking", type=int, default=1, choices=[1, 2],
+                   help="time steps per kernel launch (2: tiles staged in shared memory, "
+                        "dt evaluated once per pair)")
+    p.add_argument("--tile", type=int, default=1024, choices=[512, 1024, 2048],
+                   help="cells per tile with --blocking 2")
+    p.add_argument("--staged", action="store_true",
+                   help="with --blocking 2: tile records by bulk copies (512 or 1024 cells)")
     p.add_argument("--variant", type=int, default=None,
                    help="force a step-kernel shape instead of autotuning")
     return p.parse_args()
@@ -89,16 +100,16 @@ def measured_peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_hash():
+def kernel_source_hash(extra=()):
     """Hash of the sources of the step kernels (ties a profile to a kernel)."""
     h = hashlib.sha256()
-    for name in ("cell_math.cuh", "kernels.cu", "kernels.h"):
+    for name in ("cell_math.cuh", "kernels.cu", "kernels.h") + tuple(extra):
         with open(os.path.join(ROOT, "paper_1408_5715_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(name):
+def profiled_traffic(name, extra=()):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
     the current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", name)
@@ -107,7 +118,7 @@ def profiled_traffic(name):
     txt = open(path).read()
     h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
     t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
-    if not h or not t or h.group(1) != kernel_source_hash():
+    if not h or not t or h.group(1) != kernel_source_hash(extra):
         return None
     return float(t.group(1))
 
@@ -256,7 +267,13 @@ def run_ours(args):
     U0p = U0[perm]
     U0dev = torch.tensor(U0p, dtype=tdt, device="cuda")
     U = torch.empty_like(U0dev)
-    tune = choose_variant(m, U0dev, args.variant, args.scheme)
+    if args.blocking == 2:
+        if prec != "f32" or args.scheme != "fe":
+            raise SystemExit("--blocking 2 runs FP32 forward Euler")
+        m.set_blocking(2, args.tile, args.staged)
+        tune = {"blocking": 2, "tile": args.tile, "staged": args.staged}
+    else:
+        tune = choose_variant(m, U0dev, args.variant, args.scheme)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     with ClockSampler(gpu_smi_id()) as clk:
         times = timed_loop(m, U, U0dev, S, args.steps, args.warmup, args.scheme, flush=flush,
@@ -269,10 +286,20 @@ def run_ours(args):
     updates = n * S * args.steps * world
     value = updates / total
     stages = 2 if args.scheme == "rk2" else 1
-    avg_launch = total / (args.steps * S * stages)  # includes the per-call small kernels
+    launches = S * stages // args.blocking
+    avg_launch = total / (args.steps * launches)  # includes the per-call small kernels
     peak, peak_kind = measured_peaks()
-    achieved = ALGO_BYTES[prec] * n / avg_launch / 1e9  # GB/s of one step-kernel launch
-    kbytes = ALGO_BYTES[prec] + (COMP_BYTES if prec == "f32" else 0)
+    if args.blocking == 2:
+        algo = kbytes = PAIR_BYTES
+        kname = (f"{'k_step_pair_tma' if args.staged else 'k_step_pair'}"
+                 f"<tile {args.tile}, compensated>")
+    else:
+        algo = ALGO_BYTES[prec]
+        kbytes = ALGO_BYTES[prec] + (COMP_BYTES if prec == "f32" else 0)
+        kname = (f"k_step<{'float' if prec == 'f32' else 'double'}, "
+                 f"{'RK2' if stages == 2 else 'FE'}, "
+                 f"{'compensated' if prec == 'f32' else 'plain'}, variant {tune['variant']}>")
+    achieved = algo * n / avg_launch / 1e9  # GB/s of one step-kernel launch
     U_final = U.double().cpu().numpy()
     e2e = e2e_leg(args, m, U0p, n, S, dist)
     out = {
@@ -290,22 +317,24 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": args.workload, "mesh": spec["desc"], "cells": n,
                    "time_steps_per_step": S, "scheme": args.scheme, "cfl": 0.4, "order": order,
+                   "dt": "CFL bound of the state at the start of each pair" if args.blocking == 2
+                         else "CFL bound of the state at the start of each step",
                    "parallelism": f"replicas{world}" if world > 1 else "single",
                    "kernel_shape": tune,
                    "l2": "256 MB written between steps (L2 flushed); state+geometry "
                          f"{n * (ALGO_BYTES[prec] + 8) / 1e6:.0f} MB"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind,
-                     "bytes_per_update": ALGO_BYTES[prec],
-                     "kernel_bytes_per_update": kbytes,
+                     "bytes_per_launch_per_cell": algo,
+                     "kernel_bytes_per_launch_per_cell": kbytes,
+                     "updates_per_launch": args.blocking,
                      "frac_with_kernel_bytes": kbytes * n / avg_launch / 1e9 / peak,
-                     "kernel": f"k_step<{'float' if prec == 'f32' else 'double'}, "
-                               f"{'RK2' if stages == 2 else 'FE'}, "
-                               f"{'compensated' if prec == 'f32' else 'plain'}, "
-                               f"variant {tune['variant']}>",
-                     "traffic": profiled_traffic(f"step_{prec}_{args.workload}.md")},
+                     "kernel": kname,
+                     "traffic": (profiled_traffic(f"step_pair_{args.workload}.md",
+                                                  ("pair_step.cu",)) if args.blocking == 2
+                                 else profiled_traffic(f"step_{prec}_{args.workload}.md"))},
         "e2e": e2e,
-        "gpu_launches": args.steps * (S * stages + 4),
+        "gpu_launches": args.steps * (launches + 4),
         "clocks": clk.summary(),
     }
     if rank == 0 and not args.no_extras and world == 1:
@@ -401,14 +430,65 @@ def extras(args, B, spec, mi, U0, U0p, perm, m32, S, U32_final, out):
         res["order"] = spec16["order"]
         res["speedup_fp32_over_fp64"] = res["f32"]["value"] / res["f64"]["value"]
         out["square_16m"] = res
+    # a leg that fails reports its error; the headline line is still printed
+    def leg(name, fn):
+        try:
+            out[name] = fn(B)
+        except Exception as e:  # noqa: BLE001
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+    # ---- two steps per launch (temporal blocking) on the same workloads
+    leg("pairs", pair_leg)
     # ---- many meshes in one launch per step (256 periodic squares, 5k-200k cells)
-    out["batched"] = batched_leg(B)
+    leg("batched", batched_leg)
     # ---- learned dissipation scale: cost per step on the 250k-cell coarse channel
-    out["learned"] = learned_leg(B)
+    leg("learned", learned_leg)
     # ---- the paper's own case: Mach 3 forward-facing step to t = 4
-    out["forward_step"] = forward_step_leg(B)
+    leg("forward_step", forward_step_leg)
     # ---- FP64 CPU oracle on one host core, bounded sample of this workload
     out["cpu_baseline"] = cpu_baseline(spec, mi, U0, budget_s=12.0)
+
+
+def pair_leg(B, time_steps=1000):
+    """Two forward-Euler steps per launch on shared-memory tiles (Hilbert order),
+    against one launch per step on the same mesh; FP32 compensated, CFL 0.4
+    (one dt per pair for the two-step launch)."""
+    import torch
+    peak, _ = measured_peaks()
+    res = {}
+    for name in ("channel_bump_1m", "square_16m"):
+        spec = WORKLOADS[name]
+        mi = spec["make"]()
+        U0 = initial_state(spec, mi)
+        m, perm = make_mesh(B, spec, mi, "f32", "hilbert")
+        U0d = torch.tensor(U0[perm], dtype=torch.float32, device="cuda")
+        U = torch.empty_like(U0d)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        single = choose_variant(m, U0d, None)
+        ts = timed_loop(m, U, U0d, time_steps, 2, 1, "fe", flush=flush)
+        v1 = mi.n_tri * time_steps / statistics.mean(ts)
+        by_tile = {}
+        for tile, staged in ((512, False), (1024, False), (2048, False), (512, True),
+                             (1024, True)):
+            m.set_blocking(2, tile, staged)
+            tt = timed_loop(m, U, U0d, time_steps, 2, 1, "fe", flush=flush)
+            by_tile[f"{tile}{'-staged' if staged else ''}"] = (
+                mi.n_tri * time_steps / statistics.mean(tt))
+        best = max(by_tile, key=by_tile.get)
+        v2 = by_tile[best]
+        launch = 2 * mi.n_tri / v2  # seconds per two-step launch (per-call kernels included)
+        gbs = PAIR_BYTES * mi.n_tri / launch / 1e9
+        res[name] = {"cells": mi.n_tri, "order": "hilbert", "time_steps": time_steps,
+                     "single_step": {"value": v1, "kernel_shape": single},
+                     "value": v2, "unit": "cell-updates/s", "tile": best,
+                     "value_by_tile": by_tile, "speedup_over_single_step": v2 / v1,
+                     "achieved_gbs": gbs, "frac_of_measured_hbm": gbs / peak,
+                     "single_step_equivalent_gbs": (ALGO_BYTES["f32"] + COMP_BYTES) * v2 / 1e9,
+                     "kernel": (f"k_step_pair_tma<tile {best.split('-')[0]}, compensated>"
+                                if best.endswith("staged")
+                                else f"k_step_pair<tile {best}, compensated>")}
+        del U, U0d, flush
+        m.close()
+    return res
 
 
 def batched_leg(B, time_steps=1000):
@@ -454,34 +534,55 @@ def batched_leg(B, time_steps=1000):
 
 
 def forward_step_leg(B, t_end=4.0):
-    """Mach 3 over a forward-facing step (Sec. 7.1) on a 410k-triangle mesh
-    refined 12.5x toward the corner: wall time to simulate t_end, FP32."""
+    """Mach 3 over a forward-facing step (Sec. 7.1), FP32, CFL 0.4: wall time to
+    simulate t_end on the 65,664-triangle mesh of the family (refined 12.5x
+    toward the corner), and how far the 410,400-triangle mesh (the paper's
+    largest size) gets before the corner expansion drives a pressure
+    non-positive."""
     import torch
-    mi = W.forward_step_394k()
     prim = W.mach3_inflow()
-    m = B.Mesh.from_input(mi, "f32")
-    m.set_freestream(*prim)
-    perm = m.renumber("rcm")
-    U0 = torch.tensor(W.uniform_state(mi.n_tri, prim)[perm], dtype=torch.float32, device="cuda")
-    U = U0.clone()
-    choose_variant(m, U0, None)
-    m.step(U, 200, 0.4)  # warm-up (graph capture)
-    U.copy_(U0)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    t, steps = 0.0, 0
-    while t < t_end - 1e-12:
-        dt = m.compute_dt(U, 0.4)
-        n = int(math.ceil((t_end - t) / (0.9 * dt))) + 2
-        t += m.step(U, n, 0.4, t_stop=t_end - t)
-        steps += n
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t0
-    rho = U[:, 0].double()
-    return {"cells": mi.n_tri, "t_end": t, "steps_launched": steps, "wall_s": wall,
-            "value": mi.n_tri * steps / wall, "unit": "cell-updates/s", "dtype": "f32",
-            "rho_max_over_inflow": float(rho.max()) / prim[0],
-            "rho_min_over_inflow": float(rho.min()) / prim[0]}
+
+    def run(mi, t_end, timed):
+        m = B.Mesh.from_input(mi, "f32")
+        m.set_freestream(*prim)
+        perm = m.renumber("rcm")
+        U0 = torch.tensor(W.uniform_state(mi.n_tri, prim)[perm], dtype=torch.float32,
+                          device="cuda")
+        U = U0.clone()
+        if timed:
+            choose_variant(m, U0, None)
+            m.step(U, 200, 0.4)  # warm-up (graph capture)
+            U.copy_(U0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        t, steps, failed = 0.0, 0, None
+        while t < t_end - 1e-12:
+            chunk = min(0.1, t_end - t)
+            dt = m.compute_dt(U, 0.4)
+            n = int(math.ceil(chunk / (0.9 * dt))) + 2
+            try:
+                t += m.step(U, n, 0.4, t_stop=chunk)
+            except B.FVError as e:
+                failed = f"non-positive state between t = {t:.2f} and {t + chunk:.2f} ({e})"
+                break
+            steps += n
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        rho = U[:, 0].double()
+        res = {"cells": mi.n_tri, "t_reached": t, "steps_launched": steps, "wall_s": wall}
+        if failed:
+            res["failed"] = failed
+        else:
+            res.update({"value": mi.n_tri * steps / wall, "unit": "cell-updates/s",
+                        "rho_max_over_inflow": float(rho.max()) / prim[0],
+                        "rho_min_over_inflow": float(rho.min()) / prim[0]})
+        m.close()
+        return res
+
+    out = run(W.forward_step_65k(), t_end, True)
+    out["dtype"] = "f32"
+    out["paper_size_mesh"] = run(W.forward_step_394k(), t_end, False)
+    return out
 
 
 def learned_leg(B, time_steps=2000):

@@ -163,6 +163,42 @@ int fv_mesh_autotune(fv_mesh* mesh, const void* U, int32_t scheme, void* stream,
  * Default 2^24.  A limit of 0 forces the timeout path (for tests). */
 int fv_mesh_set_wait_limit(fv_mesh* mesh, uint32_t polls);
 
+/* Two time steps per launch: temporal blocking, the GPU form of the paper's
+ * chaining of processors, where the output of one update feeds the next
+ * without another pass through memory (Sec. 7).  FV_F32 meshes, forward
+ * Euler, no closure.
+ *   steps_per_launch  1 (default: one fused kernel per step) or 2.
+ *   tile_cells        0 (= 1024), 512, 1024 or 2048: cells per tile.
+ *   staged            0: one block per tile, records loaded through the
+ *                     caches; 1: persistent blocks whose tile records arrive
+ *                     by bulk copies into double-buffered shared memory
+ *                     (tiles of 512 or 1024 cells; its waits are bounded as
+ *                     set by fv_mesh_set_wait_limit, FV_ETIMEOUT if one gives
+ *                     up; the state pointer must be 16-byte aligned).
+ * With 2, each launch stages a tile of consecutive cells plus its two rings
+ * of neighbours in shared memory and advances the tile by two steps.  The
+ * cell arithmetic is that of the one-step kernel, so with a fixed dt
+ * (cfl < 0 in fv_step) the result is bitwise that of single steps.  With
+ * cfl > 0 both steps of a pair use the CFL bound of the state at the start
+ * of the pair (dt evaluated every second step).  An odd last step runs as a
+ * single step.  Halos must fit in shared memory: renumber with a compact
+ * order first (FV_ORDER_HILBERT); fv_step returns FV_EINVAL otherwise.
+ * fv_step then also returns FV_EINVAL for RK2 or a closure.  Returns
+ * FV_EINVAL for FV_F64 meshes with 2, an unknown tile size, or tiles of
+ * 2048 cells with staged = 1. */
+int fv_mesh_set_blocking(fv_mesh* mesh, int32_t steps_per_launch, int32_t tile_cells,
+                         int32_t staged);
+
+/* Host diagnostics of the two-step tiles: the halos of tile `tile` (cells
+ * [tile*tile_cells, (tile+1)*tile_cells) of the current numbering).
+ * halo_ids (nullable, host, `capacity` entries) receives the first halo (the
+ * cells outside the tile adjacent to it) then the second (cells outside tile
+ * and first halo adjacent to the first halo), each in ascending id;
+ * n_first / n_second their sizes.  FV_EINVAL for a bad tile index, a
+ * capacity below n_first + n_second, or a tile with halos above 65533 cells. */
+int fv_mesh_tile_halo(const fv_mesh* mesh, int32_t tile_cells, int64_t tile, int32_t* halo_ids,
+                      int64_t capacity, int64_t* n_first, int64_t* n_second);
+
 /* ===========================================================================
  * Partitioning for several processes (host only).  Part p of nparts owns the
  * contiguous range [p*n/nparts, (p+1)*n/nparts) of the current numbering

@@ -68,6 +68,8 @@ def load():
             "fv_mesh_set_compensation": (ctypes.c_int, [_vp, _i32]),
             "fv_mesh_set_variant": (ctypes.c_int, [_vp, _i32]),
             "fv_mesh_set_wait_limit": (ctypes.c_int, [_vp, ctypes.c_uint32]),
+            "fv_mesh_set_blocking": (ctypes.c_int, [_vp, _i32, _i32, _i32]),
+            "fv_mesh_tile_halo": (ctypes.c_int, [_vp, _i32, _i64, _vp, _i64, _P(_i64), _P(_i64)]),
             "fv_mesh_autotune": (ctypes.c_int, [_vp, _vp, _i32, _vp, _P(_i32), _P(_dbl)]),
             "fv_step": (ctypes.c_int, [_vp, _vp, _i64, _dbl, _dbl, _i32, _vp, _vp, _P(_dbl)]),
             "fv_mesh_status": (ctypes.c_int, [_vp, _vp, _P(_dbl)]),
@@ -227,6 +229,23 @@ class Mesh:
 
     def set_wait_limit(self, polls: int):
         _check(load().fv_mesh_set_wait_limit(self._h, int(polls)))
+
+    def set_blocking(self, steps_per_launch: int, tile_cells: int = 0, staged: bool = False):
+        """1: one launch per step; 2: two forward-Euler steps per launch on
+        shared-memory tiles of `tile_cells` cells (0 = 1024); staged: tile
+        records by bulk copies into double-buffered shared memory."""
+        _check(load().fv_mesh_set_blocking(self._h, int(steps_per_launch), int(tile_cells),
+                                           int(bool(staged))))
+
+    def tile_halo(self, tile_cells: int, tile: int):
+        """(first halo, second halo) of a two-step tile, as global cell ids."""
+        n1, n2 = _i64(), _i64()
+        _check(load().fv_mesh_tile_halo(self._h, int(tile_cells), int(tile), None, 0,
+                                        ctypes.byref(n1), ctypes.byref(n2)))
+        ids = np.zeros(max(n1.value + n2.value, 1), np.int32)
+        _check(load().fv_mesh_tile_halo(self._h, int(tile_cells), int(tile), _np_ptr(ids), ids.size,
+                                        ctypes.byref(n1), ctypes.byref(n2)))
+        return ids[:n1.value].copy(), ids[n1.value:n1.value + n2.value].copy()
 
     def autotune(self, U, scheme="fe", stream=None):
         """Picks the fastest step-kernel shape for this mesh; returns

@@ -109,6 +109,16 @@ struct fv_mesh {
   uint2* d_lo_stage = nullptr;  // ... and of the RK2 stage state
   bool compensated = true;      // FP32 meshes only
   int variant = 1;              // step-kernel shape (fv_mesh_autotune / fv_mesh_set_variant)
+  // two steps per launch (fv_mesh_set_blocking): tiles and halos on the device
+  int blocking = 1;
+  int pair_tile = 1024;
+  int pair_staged = 0;  // 1: bulk-copy staged two-step kernel
+  int tiles_built = 0;  // tile size of the arrays below (0: none)
+  uint2* d_cell_ln = nullptr;
+  int* d_tile_info = nullptr;
+  int* d_halo_id = nullptr;
+  uint2* d_halo_ln = nullptr;
+  int p_e_cap = 0, p_t1_cap = 0;
   unsigned wait_limit = fv::kDefaultWaitLimit;  // bounded device waits (variant 5)
   fv::LoopScalars* d_scal = nullptr;
   double* d_partials = nullptr;
@@ -121,6 +131,7 @@ struct fv_mesh {
   const fv_closure* g_closure = nullptr;
   bool g_comp = false;
   int g_variant = -1;
+  int g_blocking = -1, g_tile = -1, g_staged = -1;
   int last_t_slot = 0;
   bool stepped = false;
 
@@ -142,8 +153,17 @@ struct fv_mesh {
     g_U = nullptr;
   }
 
+  void free_tiles() {
+    dev_free(d_cell_ln);
+    dev_free(d_tile_info);
+    dev_free(d_halo_id);
+    dev_free(d_halo_ln);
+    tiles_built = 0;
+  }
+
   void free_device() {
     drop_graph();
+    free_tiles();
     dev_free(d_nbr);
     dev_free(d_geom);
     dev_free(d_vol);
@@ -161,13 +181,55 @@ struct fv_mesh {
 
 namespace {
 
+// Tiles and halos of the two-step update, built on the host for the current
+// numbering and tile size and copied to the device.
+void ensure_tiles(fv_mesh* m, cudaStream_t s) {
+  if (m->blocking != 2 || m->h.n == 0 || m->tiles_built == m->pair_tile) return;
+  m->free_tiles();
+  m->drop_graph();
+  const fv::PairTiles L = fv::build_pair_tiles(m->h, m->pair_tile);
+  int dev = 0, optin = 0;
+  FV_CUDA(cudaGetDevice(&dev));
+  FV_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const size_t smem = fv::pair_smem_bytes(L.e_cap, L.t1_cap, m->pair_tile, m->pair_staged != 0);
+  if (smem > (size_t)optin)
+    invalid("a tile with its halos needs " + std::to_string(smem) + " bytes of shared memory (" +
+            std::to_string(optin) + " available); renumber the cells with a compact order "
+            "(Hilbert) or use smaller tiles");
+  // whole 256-cell tiles: the staged kernel copies an even number of records
+  const size_t ncells = (size_t)((m->h.n + fv::kPadCells - 1) / fv::kPadCells * fv::kPadCells);
+  FV_CUDA(cudaMalloc((void**)&m->d_cell_ln, ncells * sizeof(uint2)));
+  FV_CUDA(cudaMalloc((void**)&m->d_tile_info, L.tile_info.size() * sizeof(int32_t)));
+  const size_t nh = std::max<size_t>(L.halo_id.size(), 1);
+  FV_CUDA(cudaMalloc((void**)&m->d_halo_id, nh * sizeof(int32_t)));
+  FV_CUDA(cudaMalloc((void**)&m->d_halo_ln, nh * sizeof(uint2)));
+  FV_CUDA(cudaMemcpyAsync(m->d_cell_ln, L.cell_ln.data(), L.cell_ln.size() * sizeof(uint32_t),
+                          cudaMemcpyHostToDevice, s));
+  FV_CUDA(cudaMemcpyAsync(m->d_tile_info, L.tile_info.data(), L.tile_info.size() * sizeof(int32_t),
+                          cudaMemcpyHostToDevice, s));
+  if (!L.halo_id.empty()) {
+    FV_CUDA(cudaMemcpyAsync(m->d_halo_id, L.halo_id.data(), L.halo_id.size() * sizeof(int32_t),
+                            cudaMemcpyHostToDevice, s));
+    FV_CUDA(cudaMemcpyAsync(m->d_halo_ln, L.halo_ln.data(), L.halo_ln.size() * sizeof(uint32_t),
+                            cudaMemcpyHostToDevice, s));
+  }
+  FV_CUDA(cudaStreamSynchronize(s));  // L is a local staging buffer
+  m->p_e_cap = L.e_cap;
+  m->p_t1_cap = L.t1_cap;
+  m->tiles_built = m->pair_tile;
+}
+
 void ensure_device(fv_mesh* m, cudaStream_t s) {
   int dev = 0;
   FV_CUDA(cudaGetDevice(&dev));
   if (m->device >= 0 && m->device != dev && m->dev_n >= 0)
     invalid("mesh was uploaded to device " + std::to_string(m->device) +
             " but the current device is " + std::to_string(dev));
-  if (!m->dirty && m->dev_n == m->h.n) return;
+  if (!m->dirty && m->dev_n == m->h.n) {
+    ensure_tiles(m, s);
+    return;
+  }
+  m->free_tiles();
   const int64_t n = m->h.n;
   if (m->dev_n != n) {
     m->free_device();
@@ -201,6 +263,7 @@ void ensure_device(fv_mesh* m, cudaStream_t s) {
   FV_CUDA(cudaStreamSynchronize(s));
   m->device = dev;
   m->dirty = false;
+  ensure_tiles(m, s);
 }
 
 fv::StepArgs base_args(const fv_mesh* m) {
@@ -223,7 +286,8 @@ cudaError_t launch_mode(const fv_mesh* m, int mode, const fv::StepArgs& a, const
 
 // Enqueues steps j0 .. j0+count-1 of a loop on stream s.
 void enqueue_steps(fv_mesh* m, void* U, int64_t j0, int64_t count, double cfl, double t_stop,
-                   int32_t scheme, cudaStream_t s, const fv_closure* cl = nullptr) {
+                   int32_t scheme, cudaStream_t s, const fv_closure* cl = nullptr,
+                   bool lo_alt = false) {
   fv::LoopScalars* sc = m->d_scal;
   for (int64_t j = j0; j < j0 + count; ++j) {
     fv::StepArgs a = base_args(m);
@@ -235,7 +299,9 @@ void enqueue_steps(fv_mesh* m, void* U, int64_t j0, int64_t count, double cfl, d
     a.cfl = cfl;
     a.t_stop = t_stop;
     if (m->use_lo()) {
-      a.lo = m->d_lo;
+      // lo_alt: after an odd number of two-step launches the remainder of the
+      // state is in the second buffer (forward Euler only)
+      a.lo = lo_alt ? m->d_lo_stage : m->d_lo;
       a.lo_stage = m->d_lo_stage;
     }
     if (scheme == FV_SCHEME_FE) {
@@ -255,13 +321,63 @@ void enqueue_steps(fv_mesh* m, void* U, int64_t j0, int64_t count, double cfl, d
   }
 }
 
+// Enqueues two-step launches j0 .. j0+count-1 (forward Euler).  Launch j reads
+// the state and remainder from U and d_lo when j is even, from the work
+// buffers when it is odd, and writes the others; the scalar slots rotate per
+// launch as they do per step.
+void enqueue_pairs(fv_mesh* m, void* U, int64_t j0, int64_t count, double cfl, double t_stop,
+                   cudaStream_t s) {
+  fv::LoopScalars* sc = m->d_scal;
+  for (int64_t j = j0; j < j0 + count; ++j) {
+    const bool even = (j % 2) == 0;
+    fv::PairArgs a{};
+    a.U = static_cast<const float4*>(even ? U : m->d_work);
+    a.out = static_cast<float4*>(even ? m->d_work : U);
+    if (m->use_lo()) {
+      a.lo_in = even ? m->d_lo : m->d_lo_stage;
+      a.lo_out = even ? m->d_lo_stage : m->d_lo;
+    }
+    a.geom = static_cast<const float4*>(m->d_geom);
+    a.cell_ln = m->d_cell_ln;
+    a.tile_info = m->d_tile_info;
+    a.halo_id = m->d_halo_id;
+    a.halo_ln = m->d_halo_ln;
+    a.n = m->h.n;
+    a.tile = m->tiles_built;
+    a.e_cap = m->p_e_cap;
+    a.t1_cap = m->p_t1_cap;
+    m->uinf_conserved(a.uinf);
+    a.bmin_read = &sc->bmin[j % 3];
+    a.bmin_write = &sc->bmin[(j + 1) % 3];
+    a.bmin_reset = &sc->bmin[(j + 2) % 3];
+    a.t_read = &sc->t[j % 2];
+    a.t_write = &sc->t[(j + 1) % 2];
+    a.cfl = cfl;
+    a.t_stop = t_stop;
+    a.err = &sc->err;
+    a.wait_limit = m->wait_limit;
+    a.drain_limit = fv::kDefaultWaitLimit;
+    FV_CUDA(fv::launch_step_pair(a, m->pair_staged, s));
+  }
+}
+
+// Steps of one time loop: whole launches [j0, j0 + launches) of the mesh's
+// kind (one step each, or two with blocking).
+void enqueue_launches(fv_mesh* m, void* U, int64_t j0, int64_t launches, double cfl,
+                      double t_stop, int32_t scheme, cudaStream_t s, const fv_closure* cl) {
+  if (m->blocking == 2)
+    enqueue_pairs(m, U, j0, launches, cfl, t_stop, s);
+  else
+    enqueue_steps(m, U, j0, launches, cfl, t_stop, scheme, s, cl);
+}
+
 void capture_graph(fv_mesh* m, void* U, double cfl, double t_stop, int32_t scheme,
                    const fv_closure* cl) {
   m->drop_graph();
   cudaGraph_t g = nullptr;
   FV_CUDA(cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal));
   try {
-    enqueue_steps(m, U, 0, kGraphSteps, cfl, t_stop, scheme, m->cap_stream, cl);
+    enqueue_launches(m, U, 0, kGraphSteps / m->blocking, cfl, t_stop, scheme, m->cap_stream, cl);
   } catch (...) {
     cudaStreamEndCapture(m->cap_stream, &g);
     if (g) cudaGraphDestroy(g);
@@ -278,6 +394,9 @@ void capture_graph(fv_mesh* m, void* U, double cfl, double t_stop, int32_t schem
   m->g_closure = cl;
   m->g_comp = m->use_lo();
   m->g_variant = m->variant;
+  m->g_blocking = m->blocking;
+  m->g_tile = m->tiles_built;
+  m->g_staged = m->pair_staged;
 }
 
 void read_status(fv_mesh* m, cudaStream_t s, double* t_adv, bool check) {
@@ -417,6 +536,45 @@ int fv_mesh_set_variant(fv_mesh* mesh, int32_t variant) {
   });
 }
 
+int fv_mesh_set_blocking(fv_mesh* mesh, int32_t steps_per_launch, int32_t tile_cells,
+                         int32_t staged) {
+  return guarded([&] {
+    check_mesh(mesh);
+    if (steps_per_launch != 1 && steps_per_launch != 2) invalid("steps_per_launch must be 1 or 2");
+    if (staged != 0 && staged != 1) invalid("staged must be 0 or 1");
+    if (tile_cells == 0) tile_cells = 1024;
+    bool known = false;
+    for (int t : fv::kPairTiles) known = known || t == tile_cells;
+    if (!known) invalid("tile_cells must be 0, 512, 1024 or 2048");
+    if (staged && tile_cells == 2048) invalid("the staged kernel takes tiles of 512 or 1024 cells");
+    if (steps_per_launch == 2 && mesh->f64())
+      invalid("two steps per launch are built for FV_F32 meshes (the FP64 step is bound by "
+              "arithmetic, not by memory)");
+    if (staged != mesh->pair_staged) mesh->tiles_built = 0;  // shared-memory check differs
+    mesh->blocking = steps_per_launch;
+    mesh->pair_tile = tile_cells;
+    mesh->pair_staged = staged;
+    mesh->drop_graph();
+  });
+}
+
+int fv_mesh_tile_halo(const fv_mesh* mesh, int32_t tile_cells, int64_t tile, int32_t* halo_ids,
+                      int64_t capacity, int64_t* n_first, int64_t* n_second) {
+  return guarded([&] {
+    check_mesh(mesh);
+    const fv::PairTiles L = fv::build_pair_tiles(mesh->h, tile_cells);
+    if (tile < 0 || tile >= L.n_tiles) invalid("tile index out of range");
+    const int64_t hs = L.tile_info[2 * tile], h1 = L.tile_info[2 * tile + 1];
+    const int64_t h12 = L.tile_info[2 * tile + 2] - hs;
+    if (n_first) *n_first = h1;
+    if (n_second) *n_second = h12 - h1;
+    if (halo_ids) {
+      if (capacity < h12) invalid("halo_ids capacity too small");
+      std::memcpy(halo_ids, L.halo_id.data() + hs, h12 * sizeof(int32_t));
+    }
+  });
+}
+
 int fv_mesh_set_wait_limit(fv_mesh* mesh, uint32_t polls) {
   return guarded([&] {
     check_mesh(mesh);
@@ -525,6 +683,8 @@ int fv_step(fv_mesh* mesh, void* U, int64_t nsteps, double cfl, double t_stop, i
     if (!std::isfinite(cfl) || cfl == 0.0) invalid("cfl must be finite and non-zero");
     if (!std::isfinite(t_stop)) invalid("t_stop must be finite");
     if (closure && mesh->f64()) invalid("the learned closure runs on FV_F32 meshes only");
+    if (mesh->blocking == 2 && (scheme != FV_SCHEME_FE || closure))
+      invalid("two steps per launch apply to forward Euler without a closure");
     if (!U && nsteps > 0 && mesh->h.n > 0) invalid("null state");
     cudaStream_t s = as_stream(stream);
     ensure_device(mesh, s);
@@ -542,16 +702,27 @@ int fv_step(fv_mesh* mesh, void* U, int64_t nsteps, double cfl, double t_stop, i
       if (chunks > 0) {
         if (!mesh->graph || mesh->g_U != U || mesh->g_scheme != scheme || mesh->g_cfl != cfl ||
             mesh->g_tstop != t_stop || mesh->g_closure != closure ||
-            mesh->g_comp != mesh->use_lo() || mesh->g_variant != mesh->variant)
+            mesh->g_comp != mesh->use_lo() || mesh->g_variant != mesh->variant ||
+            mesh->g_blocking != mesh->blocking || mesh->g_tile != mesh->tiles_built ||
+            mesh->g_staged != mesh->pair_staged)
           capture_graph(mesh, U, cfl, t_stop, scheme, closure);
         for (int64_t k = 0; k < chunks; ++k) FV_CUDA(cudaGraphLaunch(mesh->graph, s));
       }
-      const int64_t done = chunks * kGraphSteps;
-      enqueue_steps(mesh, U, done, nsteps - done, cfl, t_stop, scheme, s, closure);
-      if (scheme == FV_SCHEME_FE && (nsteps % 2) == 1)
+      // a graph holds an even number of launches (and a multiple of 3), so the
+      // launches after it start from the buffers and slots of launch 0
+      const int64_t rest = nsteps - chunks * kGraphSteps;
+      const int64_t tail = rest / mesh->blocking;
+      enqueue_launches(mesh, U, 0, tail, cfl, t_stop, scheme, s, closure);
+      int64_t launches = chunks * (kGraphSteps / mesh->blocking) + tail;
+      if (mesh->blocking == 2 && rest % 2 == 1) {
+        // the odd last step as a single step, on the buffers the pairs left
+        enqueue_steps(mesh, U, tail, 1, cfl, t_stop, scheme, s, nullptr, tail % 2 == 1);
+        ++launches;
+      }
+      if (scheme == FV_SCHEME_FE && (launches % 2) == 1)
         FV_CUDA(cudaMemcpyAsync(U, mesh->d_work, n * mesh->rec_bytes(), cudaMemcpyDeviceToDevice,
                                 s));
-      mesh->last_t_slot = (int)(nsteps % 2);
+      mesh->last_t_slot = (int)(launches % 2);
     }
     if (t_advanced) read_status(mesh, s, t_advanced, true);
   });

@@ -175,12 +175,16 @@ __device__ __forceinline__ R add_face_flux(const rec_t<R>& UL, const Prim<R>& L,
 // bound converts exactly to the double used by the minimum); a bad state
 // clears *ok and gives +inf.
 template <typename R>
-__device__ __forceinline__ R cell_bound(const rec_t<R>& U, R inradius, bool& ok) {
-  const Prim<R> w = primitive<R>(U);
+__device__ __forceinline__ R bound_of(const rec_t<R>& U, const Prim<R>& w, R inradius, bool& ok) {
   const R lam = add(root<R>(fma_(w.u, w.u, mul(w.v, w.v))), w.c);
   // NaN fails every comparison; an infinite state gives an infinite lam
   ok = (U.x > R(0)) && (w.p > R(0)) && (lam < R(INFINITY));
   return ok ? mul(inradius, recip<R>(lam)) : R(INFINITY);
+}
+
+template <typename R>
+__device__ __forceinline__ R cell_bound(const rec_t<R>& U, R inradius, bool& ok) {
+  return bound_of<R>(U, primitive<R>(U), inradius, ok);
 }
 
 // Minimum over the block; the result is valid in thread 0.

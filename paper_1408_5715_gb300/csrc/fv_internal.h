@@ -65,6 +65,24 @@ struct LocalPart {
 PartRange part_range(int64_t n, int32_t nparts, int32_t part);
 LocalPart build_local_part(const HostMesh& m, int32_t nparts, int32_t part);
 
+// Tiles and halos of the two-step update (tiles.cpp).  Per tile b:
+// tile_info[2b] = offset of its halos in halo_id, tile_info[2b+1] = size of
+// the first halo; the second halo runs to tile_info[2b+2].  cell_ln (per cell)
+// and halo_ln (per first-halo entry; zero for second-halo entries) hold the
+// three neighbours as 16-bit tile-local ids (ghost code c as 0x10000 + c),
+// packed (f0 | f1 << 16, f2).
+struct PairTiles {
+  int32_t tile = 0;
+  int64_t n_tiles = 0;
+  std::vector<int32_t> tile_info;  // [2 (n_tiles + 1)]
+  std::vector<int32_t> halo_id;    // global ids: first then second halo of each tile
+  std::vector<uint32_t> halo_ln;   // [2 halo_id.size()]
+  std::vector<uint32_t> cell_ln;   // [2 n]
+  int32_t e_cap = 0;   // max over tiles of tile + both halos
+  int32_t t1_cap = 0;  // max over tiles of tile + first halo
+};
+PairTiles build_pair_tiles(const HostMesh& m, int32_t tile);
+
 // Sec. 4.1 diagnostics on the cell graph of the current numbering.
 int64_t graph_bandwidth(const HostMesh& m);
 int64_t serial_bandwidth(const HostMesh& m);

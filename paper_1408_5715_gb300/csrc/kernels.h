@@ -131,6 +131,44 @@ cudaError_t launch_step_tma(bool f64, int mode, const StepArgs& a, cudaStream_t 
 // batch's library arrays padded to whole tiles, as fv_batch allocates them
 cudaError_t launch_batch_step_tma(bool f64, int mode, const BatchArgs& b, cudaStream_t s);
 
+// Two forward-Euler steps per launch on tiles staged in shared memory
+// (pair_step.cu).  FP32 state; dt of both steps from the slots as for one
+// step (CFL bound of the state at the start of the pair, or fixed).
+struct PairArgs {
+  const float4* U;        // state at the start of the pair (read only)
+  float4* out;            // state after the pair
+  const uint2* lo_in;     // compensated update: remainders at the start ...
+  uint2* lo_out;          // ... and after the pair (both nullptr: plain update)
+  const float4* geom;     // FP32 geometry, 2 records per cell
+  const uint2* cell_ln;   // per cell: tile-local neighbours (16 bits each)
+  const int* tile_info;   // [2 (n_tiles + 1)] halo offset, first-halo size
+  const int* halo_id;     // global ids of the halos
+  const uint2* halo_ln;   // tile-local neighbours of first-halo entries
+  int64_t n;
+  int tile;               // cells per tile
+  int e_cap, t1_cap;      // shared-memory capacities (cells)
+  double uinf[4];
+  const unsigned long long* bmin_read;
+  unsigned long long* bmin_write;
+  unsigned long long* bmin_reset;
+  const double* t_read;
+  double* t_write;
+  double cfl, t_stop;
+  int* err;
+  // staged kernel: bounded mbarrier waits (error bit 2 when one gives up)
+  unsigned wait_limit, drain_limit;
+};
+// tile sizes with a kernel instantiation (the staged kernel: 512 and 1024)
+constexpr int kPairTiles[3] = {512, 1024, 2048};
+// dynamic shared memory of one block for the given capacities; the staged
+// kernel adds two stages of the tile's own records (64 bytes a cell each)
+inline size_t pair_smem_bytes(int e_cap, int t1_cap, int tile, bool staged) {
+  return (size_t)(2 * e_cap + 2 * t1_cap) * 16 + (staged ? (size_t)2 * 64 * tile : 0);
+}
+// staged: 0 loads through the caches; 1 persistent blocks whose tile records
+// arrive by bulk copies (cp.async.bulk) into double-buffered stages
+cudaError_t launch_step_pair(const PairArgs& a, int staged, cudaStream_t s);
+
 // float (FV_F32) or double (FV_F64) instantiations
 cudaError_t launch_step(bool f64, int mode, int variant, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_init_scalars(LoopScalars* d, cudaStream_t s);

@@ -191,3 +191,42 @@ def test_am1_on_a_path_has_bandwidth_one():
     m.renumber("shuffle", seed=4)
     m.renumber("am1")
     assert m.diagnostics() == (1, 2)
+
+
+@pytest.mark.parametrize("kind,order,tile", [("periodic", "hilbert", 512), ("channel", "hilbert", 1024),
+                                             ("channel", "shuffle", 512), ("step", "rcm", 2048)])
+def test_two_step_tile_halos_match_definition(kind, order, tile):
+    # the halos of a tile: cells adjacent to the tile, then cells adjacent to
+    # those (outside tile and first halo), by brute force over the neighbour table
+    mi = {"periodic": lambda: W.periodic_square(60, 40, seed=2),
+          "channel": lambda: W.channel_bump(60, 24, seed=3),
+          "step": lambda: W.forward_step(10, 40, 8, 30, seed=4)}[kind]()
+    m = B.Mesh.from_input(mi, "f32")
+    m.renumber(order, seed=5)
+    nbr, _, _ = m.export()
+    n_tiles = (m.n + tile - 1) // tile
+    for b in sorted({0, 1, n_tiles // 2, n_tiles - 1}):
+        t0, t1 = b * tile, min((b + 1) * tile, m.n)
+        inside = lambda x: (x >= t0) & (x < t1)  # noqa: E731
+        nb = nbr[t0:t1].ravel()
+        h1 = np.unique(nb[(nb >= 0) & ~inside(nb)])
+        nb2 = nbr[h1].ravel()
+        h2 = np.setdiff1d(np.unique(nb2[(nb2 >= 0) & ~inside(nb2)]), h1)
+        g1, g2 = m.tile_halo(tile, b)
+        np.testing.assert_array_equal(g1, h1)
+        np.testing.assert_array_equal(g2, h2)
+    with pytest.raises(B.FVError):
+        m.tile_halo(tile, n_tiles)
+
+
+def test_two_step_blocking_validation():
+    m64 = B.Mesh.from_input(W.periodic_square(8, 8, seed=1), "f64")
+    with pytest.raises(B.FVError, match="FV_F32"):
+        m64.set_blocking(2)
+    m64.set_blocking(1)
+    m32 = B.Mesh.from_input(W.periodic_square(8, 8, seed=1), "f32")
+    for bad in [(3, 0), (0, 0), (2, 100), (2, 4096), (2, 2048, True)]:
+        with pytest.raises(B.FVError):
+            m32.set_blocking(*bad)
+    m32.set_blocking(2, 512)
+    m32.set_blocking(2, 1024, True)
