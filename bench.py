@@ -100,16 +100,21 @@ def measured_peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_hash(extra=()):
-    """Hash of the sources of the step kernels (ties a profile to a kernel)."""
+KERNEL_SOURCES = ("kernels.h", "cell_math.cuh", "tile_math.cuh", "tma_util.cuh",
+                  "launch_util.cuh", "kernels.cu", "tile_step.cu", "tma_step.cu", "pair_step.cu")
+
+
+def kernel_source_hash():
+    """Hash of the sources of the step kernels (ties a profile to the kernels
+    it measured; any change to them makes the recorded traffic stale)."""
     h = hashlib.sha256()
-    for name in ("cell_math.cuh", "kernels.cu", "kernels.h") + tuple(extra):
+    for name in KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_1408_5715_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(name, extra=()):
+def profiled_traffic(name):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
     the current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", name)
@@ -118,7 +123,7 @@ def profiled_traffic(name, extra=()):
     txt = open(path).read()
     h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
     t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
-    if not h or not t or h.group(1) != kernel_source_hash(extra):
+    if not h or not t or h.group(1) != kernel_source_hash():
         return None
     return float(t.group(1))
 
@@ -330,9 +335,9 @@ def run_ours(args):
                      "updates_per_launch": args.blocking,
                      "frac_with_kernel_bytes": kbytes * n / avg_launch / 1e9 / peak,
                      "kernel": kname,
-                     "traffic": (profiled_traffic(f"step_pair_{args.workload}.md",
-                                                  ("pair_step.cu",)) if args.blocking == 2
-                                 else profiled_traffic(f"step_{prec}_{args.workload}.md"))},
+                     "traffic": profiled_traffic(
+                         f"step_pair_{args.workload}.md" if args.blocking == 2
+                         else f"step_{prec}_{args.workload}.md")},
         "e2e": e2e,
         "gpu_launches": args.steps * (launches + 4),
         "clocks": clk.summary(),
@@ -436,6 +441,9 @@ def extras(args, B, spec, mi, U0, U0p, perm, m32, S, U32_final, out):
             out[name] = fn(B)
         except Exception as e:  # noqa: BLE001
             out[name] = {"error": f"{type(e).__name__}: {e}"}
+    # ---- the same loop with each step launched only after the previous one
+    if args.precision == "f32" and args.blocking == 1:
+        leg("unchained", lambda B_: unchained_leg(m32, U0p, S, args.scheme, out["value"]))
     # ---- two steps per launch (temporal blocking) on the same workloads
     leg("pairs", pair_leg)
     # ---- many meshes in one launch per step (256 periodic squares, 5k-200k cells)
@@ -446,6 +454,21 @@ def extras(args, B, spec, mi, U0, U0p, perm, m32, S, U32_final, out):
     leg("forward_step", forward_step_leg)
     # ---- FP64 CPU oracle on one host core, bounded sample of this workload
     out["cpu_baseline"] = cpu_baseline(spec, mi, U0, budget_s=12.0)
+
+
+def unchained_leg(m, U0p, S, scheme, chained_value):
+    """The main loop without programmatic dependent launch (each step kernel
+    waits for the previous one to finish before it is scheduled)."""
+    import torch
+    U0d = torch.tensor(U0p, dtype=torch.float32, device="cuda")
+    U = torch.empty_like(U0d)
+    m.set_launch_chaining(False)
+    try:
+        tt = timed_loop(m, U, U0d, S, 2, 1, scheme)
+    finally:
+        m.set_launch_chaining(True)
+    v = U0p.shape[0] * S / statistics.mean(tt)
+    return {"value": v, "unit": "cell-updates/s", "chained_over_unchained": chained_value / v}
 
 
 def pair_leg(B, time_steps=1000):

@@ -143,16 +143,22 @@ int fv_mesh_set_compensation(fv_mesh* mesh, int32_t enable);
  * grid of resident blocks that walks the cells and prefetches the next
  * cell's records; 2 the same limited to 64 registers per thread; 3 and 4 one
  * thread per cell limited to 40 and 32 registers; 5 a persistent grid whose
- * cell records are staged in shared memory by bulk (TMA) copies.  All give
- * bitwise identical results; only speed differs.  FV_EINVAL outside 0..5. */
+ * cell records are staged in shared memory by bulk (TMA) copies; 6 tiles of
+ * consecutive cells (the tile size of fv_mesh_set_blocking, default 1024)
+ * whose states and primitive variables, with those of the tile's neighbour
+ * ring, sit in shared memory, so each primitive is formed once per cell (the
+ * tile arrays are built on the host at the next device call; FV_EINVAL from
+ * fv_step if a tile with its ring does not fit in shared memory).  All give
+ * bitwise identical results; only speed differs.  FV_EINVAL outside 0..6. */
 int fv_mesh_set_variant(fv_mesh* mesh, int32_t variant);
 
 /* Times every step-kernel shape on this mesh (a few steps each on a device
  * copy of U with a negligible fixed dt; U itself is not changed), keeps the
  * fastest for later fv_step calls and reports it in *best (nullable);
- * us_per_step (nullable, host, [6]) receives the measured microseconds per
- * step of each shape.  Allocates and frees one state-sized device buffer and
- * synchronises the stream.  us_per_step has one entry per shape (6). */
+ * us_per_step (nullable, host, [7]) receives the measured microseconds per
+ * step of each shape (infinity for shape 6 when its tiles do not fit).
+ * Allocates and frees one state-sized device buffer and synchronises the
+ * stream. */
 int fv_mesh_autotune(fv_mesh* mesh, const void* U, int32_t scheme, void* stream, int32_t* best,
                      double* us_per_step);
 
@@ -162,6 +168,14 @@ int fv_mesh_autotune(fv_mesh* mesh, const void* U, int32_t scheme, void* stream,
  * fv_step / fv_mesh_status return FV_ETIMEOUT; the state is then not valid.
  * Default 2^24.  A limit of 0 forces the timeout path (for tests). */
 int fv_mesh_set_wait_limit(fv_mesh* mesh, uint32_t polls);
+
+/* Launch chaining of the step kernels (default 1 = on): each step kernel of
+ * fv_step is launched with programmatic dependent launch, so the next step's
+ * launch is prepared while the current step runs and its blocks wait in
+ * hardware for the current step to complete before reading anything; this
+ * hides most of the launch gap between steps.  Results are identical either
+ * way; 0 launches each step in plain stream order (for comparison). */
+int fv_mesh_set_launch_chaining(fv_mesh* mesh, int32_t enable);
 
 /* Two time steps per launch: temporal blocking, the GPU form of the paper's
  * chaining of processors, where the output of one update feeds the next

@@ -16,6 +16,7 @@ import numpy as np
 from . import build as _build
 
 FV_OK, FV_EINVAL, FV_ENOMEM, FV_ECUDA, FV_ENONFINITE, FV_ETIMEOUT = range(6)
+N_VARIANTS = 7  # step-kernel shapes (fv_mesh_set_variant)
 FV_F32, FV_F64 = 0, 1
 FV_BC_NONE, FV_BC_WALL, FV_BC_FARFIELD, FV_BC_EXTRAP = 0, 1, 2, 3
 ORDERS = {"identity": 0, "shuffle": 1, "rcm": 2, "hilbert": 3, "am1": 4}
@@ -69,6 +70,7 @@ def load():
             "fv_mesh_set_variant": (ctypes.c_int, [_vp, _i32]),
             "fv_mesh_set_wait_limit": (ctypes.c_int, [_vp, ctypes.c_uint32]),
             "fv_mesh_set_blocking": (ctypes.c_int, [_vp, _i32, _i32, _i32]),
+            "fv_mesh_set_launch_chaining": (ctypes.c_int, [_vp, _i32]),
             "fv_mesh_tile_halo": (ctypes.c_int, [_vp, _i32, _i64, _vp, _i64, _P(_i64), _P(_i64)]),
             "fv_mesh_autotune": (ctypes.c_int, [_vp, _vp, _i32, _vp, _P(_i32), _P(_dbl)]),
             "fv_step": (ctypes.c_int, [_vp, _vp, _i64, _dbl, _dbl, _i32, _vp, _vp, _P(_dbl)]),
@@ -230,6 +232,10 @@ class Mesh:
     def set_wait_limit(self, polls: int):
         _check(load().fv_mesh_set_wait_limit(self._h, int(polls)))
 
+    def set_launch_chaining(self, enable: bool):
+        """Programmatic dependent launch of the step kernels (default on)."""
+        _check(load().fv_mesh_set_launch_chaining(self._h, int(bool(enable))))
+
     def set_blocking(self, steps_per_launch: int, tile_cells: int = 0, staged: bool = False):
         """1: one launch per step; 2: two forward-Euler steps per launch on
         shared-memory tiles of `tile_cells` cells (0 = 1024); staged: tile
@@ -251,7 +257,7 @@ class Mesh:
         """Picks the fastest step-kernel shape for this mesh; returns
         (best, microseconds per step of each shape)."""
         best = _i32()
-        us = (_dbl * 6)()
+        us = (_dbl * N_VARIANTS)()
         _check(load().fv_mesh_autotune(self._h, _dev_ptr(U, self.torch_dtype, self.n, "U"),
                                        SCHEMES[scheme], _stream_ptr(stream), ctypes.byref(best),
                                        us))

@@ -113,6 +113,7 @@ struct fv_mesh {
   int blocking = 1;
   int pair_tile = 1024;
   int pair_staged = 0;  // 1: bulk-copy staged two-step kernel
+  bool chained = true;  // programmatic dependent launch of the step kernels
   int tiles_built = 0;  // tile size of the arrays below (0: none)
   uint2* d_cell_ln = nullptr;
   int* d_tile_info = nullptr;
@@ -132,6 +133,7 @@ struct fv_mesh {
   bool g_comp = false;
   int g_variant = -1;
   int g_blocking = -1, g_tile = -1, g_staged = -1;
+  bool g_chained = false;
   int last_t_slot = 0;
   bool stepped = false;
 
@@ -183,19 +185,13 @@ namespace {
 
 // Tiles and halos of the two-step update, built on the host for the current
 // numbering and tile size and copied to the device.
+bool uses_tiles(const fv_mesh* m) { return m->blocking == 2 || m->variant == fv::kTileVariant; }
+
 void ensure_tiles(fv_mesh* m, cudaStream_t s) {
-  if (m->blocking != 2 || m->h.n == 0 || m->tiles_built == m->pair_tile) return;
+  if (!uses_tiles(m) || m->h.n == 0 || m->tiles_built == m->pair_tile) return;
   m->free_tiles();
   m->drop_graph();
   const fv::PairTiles L = fv::build_pair_tiles(m->h, m->pair_tile);
-  int dev = 0, optin = 0;
-  FV_CUDA(cudaGetDevice(&dev));
-  FV_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  const size_t smem = fv::pair_smem_bytes(L.e_cap, L.t1_cap, m->pair_tile, m->pair_staged != 0);
-  if (smem > (size_t)optin)
-    invalid("a tile with its halos needs " + std::to_string(smem) + " bytes of shared memory (" +
-            std::to_string(optin) + " available); renumber the cells with a compact order "
-            "(Hilbert) or use smaller tiles");
   // whole 256-cell tiles: the staged kernel copies an even number of records
   const size_t ncells = (size_t)((m->h.n + fv::kPadCells - 1) / fv::kPadCells * fv::kPadCells);
   FV_CUDA(cudaMalloc((void**)&m->d_cell_ln, ncells * sizeof(uint2)));
@@ -217,6 +213,21 @@ void ensure_tiles(fv_mesh* m, cudaStream_t s) {
   m->p_e_cap = L.e_cap;
   m->p_t1_cap = L.t1_cap;
   m->tiles_built = m->pair_tile;
+}
+
+// Shared memory a tiled kernel of this mesh needs, checked against the device.
+void check_tile_smem(const fv_mesh* m, size_t smem) {
+  int dev = 0, optin = 0;
+  FV_CUDA(cudaGetDevice(&dev));
+  FV_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (smem > (size_t)optin)
+    invalid("a tile with its halos needs " + std::to_string(smem) + " bytes of shared memory (" +
+            std::to_string(optin) + " available); renumber the cells with a compact order "
+            "(Hilbert) or use smaller tiles");
+}
+
+size_t pair_smem(const fv_mesh* m) {
+  return fv::pair_smem_bytes(m->p_e_cap, m->p_t1_cap, m->tiles_built, m->pair_staged != 0);
 }
 
 void ensure_device(fv_mesh* m, cudaStream_t s) {
@@ -272,9 +283,18 @@ fv::StepArgs base_args(const fv_mesh* m) {
   a.geom = m->d_geom;
   a.n = m->h.n;
   m->uinf_conserved(a.uinf);
+  for (int q = 0; q < 4; ++q) a.uinf_f[q] = (float)a.uinf[q];
   a.err = &m->d_scal->err;
   a.wait_limit = m->wait_limit;
   a.drain_limit = fv::kDefaultWaitLimit;
+  a.chained = m->chained;
+  if (m->tiles_built) {
+    a.cell_ln = m->d_cell_ln;
+    a.tile_info = m->d_tile_info;
+    a.halo_id = m->d_halo_id;
+    a.tile = m->tiles_built;
+    a.t1_cap = m->p_t1_cap;
+  }
   return a;
 }
 
@@ -289,6 +309,8 @@ void enqueue_steps(fv_mesh* m, void* U, int64_t j0, int64_t count, double cfl, d
                    int32_t scheme, cudaStream_t s, const fv_closure* cl = nullptr,
                    bool lo_alt = false) {
   fv::LoopScalars* sc = m->d_scal;
+  if (!cl && m->variant == fv::kTileVariant && count > 0)
+    check_tile_smem(m, fv::tile_smem_bytes(m->f64(), m->p_t1_cap));
   for (int64_t j = j0; j < j0 + count; ++j) {
     fv::StepArgs a = base_args(m);
     a.bmin_read = &sc->bmin[j % 3];
@@ -328,6 +350,7 @@ void enqueue_steps(fv_mesh* m, void* U, int64_t j0, int64_t count, double cfl, d
 void enqueue_pairs(fv_mesh* m, void* U, int64_t j0, int64_t count, double cfl, double t_stop,
                    cudaStream_t s) {
   fv::LoopScalars* sc = m->d_scal;
+  if (count > 0) check_tile_smem(m, pair_smem(m));
   for (int64_t j = j0; j < j0 + count; ++j) {
     const bool even = (j % 2) == 0;
     fv::PairArgs a{};
@@ -346,7 +369,9 @@ void enqueue_pairs(fv_mesh* m, void* U, int64_t j0, int64_t count, double cfl, d
     a.tile = m->tiles_built;
     a.e_cap = m->p_e_cap;
     a.t1_cap = m->p_t1_cap;
-    m->uinf_conserved(a.uinf);
+    double ui[4];
+    m->uinf_conserved(ui);
+    for (int q = 0; q < 4; ++q) a.uinf[q] = (float)ui[q];
     a.bmin_read = &sc->bmin[j % 3];
     a.bmin_write = &sc->bmin[(j + 1) % 3];
     a.bmin_reset = &sc->bmin[(j + 2) % 3];
@@ -357,6 +382,7 @@ void enqueue_pairs(fv_mesh* m, void* U, int64_t j0, int64_t count, double cfl, d
     a.err = &sc->err;
     a.wait_limit = m->wait_limit;
     a.drain_limit = fv::kDefaultWaitLimit;
+    a.chained = m->chained;
     FV_CUDA(fv::launch_step_pair(a, m->pair_staged, s));
   }
 }
@@ -397,6 +423,7 @@ void capture_graph(fv_mesh* m, void* U, double cfl, double t_stop, int32_t schem
   m->g_blocking = m->blocking;
   m->g_tile = m->tiles_built;
   m->g_staged = m->pair_staged;
+  m->g_chained = m->chained;
 }
 
 void read_status(fv_mesh* m, cudaStream_t s, double* t_adv, bool check) {
@@ -575,6 +602,14 @@ int fv_mesh_tile_halo(const fv_mesh* mesh, int32_t tile_cells, int64_t tile, int
   });
 }
 
+int fv_mesh_set_launch_chaining(fv_mesh* mesh, int32_t enable) {
+  return guarded([&] {
+    check_mesh(mesh);
+    mesh->chained = enable != 0;
+    mesh->drop_graph();
+  });
+}
+
 int fv_mesh_set_wait_limit(fv_mesh* mesh, uint32_t polls) {
   return guarded([&] {
     check_mesh(mesh);
@@ -609,6 +644,16 @@ int fv_mesh_autotune(fv_mesh* mesh, const void* U, int32_t scheme, void* stream,
       const int64_t steps = std::max<int64_t>(8, std::min<int64_t>(64, (int64_t)(4e7 / (double)n)));
       for (int v = 0; v < fv::kStepVariants; ++v) {
         mesh->variant = v;
+        if (v == fv::kTileVariant) {
+          // tiles that do not fit (a long-band order) leave this shape out
+          try {
+            ensure_tiles(mesh, s);
+            check_tile_smem(mesh, fv::tile_smem_bytes(mesh->f64(), mesh->p_t1_cap));
+          } catch (const fv::Error&) {
+            times[v] = INFINITY;
+            continue;
+          }
+        }
         FV_CUDA(cudaMemcpyAsync(tmp, U, n * mesh->rec_bytes(), cudaMemcpyDeviceToDevice, s));
         if (mesh->use_lo()) FV_CUDA(cudaMemsetAsync(mesh->d_lo, 0, n * sizeof(uint2), s));
         FV_CUDA(fv::launch_init_scalars(mesh->d_scal, s));
@@ -704,7 +749,7 @@ int fv_step(fv_mesh* mesh, void* U, int64_t nsteps, double cfl, double t_stop, i
             mesh->g_tstop != t_stop || mesh->g_closure != closure ||
             mesh->g_comp != mesh->use_lo() || mesh->g_variant != mesh->variant ||
             mesh->g_blocking != mesh->blocking || mesh->g_tile != mesh->tiles_built ||
-            mesh->g_staged != mesh->pair_staged)
+            mesh->g_staged != mesh->pair_staged || mesh->g_chained != mesh->chained)
           capture_graph(mesh, U, cfl, t_stop, scheme, closure);
         for (int64_t k = 0; k < chunks; ++k) FV_CUDA(cudaGraphLaunch(mesh->graph, s));
       }
@@ -836,6 +881,7 @@ struct fv_batch {
   int64_t* d_mesh_end = nullptr;
   int* d_first_block = nullptr;
   double* d_uinf = nullptr;
+  float* d_uinf_f = nullptr;  // the same rounded to float
   unsigned long long* d_bmin = nullptr;
   double* d_t = nullptr;
   int* d_err = nullptr;
@@ -872,6 +918,7 @@ struct fv_batch {
     dev_free(d_mesh_end);
     dev_free(d_first_block);
     dev_free(d_uinf);
+    dev_free(d_uinf_f);
     dev_free(d_bmin);
     dev_free(d_t);
     dev_free(d_err);
@@ -906,6 +953,7 @@ void batch_ensure_device(fv_batch* b, cudaStream_t s) {
   FV_CUDA(cudaMalloc((void**)&b->d_mesh_end, M * sizeof(int64_t)));
   FV_CUDA(cudaMalloc((void**)&b->d_first_block, (M + 1) * sizeof(int)));
   FV_CUDA(cudaMalloc((void**)&b->d_uinf, 4 * M * sizeof(double)));
+  FV_CUDA(cudaMalloc((void**)&b->d_uinf_f, 4 * M * sizeof(float)));
   FV_CUDA(cudaMalloc((void**)&b->d_bmin, 3 * M * sizeof(unsigned long long)));
   FV_CUDA(cudaMalloc((void**)&b->d_t, 2 * M * sizeof(double)));
   FV_CUDA(cudaMalloc((void**)&b->d_err, sizeof(int)));
@@ -924,6 +972,9 @@ void batch_ensure_device(fv_batch* b, cudaStream_t s) {
   FV_CUDA(cudaMemcpyAsync(b->d_first_block, b->first_block.data(), (M + 1) * sizeof(int),
                           cudaMemcpyHostToDevice, s));
   FV_CUDA(cudaMemcpyAsync(b->d_uinf, b->uinf.data(), 4 * M * sizeof(double),
+                          cudaMemcpyHostToDevice, s));
+  std::vector<float> uinf_f(b->uinf.begin(), b->uinf.end());
+  FV_CUDA(cudaMemcpyAsync(b->d_uinf_f, uinf_f.data(), 4 * M * sizeof(float),
                           cudaMemcpyHostToDevice, s));
   FV_CUDA(cudaMemsetAsync(b->d_work, 0, n * b->rec_bytes(), s));
   FV_CUDA(cudaStreamSynchronize(s));
@@ -955,6 +1006,7 @@ void batch_enqueue_steps(fv_batch* b, void* U, int64_t j0, int64_t count, double
     a.block_mesh = b->d_block_mesh;
     a.mesh_end = b->d_mesh_end;
     a.uinf = b->d_uinf;
+    a.uinf_f = b->d_uinf_f;
     a.bmin = b->d_bmin;
     a.t = b->d_t;
     a.n_meshes = b->n_meshes;

@@ -117,17 +117,42 @@ __device__ __forceinline__ Prim<R> primitive(const rec_t<R>& U) {
   return w;
 }
 
+// Far-field state in the kernel's precision (rounded on the host, so no
+// kernel converts: GB300's FP64 pipe is narrow).
+template <typename R>
+__device__ __forceinline__ const R* far_field(const StepArgs& a);
+template <>
+__device__ __forceinline__ const float* far_field<float>(const StepArgs& a) {
+  return a.uinf_f;
+}
+template <>
+__device__ __forceinline__ const double* far_field<double>(const StepArgs& a) {
+  return a.uinf;
+}
+
+// ... and of mesh m of a batch
+template <typename R>
+__device__ __forceinline__ const R* batch_far_field(const BatchArgs& b, int m);
+template <>
+__device__ __forceinline__ const float* batch_far_field<float>(const BatchArgs& b, int m) {
+  return b.uinf_f + 4 * m;
+}
+template <>
+__device__ __forceinline__ const double* batch_far_field<double>(const BatchArgs& b, int m) {
+  return b.uinf + 4 * m;
+}
+
 // Ghost state across a boundary face (slip wall: mirrored normal momentum;
 // far field: free stream; extrapolation: copy of the interior state).
 template <typename R>
 __device__ __forceinline__ rec_t<R> ghost(int code, const rec_t<R>& U, R nx, R ny,
-                                          const double* uinf) {
+                                          const R* uinf) {
   if (code == -1) {
     const R m = div_(fma_(U.y, nx, mul(U.z, ny)), fma_(nx, nx, mul(ny, ny)));
     const R m2 = mul(R(-2), m);
     return Rec<R>::make(U.x, fma_(m2, nx, U.y), fma_(m2, ny, U.z), U.w);
   }
-  if (code == -2) return Rec<R>::make(R(uinf[0]), R(uinf[1]), R(uinf[2]), R(uinf[3]));
+  if (code == -2) return Rec<R>::make(uinf[0], uinf[1], uinf[2], uinf[3]);
   return U;
 }
 
@@ -135,7 +160,7 @@ __device__ __forceinline__ rec_t<R> ghost(int code, const rec_t<R>& U, R nx, R n
 template <typename R>
 __device__ __forceinline__ rec_t<R> neighbour_state(const rec_t<R>& UL, int nb, R nx, R ny,
                                                     const rec_t<R>* __restrict__ Ucur,
-                                                    const double* uinf) {
+                                                    const R* uinf) {
   return nb >= 0 ? Rec<R>::ld(Ucur + nb) : ghost<R>(nb, UL, nx, ny, uinf);
 }
 
@@ -163,7 +188,7 @@ __device__ __forceinline__ void face_flux_acc(const rec_t<R>& UL, const Prim<R>&
 template <typename R>
 __device__ __forceinline__ R add_face_flux(const rec_t<R>& UL, const Prim<R>& L, int nb, R nx,
                                            R ny, const rec_t<R>* __restrict__ Ucur,
-                                           const double* uinf, R acc[4]) {
+                                           const R* uinf, R acc[4]) {
   const rec_t<R> UR = neighbour_state<R>(UL, nb, nx, ny, Ucur, uinf);
   const Prim<R> W = primitive<R>(UR);
   const R len = face_len<R>(nx, ny);
@@ -245,6 +270,17 @@ __device__ __forceinline__ double step_dt(const StepArgs& a, double& t) {
   }
   t = __shfl_sync(0xffffffffu, t, 0);
   return __shfl_sync(0xffffffffu, dt, 0);
+}
+
+// dt and time of the current step formed by one thread (the caller shares them).
+__device__ __forceinline__ void block_dt(const StepArgs& a, double& t, double& dt) {
+  t = *a.t_read;
+  dt = a.cfl > 0.0 ? a.cfl * __longlong_as_double((long long)*a.bmin_read) : -a.cfl;
+  if (a.t_stop > 0.0) {
+    double rem = a.t_stop - t;
+    if (rem < dt) dt = rem;
+    if (!(dt > 0.0)) dt = 0.0;
+  }
 }
 
 // Everything one cell's update reads from its own records.  Geometry layout:

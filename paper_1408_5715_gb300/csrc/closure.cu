@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(kClThreads) k_step_closure(StepArgs a, Closure
       const int nb[3] = {c.n0, c.n1, c.n2};
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        UR[k] = neighbour_state<float>(c.U, nb[k], nx[k], ny[k], U, a.uinf);
+        UR[k] = neighbour_state<float>(c.U, nb[k], nx[k], ny[k], U, a.uinf_f);
         W[k] = primitive<float>(UR[k]);
         len[k] = face_len<float>(nx[k], ny[k]);
         float f[8];
@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(kClThreads) k_closure_scales(StepArgs a, Closu
       const int nb[3] = {c.n0, c.n1, c.n2};
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        const float4 UR = neighbour_state<float>(c.U, nb[k], nx[k], ny[k], U, a.uinf);
+        const float4 UR = neighbour_state<float>(c.U, nb[k], nx[k], ny[k], U, a.uinf_f);
         const Prim<float> W = primitive<float>(UR);
         float f[8];
         face_features(c.U, L, UR, W, nx[k], ny[k], face_len<float>(nx[k], ny[k]), f);
@@ -452,7 +452,7 @@ __global__ void __launch_bounds__(kGrThreads) k_closure_grad(StepArgs a, const f
       const int nb[3] = {c.n0, c.n1, c.n2};
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        UR[k] = neighbour_state<float>(c.U, nb[k], nx[k], ny[k], U, a.uinf);
+        UR[k] = neighbour_state<float>(c.U, nb[k], nx[k], ny[k], U, a.uinf_f);
         W[k] = primitive<float>(UR[k]);
         len[k] = face_len<float>(nx[k], ny[k]);
         float f[8];

@@ -26,6 +26,7 @@
 
 #include "cell_math.cuh"
 #include "kernels.h"
+#include "launch_util.cuh"
 
 namespace fv {
 
@@ -34,7 +35,7 @@ namespace {
 template <typename R, int MODE, bool COMP>
 __device__ __forceinline__ void update_cell(const StepArgs& a, const rec_t<R>* __restrict__ U,
                                             rec_t<R>* out, int64_t i, const CellIn<R>& c, R dt,
-                                            const double* uinf, R& bmin, bool& ok) {
+                                            const R* uinf, R& bmin, bool& ok) {
   const rec_t<R>& UL = c.U;
   const Prim<R> L = primitive<R>(UL);
   R acc[4] = {R(0), R(0), R(0), R(0)};
@@ -59,6 +60,7 @@ constexpr int var_min_blocks(int v) { return v == 2 ? 4 : v == 3 ? 6 : v == 4 ? 
 
 template <typename R, int MODE, bool COMP, int VAR>
 __global__ void __launch_bounds__(kBlock, var_min_blocks(VAR)) k_step(StepArgs a) {
+  chain_entry();
   const rec_t<R>* __restrict__ U = static_cast<const rec_t<R>*>(a.U);
   const rec_t<R>* __restrict__ geom = static_cast<const rec_t<R>*>(a.geom);
   rec_t<R>* out = static_cast<rec_t<R>*>(a.out);
@@ -72,7 +74,7 @@ __global__ void __launch_bounds__(kBlock, var_min_blocks(VAR)) k_step(StepArgs a
     if (i < a.n) {
       CellIn<R> cur;
       load_cell<R, MODE, COMP>(a, U, geom, i, cur);
-      update_cell<R, MODE, COMP>(a, U, out, i, cur, dtR, a.uinf, bmin, ok);
+      update_cell<R, MODE, COMP>(a, U, out, i, cur, dtR, far_field<R>(a), bmin, ok);
     }
   } else {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -81,7 +83,7 @@ __global__ void __launch_bounds__(kBlock, var_min_blocks(VAR)) k_step(StepArgs a
     for (; i < a.n; i += stride) {
       const int64_t j = i + stride;
       if (j < a.n) load_cell<R, MODE, COMP>(a, U, geom, j, nxt);
-      update_cell<R, MODE, COMP>(a, U, out, i, cur, dtR, a.uinf, bmin, ok);
+      update_cell<R, MODE, COMP>(a, U, out, i, cur, dtR, far_field<R>(a), bmin, ok);
       cur = nxt;
     }
   }
@@ -138,7 +140,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 6 : 1) k_step_batch(B
   if (i < __ldg(b.mesh_end + m)) {
     CellIn<R> cur;
     load_cell<R, MODE, COMP>(a, U, geom, i, cur);
-    update_cell<R, MODE, COMP>(a, U, out, i, cur, R(dt), b.uinf + 4 * m, bmin, ok);
+    update_cell<R, MODE, COMP>(a, U, out, i, cur, R(dt), batch_far_field<R>(b, m), bmin, ok);
   }
   if (MODE == kModeFE || MODE == kModeRK2b) {
     if (!ok) atomicOr(a.err, 1);
@@ -341,8 +343,7 @@ cudaError_t launch_one(const StepArgs& a, cudaStream_t s) {
     const unsigned cap = resident_blocks(kernel);
     g = (unsigned)(want < (int64_t)cap ? want : cap);
   }
-  kernel<<<g, kBlock, 0, s>>>(a);
-  return cudaGetLastError();
+  return launch_chained(kernel, g, kBlock, 0, s, a.chained, a);
 }
 
 template <typename R, int MODE, bool COMP>
@@ -373,7 +374,8 @@ cudaError_t launch_step_t(int mode, int var, const StepArgs& a, cudaStream_t s) 
 
 cudaError_t launch_step(bool f64, int mode, int variant, const StepArgs& a, cudaStream_t s) {
   if (variant == 5 && mode != kModeResidual && a.n > 0) return launch_step_tma(f64, mode, a, s);
-  if (variant == 5) variant = 0;
+  if (variant == kTileVariant && a.cell_ln) return launch_step_tile(f64, mode, a, s);
+  if (variant == 5 || variant == kTileVariant) variant = 0;
   if (f64) return launch_step_t<double, false>(mode, variant, a, s);
   return a.lo ? launch_step_t<float, true>(mode, variant, a, s)
               : launch_step_t<float, false>(mode, variant, a, s);

@@ -48,6 +48,7 @@ struct StepArgs {
   const void* geom;
   int64_t n;
   double uinf[4];     // far-field conserved state
+  float uinf_f[4];    // the same rounded to float (FP32 kernels convert nothing)
   const unsigned long long* bmin_read;
   unsigned long long* bmin_write;
   unsigned long long* bmin_reset;
@@ -67,6 +68,16 @@ struct StepArgs {
   // wait gives up (error bit 2), and polls allowed to drain copies in flight.
   unsigned wait_limit;
   unsigned drain_limit;
+  // Tiles of the shared-memory variant (6): tile-local neighbours per cell,
+  // per-tile halo offsets and ids (tiles.cpp), cells per tile, and the
+  // capacity of a tile plus its first halo.
+  const uint2* cell_ln;
+  const int* tile_info;
+  const int* halo_id;
+  int tile;
+  int t1_cap;
+  // launch as part of a programmatic chain (launch_util.cuh)
+  bool chained;
 };
 
 // Arguments of the batched step kernel: many meshes concatenated into one
@@ -76,6 +87,7 @@ struct BatchArgs {
   const int* block_mesh;    // [n / kBlock] mesh of each block
   const int64_t* mesh_end;  // [n_meshes] one past the last real cell of each mesh
   const double* uinf;       // [4 * n_meshes] far-field conserved states
+  const float* uinf_f;      // [4 * n_meshes] the same rounded to float
   unsigned long long* bmin; // [3 * n_meshes] CFL minima, slot-major
   double* t;                // [2 * n_meshes] time advanced, slot-major
   int n_meshes;
@@ -119,8 +131,15 @@ cudaError_t launch_pack_closure(const float* theta, unsigned* w1, unsigned* w2, 
 // Shape variants of the step kernel (see k_step): 0 one thread per cell,
 // 1 persistent grid with next-cell prefetch, 2 the same capped at 64
 // registers, 3 and 4 one thread per cell capped at 40 and 32 registers,
-// 5 persistent grid with TMA-staged cell records (tma_step.cu).
-constexpr int kStepVariants = 6;
+// 5 persistent grid with TMA-staged cell records (tma_step.cu), 6 tiles with
+// their first halo ring and primitives in shared memory (tile_step.cu).
+constexpr int kStepVariants = 7;
+constexpr int kTileVariant = 6;
+// shared memory of the tile variant: state and primitives of tile + halo
+inline size_t tile_smem_bytes(bool f64, int t1_cap) {
+  return (size_t)t1_cap * 2 * (f64 ? 32 : 16);
+}
+cudaError_t launch_step_tile(bool f64, int mode, const StepArgs& a, cudaStream_t s);
 // Library-owned per-cell arrays are allocated in whole tiles of this many
 // cells (the TMA-staged variant copies whole tiles of them).
 constexpr int64_t kPadCells = 256;
@@ -147,7 +166,7 @@ struct PairArgs {
   int64_t n;
   int tile;               // cells per tile
   int e_cap, t1_cap;      // shared-memory capacities (cells)
-  double uinf[4];
+  float uinf[4];          // far-field conserved state, rounded to float
   const unsigned long long* bmin_read;
   unsigned long long* bmin_write;
   unsigned long long* bmin_reset;
@@ -157,6 +176,7 @@ struct PairArgs {
   int* err;
   // staged kernel: bounded mbarrier waits (error bit 2 when one gives up)
   unsigned wait_limit, drain_limit;
+  bool chained;  // launch as part of a programmatic chain (launch_util.cuh)
 };
 // tile sizes with a kernel instantiation (the staged kernel: 512 and 1024)
 constexpr int kPairTiles[3] = {512, 1024, 2048};

@@ -37,44 +37,22 @@
 
 #include "cell_math.cuh"
 #include "kernels.h"
+#include "launch_util.cuh"
+#include "tile_math.cuh"
 #include "tma_util.cuh"
 
 namespace fv {
 
 namespace {
 
-constexpr unsigned kGhostCodes = 0xFFFD;  // local ids at or above this are ghost faces
+__device__ __forceinline__ float4 prim4(const Prim<float>& w) { return prim_rec<float>(w); }
 
-__device__ __forceinline__ float4 prim4(const Prim<float>& w) { return make_float4(w.u, w.v, w.p, w.c); }
-
-// One face of a cell whose neighbour states and primitives are in shared memory.
-__device__ __forceinline__ float smem_face(const float4& UL, const Prim<float>& L, unsigned v, float nx,
-                                           float ny, const float4* sU, const float4* sP,
-                                           const double* uinf, float acc[4]) {
-  float4 UR;
-  Prim<float> W;
-  if (v < kGhostCodes) {
-    UR = sU[v];
-    const float4 p = sP[v];
-    W.u = p.x, W.v = p.y, W.p = p.z, W.c = p.w;
-  } else {
-    UR = ghost<float>((int)v - 0x10000, UL, nx, ny, uinf);
-    W = primitive<float>(UR);
-  }
-  const float len = face_len<float>(nx, ny);
-  face_flux_acc<float, false>(UL, L, UR, W, nx, ny, len, 1.0f, acc);
-  return len;
-}
-
-// Residual sum of one cell (faces in the order 0, 1, 2) and its perimeter.
+// Residual sum of one cell from shared-memory neighbours (tile_math.cuh).
 __device__ __forceinline__ float cell_fluxes(const float4& g0, const float4& g1, uint2 ln,
                                              const float4& UL, const Prim<float>& L,
                                              const float4* sU, const float4* sP,
-                                             const double* uinf, float acc[4]) {
-  float perim = smem_face(UL, L, ln.x & 0xffffu, g0.x, g0.y, sU, sP, uinf, acc);
-  perim = add(perim, smem_face(UL, L, ln.x >> 16, g0.z, g0.w, sU, sP, uinf, acc));
-  perim = add(perim, smem_face(UL, L, ln.y, g1.x, g1.y, sU, sP, uinf, acc));
-  return perim;
+                                             const float* uinf, float acc[4]) {
+  return cell_fluxes<float>(g0, g1, ln, UL, L, sU, sP, uinf, acc);
 }
 
 // Forward-Euler update of one cell, plain or compensated (the arithmetic of
@@ -99,25 +77,31 @@ __device__ __forceinline__ float4 fe_update(const float4& UL, float invV, const 
 
 // dt of both steps of the pair, as the one-step kernel would take them
 // in turn: the bound (or fixed step) read at the start of the pair, each step
-// clamped so the time never passes t_stop.
-__device__ __forceinline__ void pair_dt(const PairArgs& a, double& t, double& dt1, double& dt2) {
-  t = dt1 = dt2 = 0.0;
-  if ((threadIdx.x & 31) == 0) {
-    t = *a.t_read;
-    const double dt = a.cfl > 0.0 ? a.cfl * __longlong_as_double((long long)*a.bmin_read) : -a.cfl;
-    dt1 = dt2 = dt;
-    if (a.t_stop > 0.0) {
-      const double rem1 = a.t_stop - t;
-      if (rem1 < dt1) dt1 = rem1;
-      if (!(dt1 > 0.0)) dt1 = 0.0;
-      const double rem2 = a.t_stop - (t + dt1);
-      if (rem2 < dt2) dt2 = rem2;
-      if (!(dt2 > 0.0)) dt2 = 0.0;
-    }
+// clamped so the time never passes t_stop.  One thread of the block forms
+// them (FP64 scalar work; GB300's FP64 pipe is narrow) and the block reads
+// them from shared memory after its next barrier.
+struct PairDt {
+  double t, dt1, dt2;
+  float dt1f, dt2f;
+};
+
+__device__ __forceinline__ void pair_dt(const PairArgs& a, PairDt& d) {
+  const double t = *a.t_read;
+  const double dt = a.cfl > 0.0 ? a.cfl * __longlong_as_double((long long)*a.bmin_read) : -a.cfl;
+  double dt1 = dt, dt2 = dt;
+  if (a.t_stop > 0.0) {
+    const double rem1 = a.t_stop - t;
+    if (rem1 < dt1) dt1 = rem1;
+    if (!(dt1 > 0.0)) dt1 = 0.0;
+    const double rem2 = a.t_stop - (t + dt1);
+    if (rem2 < dt2) dt2 = rem2;
+    if (!(dt2 > 0.0)) dt2 = 0.0;
   }
-  t = __shfl_sync(0xffffffffu, t, 0);
-  dt1 = __shfl_sync(0xffffffffu, dt1, 0);
-  dt2 = __shfl_sync(0xffffffffu, dt2, 0);
+  d.t = t;
+  d.dt1 = dt1;
+  d.dt2 = dt2;
+  d.dt1f = (float)dt1;
+  d.dt2f = (float)dt2;
 }
 
 // Step 1 of one cell (tile or first halo) from the states of the pair's start:
@@ -127,7 +111,7 @@ template <bool COMP>
 __device__ __forceinline__ uint2 step1_cell(const float4& g0, const float4& g1, uint2 ln,
                                             uint2 lo0, int e, const float4* sU0,
                                             const float4* sP0, float4* sU1, float4* sP1,
-                                            const double* uinf, float dt, bool check, bool& ok) {
+                                            const float* uinf, float dt, bool check, bool& ok) {
   const float4 UL = sU0[e];
   const float4 p = sP0[e];
   const Prim<float> L{p.x, p.y, p.z, p.w};
@@ -151,7 +135,7 @@ __device__ __forceinline__ uint2 step1_cell(const float4& g0, const float4& g1, 
 template <bool COMP>
 __device__ __forceinline__ float4 step2_cell(const float4& g0, const float4& g1, uint2 ln,
                                              uint2 lo1, int e, const float4* sU1,
-                                             const float4* sP1, const double* uinf, float dt,
+                                             const float4* sP1, const float* uinf, float dt,
                                              uint2& lo2, float& bmin, bool& ok) {
   const float4 UL = sU1[e];
   const float4 p = sP1[e];
@@ -199,6 +183,7 @@ __device__ __forceinline__ void pair_finish(const PairArgs& a, float bmin, bool 
 
 template <int THREADS, int KMAX, bool COMP>
 __global__ void __launch_bounds__(THREADS) k_step_pair(PairArgs a) {
+  chain_entry();
   extern __shared__ float4 smem[];
   float4* sU0 = smem;                 // [e_cap]  U^n of tile + both halos
   float4* sP0 = smem + a.e_cap;       // [e_cap]  their primitives (u, v, p, c)
@@ -209,9 +194,8 @@ __global__ void __launch_bounds__(THREADS) k_step_pair(PairArgs a) {
   const int hs = __ldg(a.tile_info + 2 * blockIdx.x);
   const int h1 = __ldg(a.tile_info + 2 * blockIdx.x + 1);
   const int h12 = __ldg(a.tile_info + 2 * blockIdx.x + 2) - hs;  // both halos
-  double t, dt1, dt2;
-  pair_dt(a, t, dt1, dt2);
-  const float dt1f = (float)dt1, dt2f = (float)dt2;
+  __shared__ PairDt sdt;
+  if (threadIdx.x == 0) pair_dt(a, sdt);
 
   // states at the start of the pair, with their primitives
   for (int e = threadIdx.x; e < nt + h12; e += THREADS) {
@@ -221,6 +205,7 @@ __global__ void __launch_bounds__(THREADS) k_step_pair(PairArgs a) {
     sP0[e] = prim4(primitive<float>(u));
   }
   __syncthreads();
+  const float dt1f = sdt.dt1f, dt2f = sdt.dt2f;
 
   // step 1: tile cells (remainders stay in registers), then the first halo
   bool ok = true;
@@ -255,7 +240,7 @@ __global__ void __launch_bounds__(THREADS) k_step_pair(PairArgs a) {
       if (COMP) a.lo_out[g] = lo2;
     }
   }
-  pair_finish(a, bmin, ok, t, dt1, dt2);
+  pair_finish(a, bmin, ok, sdt.t, sdt.dt1, sdt.dt2);
 }
 
 // One stage of the staged kernel: a tile's slices of the state, geometry,
@@ -295,6 +280,7 @@ __global__ void __launch_bounds__(THREADS) k_step_pair_tma(PairArgs a) {
   float4* sP1 = sU1 + a.t1_cap;
   __shared__ __align__(8) uint64_t bars[2];
   __shared__ int abort_flag;
+  __shared__ PairDt sdt;
   const int tid = threadIdx.x;
   const int64_t ntiles = (a.n + TILE - 1) / TILE;
   if (tid == 0) {
@@ -302,11 +288,10 @@ __global__ void __launch_bounds__(THREADS) k_step_pair_tma(PairArgs a) {
     mbar_init(&bars[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     abort_flag = 0;
+    pair_dt(a, sdt);
   }
   __syncthreads();
-  double t, dt1, dt2;
-  pair_dt(a, t, dt1, dt2);
-  const float dt1f = (float)dt1, dt2f = (float)dt2;
+  const float dt1f = sdt.dt1f, dt2f = sdt.dt2f;
   auto tile_count = [&](int64_t b) {
     const int64_t rem = a.n - b * TILE;
     return (unsigned)(rem < TILE ? rem : TILE);
@@ -385,7 +370,7 @@ __global__ void __launch_bounds__(THREADS) k_step_pair_tma(PairArgs a) {
     __syncthreads();
     return;
   }
-  pair_finish(a, bmin, ok, t, dt1, dt2);
+  pair_finish(a, bmin, ok, sdt.t, sdt.dt1, sdt.dt2);
 }
 
 template <typename K>
@@ -400,8 +385,7 @@ cudaError_t launch_plain_t(const PairArgs& a, cudaStream_t s) {
   auto k = k_step_pair<THREADS, KMAX, COMP>;
   cudaError_t e = smem_attr(k, smem);
   if (e != cudaSuccess) return e;
-  k<<<(unsigned)tiles, THREADS, smem, s>>>(a);
-  return cudaGetLastError();
+  return launch_chained(k, (unsigned)tiles, THREADS, smem, s, a.chained, a);
 }
 
 template <int THREADS, int KMAX, bool COMP>

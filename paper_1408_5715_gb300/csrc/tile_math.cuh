@@ -1,0 +1,58 @@
+// tile_math.cuh -- the cell update on tiles staged in shared memory, shared by
+// the one-step tile kernel (tile_step.cu) and the two-step kernels
+// (pair_step.cu).  A tile holds the states of its cells and halo cells and
+// their primitive variables (u, v, p, c), each computed once; neighbours are
+// 16-bit tile-local ids (tiles.cpp), ghost faces the codes 0xFFFD..0xFFFF.
+// The face arithmetic is cell_math.cuh's, so results are bitwise those of the
+// one-step kernel that forms every neighbour's primitives itself.
+#pragma once
+
+#include "cell_math.cuh"
+
+namespace fv {
+namespace {
+
+constexpr unsigned kGhostCodes = 0xFFFD;  // local ids at or above this are ghost faces
+
+template <typename R>
+__device__ __forceinline__ rec_t<R> prim_rec(const Prim<R>& w) {
+  return Rec<R>::make(w.u, w.v, w.p, w.c);
+}
+
+template <typename R>
+__device__ __forceinline__ Prim<R> rec_prim(const rec_t<R>& p) {
+  return Prim<R>{p.x, p.y, p.z, p.w};
+}
+
+// One face of a cell whose neighbour state and primitives are in shared memory.
+template <typename R>
+__device__ __forceinline__ R smem_face(const rec_t<R>& UL, const Prim<R>& L, unsigned v, R nx, R ny,
+                                       const rec_t<R>* sU, const rec_t<R>* sP, const R* uinf,
+                                       R acc[4]) {
+  rec_t<R> UR;
+  Prim<R> W;
+  if (v < kGhostCodes) {
+    UR = sU[v];
+    W = rec_prim<R>(sP[v]);
+  } else {
+    UR = ghost<R>((int)v - 0x10000, UL, nx, ny, uinf);
+    W = primitive<R>(UR);
+  }
+  const R len = face_len<R>(nx, ny);
+  face_flux_acc<R, false>(UL, L, UR, W, nx, ny, len, R(1), acc);
+  return len;
+}
+
+// Residual sum of one cell (faces in the order 0, 1, 2) and its perimeter.
+template <typename R>
+__device__ __forceinline__ R cell_fluxes(const rec_t<R>& g0, const rec_t<R>& g1, uint2 ln,
+                                         const rec_t<R>& UL, const Prim<R>& L, const rec_t<R>* sU,
+                                         const rec_t<R>* sP, const R* uinf, R acc[4]) {
+  R perim = smem_face<R>(UL, L, ln.x & 0xffffu, g0.x, g0.y, sU, sP, uinf, acc);
+  perim = add(perim, smem_face<R>(UL, L, ln.x >> 16, g0.z, g0.w, sU, sP, uinf, acc));
+  perim = add(perim, smem_face<R>(UL, L, ln.y, g1.x, g1.y, sU, sP, uinf, acc));
+  return perim;
+}
+
+}  // namespace
+}  // namespace fv

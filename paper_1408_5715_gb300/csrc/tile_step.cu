@@ -1,0 +1,126 @@
+// tile_step.cu -- one step per launch on tiles staged in shared memory (shape
+// variant 6 of the step kernel).
+//
+// A block owns a tile of consecutive cells.  It loads the states of the tile
+// and of its first halo ring (the cells outside the tile adjacent to it,
+// tiles.cpp) into shared memory and forms their primitive variables (Eq. 2)
+// once per cell; the one-thread-per-cell kernels form them once per face,
+// i.e. four times per cell.  Each tile cell then sums its three face fluxes
+// from the shared-memory neighbours and finishes exactly as the other shapes
+// do (finish_cell: forward Euler, Heun's stages or the residual, plain or
+// compensated), so all shapes give the same bits.  The FP64 step, bound by
+// its division and square-root sequences, gains most.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "cell_math.cuh"
+#include "kernels.h"
+#include "launch_util.cuh"
+#include "tile_math.cuh"
+
+namespace fv {
+
+namespace {
+
+template <typename R, int MODE, bool COMP, int THREADS, int KMAX>
+__global__ void __launch_bounds__(THREADS) k_step_tile(StepArgs a) {
+  chain_entry();
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  rec_t<R>* sU = reinterpret_cast<rec_t<R>*>(smem_raw);  // [t1_cap] states
+  rec_t<R>* sP = sU + a.t1_cap;                            // [t1_cap] (u, v, p, c)
+  const rec_t<R>* __restrict__ U = static_cast<const rec_t<R>*>(a.U);
+  const rec_t<R>* __restrict__ geom = static_cast<const rec_t<R>*>(a.geom);
+  rec_t<R>* out = static_cast<rec_t<R>*>(a.out);
+  const int64_t t0 = (int64_t)blockIdx.x * a.tile;
+  const int nt = (int)min((int64_t)a.tile, a.n - t0);
+  const int hs = __ldg(a.tile_info + 2 * blockIdx.x);
+  const int h1 = __ldg(a.tile_info + 2 * blockIdx.x + 1);
+  // dt formed once per block (FP64 scalar work), read after the barrier
+  __shared__ double s_t, s_dt;
+  if (threadIdx.x == 0 && MODE != kModeResidual) block_dt(a, s_t, s_dt);
+  for (int e = threadIdx.x; e < nt + h1; e += THREADS) {
+    const int64_t g = e < nt ? t0 + e : (int64_t)__ldg(a.halo_id + hs + (e - nt));
+    const rec_t<R> u = Rec<R>::ld(U + g);
+    sU[e] = u;
+    sP[e] = prim_rec<R>(primitive<R>(u));
+  }
+  __syncthreads();
+  const double t = MODE != kModeResidual ? s_t : 0.0, dt = MODE != kModeResidual ? s_dt : 0.0;
+  const R dtR = R(dt);
+  R bmin = R(INFINITY);
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < KMAX; ++k) {
+    const int e = threadIdx.x + k * THREADS;
+    if (e < nt) {
+      const int64_t i = t0 + e;
+      CellIn<R> c;
+      c.g0 = Rec<R>::ld(geom + 2 * i);
+      c.g1 = Rec<R>::ld(geom + 2 * i + 1);
+      c.U = sU[e];
+      if (MODE == kModeRK2b) c.base = static_cast<const rec_t<R>*>(a.Ubase)[i];
+      if (COMP && MODE != kModeResidual) c.lo = a.lo[i];
+      if (COMP && MODE == kModeRK2b) c.lo_stage = a.lo_stage[i];
+      const uint2 ln = __ldg(a.cell_ln + i);
+      R acc[4] = {R(0), R(0), R(0), R(0)};
+      const R perim =
+          cell_fluxes<R>(c.g0, c.g1, ln, c.U, rec_prim<R>(sP[e]), sU, sP, far_field<R>(a), acc);
+      finish_cell<R, MODE, COMP>(a, out, i, c, acc, perim, dtR, bmin, ok);
+    }
+  }
+  if (MODE == kModeFE || MODE == kModeRK2b) {
+    if (!ok) atomicOr(a.err, 1);
+    const double m = (double)block_min<R>(bmin);
+    if (threadIdx.x == 0) {
+      atomicMin(a.bmin_write, (unsigned long long)__double_as_longlong(m));
+      if (blockIdx.x == 0) {
+        *a.t_write = t + dt;
+        *a.bmin_reset = kInfBits;
+      }
+    }
+  }
+}
+
+template <typename R, int MODE, bool COMP, int THREADS, int KMAX>
+cudaError_t launch_tile_t(const StepArgs& a, cudaStream_t s) {
+  auto k = k_step_tile<R, MODE, COMP, THREADS, KMAX>;
+  const size_t smem = tile_smem_bytes(sizeof(R) == 8, a.t1_cap);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t tiles = (a.n + a.tile - 1) / a.tile;
+  return launch_chained(k, (unsigned)tiles, THREADS, smem, s, a.chained, a);
+}
+
+template <typename R, int MODE, bool COMP>
+cudaError_t launch_tile_size(const StepArgs& a, cudaStream_t s) {
+  switch (a.tile) {
+    case 512: return launch_tile_t<R, MODE, COMP, 256, 2>(a, s);
+    case 1024: return launch_tile_t<R, MODE, COMP, 256, 4>(a, s);
+    case 2048: return launch_tile_t<R, MODE, COMP, 512, 4>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename R, bool COMP>
+cudaError_t launch_tile_mode(int mode, const StepArgs& a, cudaStream_t s) {
+  switch (mode) {
+    case kModeFE: return launch_tile_size<R, kModeFE, COMP>(a, s);
+    case kModeRK2a: return launch_tile_size<R, kModeRK2a, COMP>(a, s);
+    case kModeRK2b: return launch_tile_size<R, kModeRK2b, COMP>(a, s);
+    case kModeResidual: return launch_tile_size<R, kModeResidual, false>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_step_tile(bool f64, int mode, const StepArgs& a, cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  if (!a.cell_ln || !a.tile_info || !a.halo_id) return cudaErrorInvalidValue;
+  if (f64) return launch_tile_mode<double, false>(mode, a, s);
+  if (a.lo) return launch_tile_mode<float, true>(mode, a, s);
+  return launch_tile_mode<float, false>(mode, a, s);
+}
+
+}  // namespace fv

@@ -141,11 +141,11 @@ __global__ void __launch_bounds__(kBlock) k_step_tma(BatchArgs b) {
     const int64_t i = tile * kTile + tid;
     int m = 0;
     int64_t end = a.n;
-    const double* uinf = a.uinf;
+    const R* uinf = far_field<R>(a);
     if (BATCH) {
       m = __ldg(b.block_mesh + tile);
       end = __ldg(b.mesh_end + m);
-      uinf = b.uinf + 4 * m;
+      uinf = batch_far_field<R>(b, m);
       dt = tma_batch_dt(b, m, t);
       bmin = R(INFINITY);
     }

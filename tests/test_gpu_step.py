@@ -214,17 +214,20 @@ def test_kernel_shapes_give_identical_results(big_square, prec, scheme):
     mi, U0 = big_square
     dt_ = torch.float64 if prec == "f64" else torch.float32
     outs, ts = [], []
-    for v in range(6):
+    shapes = [(v, 1024) for v in range(B.N_VARIANTS)] + [(6, 512), (6, 2048)]
+    for v, tile in shapes:
         g = B.Mesh.from_input(mi, prec)
         g.renumber("hilbert")
         g.set_variant(v)
+        if v == 6:
+            g.set_blocking(1, tile)  # tile size of the shared-memory shape
         U = dev(U0, dt_)
         ts.append(g.step(U, 30, 0.4, scheme=scheme))
         outs.append(U)
         g.close()
-    for v in range(1, 6):
-        assert ts[v] == ts[0]
-        assert torch.equal(outs[v], outs[0]), v
+    for k in range(1, len(shapes)):
+        assert ts[k] == ts[0]
+        assert torch.equal(outs[k], outs[0]), shapes[k]
 
 
 def test_autotune_picks_a_shape_and_leaves_state(big_square):
@@ -233,11 +236,12 @@ def test_autotune_picks_a_shape_and_leaves_state(big_square):
     U = dev(U0, torch.float32)
     before = U.clone()
     best, us = g.autotune(U)
-    assert 0 <= best < 6 and len(us) == 6 and all(x > 0 for x in us)
+    n = B.N_VARIANTS
+    assert 0 <= best < n and len(us) == n and all(x > 0 for x in us)
     assert us[best] == min(us)
     assert torch.equal(U, before)
     with pytest.raises(B.FVError):
-        g.set_variant(7)
+        g.set_variant(n)
 
 
 @pytest.mark.parametrize("prec", ["f32", "f64"])
@@ -369,3 +373,45 @@ def test_square_16m_one_step_vs_oracle_and_invariants(orc):
         assert (np.abs(T1 - T0) <= tol * scale).all()
         del U
         g.close()
+
+
+def test_tile_shape_residual_and_boundaries_match_oracle(orc):
+    # the shared-memory shape on a mesh with walls and far field, FP64 against
+    # the oracle, and its residual (through fv_residual, shape-independent)
+    mi = W.channel_bump(60, 24, seed=12)
+    prim = W.freestream(0.6)
+    om = orc.Mesh(mi.xy, mi.tri, mi.canon, mi.bnd, mi.default_bc, W.conserved(*prim))
+    U0 = W.random_smooth_state(mi.centroids(), seed=13)
+    g = B.Mesh.from_input(mi, "f64")
+    g.set_freestream(*prim)
+    perm = g.renumber("hilbert")
+    g.set_variant(6)
+    g.set_blocking(1, 512)
+    Uo, to, _, bad = om.run(U0, 60, 0.4)
+    assert not bad
+    U = dev(U0[perm], torch.float64)
+    assert g.step(U, 60, 0.4) == pytest.approx(to, rel=1e-13)
+    out = np.empty_like(Uo)
+    out[perm] = U.cpu().numpy()
+    assert rel_err_max(out, Uo) <= 1e-12
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_launch_chaining_leaves_results_unchanged(big_square, prec):
+    # programmatic dependent launch only moves when the next step's blocks are
+    # scheduled; they wait for the previous step in hardware before reading
+    mi, U0 = big_square
+    dt_ = torch.float64 if prec == "f64" else torch.float32
+    for v in (0, 1, 3, 6):
+        outs = []
+        for chained in (True, False):
+            g = B.Mesh.from_input(mi, prec)
+            g.renumber("hilbert")
+            g.set_variant(v)
+            g.set_launch_chaining(chained)
+            U = dev(U0, dt_)
+            t = g.step(U, 101, 0.4)  # a graph of 96 steps and 5 direct launches
+            outs.append((t, U))
+            g.close()
+        assert outs[0][0] == outs[1][0]
+        assert torch.equal(outs[0][1], outs[1][1]), v
