@@ -3,8 +3,8 @@
 
 Default workload: the 1M-triangle channel with a 10%-thick circular-arc bump
 (graded 4x over the bump and at the lower wall, jittered interior nodes,
-far-field inflow/outflow at Mach 0.5, slip walls), RCM cell order, FP32
-state, forward Euler at CFL 0.4.  One benchmark step = one call of the time
+far-field inflow/outflow at Mach 0.5, slip walls), Hilbert cell order (the
+faster of RCM and Hilbert on this mesh), FP32 state, forward Euler at CFL 0.4.  One benchmark step = one call of the time
 loop (10,000 time steps, each one fused kernel, replayed as captured CUDA
 graphs) followed by the FP64 conserved totals -- every row of the hot path.
 
@@ -74,7 +74,7 @@ def parse_args():
 
 WORKLOADS = {
     "channel_bump_1m": dict(make=W.channel_bump_1m, init="uniform", mach=0.5, time_steps=10000,
-                            order="rcm", desc="channel 3x1, 10% circular-arc bump, 1250x400 quads, "
+                            order="hilbert", desc="channel 3x1, 10% circular-arc bump, 1250x400 quads, "
                             "graded 4x, jitter 20%, far field M=0.5, slip walls"),
     "square_16m": dict(make=W.vortex_square_16m, init="vortex", mach=0.5, time_steps=1000,
                        order="hilbert", desc="periodic unit square, 4096x2048 quads, jitter 20%, "
@@ -529,27 +529,37 @@ def batched_leg(B, time_steps=1000):
         m.close()
     flat0 = torch.tensor(batch.pack(states), dtype=torch.float32, device="cuda")
     U = torch.empty_like(flat0)
-    times = []
-    for it in range(3):
-        U.copy_(flat0)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        batch.step(U, time_steps, 0.4, sync=False)
-        batch.totals(U)
-        e1.record()
-        torch.cuda.synchronize()
-        if it > 0:
-            times.append(e0.elapsed_time(e1) / 1e3)
-    t_adv = batch.step(U, 0, 0.4)  # collects the error flag of the runs above
+    by_shape = {}
+    for shape in (5, 6, 0):
+        batch.set_variant(shape)
+        times = []
+        for it in range(3):
+            U.copy_(flat0)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            batch.step(U, time_steps, 0.4, sync=False)
+            batch.totals(U)
+            e1.record()
+            torch.cuda.synchronize()
+            if it > 0:
+                times.append(e0.elapsed_time(e1) / 1e3)
+        batch.step(U, 0, 0.4)  # collects the error flag of the runs above
+        by_shape[shape] = statistics.mean(times)
+    best = min(by_shape, key=by_shape.get)
     cells = int(sum(batch.sizes))
-    v = cells * time_steps / statistics.mean(times)
+    v = cells * time_steps / by_shape[best]
     peak, _ = measured_peaks()
     gbs = (ALGO_BYTES["f32"] + COMP_BYTES) * v / 1e9
     res = {"value": v, "unit": "cell-updates/s", "meshes": batch.n_meshes, "cells": cells,
            "padded_cells": batch.n_padded, "time_steps": time_steps, "dtype": "f32",
-           "order": "hilbert", "kernel": "k_step_batch<float, FE, compensated>",
+           "order": "hilbert",
+           "kernel": {5: "k_step_tma<float, FE, compensated, batch>",
+                      6: "k_step_tile_batch<float, FE, compensated>",
+                      0: "k_step_batch<float, FE, compensated>"}[best],
+           "shape": best,
+           "value_by_shape": {k: cells * time_steps / t for k, t in by_shape.items()},
            "achieved_gbs_kernel_bytes": gbs, "frac_of_measured_hbm": gbs / peak,
            "launches_per_step": time_steps + 4}
     batch.close()

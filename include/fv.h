@@ -350,9 +350,12 @@ int fv_batch_destroy(fv_batch* batch);
  * the records up to offsets[k + 1] are padding, ignored and unspecified. */
 int fv_batch_info(const fv_batch* batch, int64_t* n_cells_padded, int64_t* offsets);
 
-/* Kernel shape of a batch: 5 (default) TMA-staged 256-cell tiles, one per
- * block of the batch (see fv_mesh_set_variant); 0 one thread per cell.  Both
- * give bitwise identical results. */
+/* Kernel shape of a batch: 5 TMA-staged 256-cell tiles, one per block of the
+ * batch (see fv_mesh_set_variant); 0 one thread per cell; 6 tiles of 1024
+ * cells within each mesh with their neighbour ring and primitives in shared
+ * memory (needs compactly numbered meshes: FV_EINVAL if a tile's ring does
+ * not fit).  Default: 6 when its tiles fit, else 0 (decided at the first
+ * device call).  All give bitwise identical results. */
 int fv_batch_set_variant(fv_batch* batch, int32_t variant);
 
 /* Compensated float update for FV_F32 batches (see fv_mesh_set_compensation). */

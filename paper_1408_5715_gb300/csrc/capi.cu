@@ -4,6 +4,7 @@
 // and a thread-local message.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -58,6 +59,7 @@ void dev_free(T*& p) {
 // (period 2) and the rotating dt slots (period 3) are back in their starting
 // roles after each graph, and the same graph can be replayed.
 constexpr int64_t kGraphSteps = 96;
+constexpr int kBatchTile = 1024;  // cells per tile of the batched shared-memory shape
 
 }  // namespace
 
@@ -867,7 +869,15 @@ struct fv_batch {
   std::vector<double> vol;
   std::vector<double> uinf;          // 4 per mesh (conserved)
   bool compensated = true;
-  int variant = 5;                   // 0: one thread per cell; 5: TMA-staged tiles
+  // 0: one thread per cell; 5: TMA-staged tiles; 6: tiles; -1: 6 when its
+  // tiles fit in shared memory, else 0 (chosen at the first device call)
+  int variant = -1;
+  // shared-memory tiles of 1024 cells within each mesh (shape 6)
+  bool tiles_ok = false;
+  int32_t t1_cap = 0;
+  std::vector<int32_t> tile_mesh, tile_cells, mesh_first_tile, tile_info, halo_id;
+  std::vector<int64_t> tile_start;
+  std::vector<uint32_t> cell_ln;     // [2n]
   // device
   int device = -1;
   bool uploaded = false;
@@ -887,12 +897,20 @@ struct fv_batch {
   int* d_err = nullptr;
   double* d_partials = nullptr;
   double* d_totals = nullptr;
+  int* d_tile_mesh = nullptr;
+  int64_t* d_tile_start = nullptr;
+  int* d_tile_cells = nullptr;
+  int* d_mesh_first_tile = nullptr;
+  int* d_tile_info = nullptr;
+  int* d_halo_id = nullptr;
+  uint2* d_cell_ln = nullptr;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
   const void* g_U = nullptr;
   int32_t g_scheme = -1;
   double g_cfl = 0.0, g_tstop = 0.0;
   bool g_comp = false;
+  int g_variant = -1;
   int last_t_slot = 0;
   bool stepped = false;
 
@@ -924,6 +942,13 @@ struct fv_batch {
     dev_free(d_err);
     dev_free(d_partials);
     dev_free(d_totals);
+    dev_free(d_tile_mesh);
+    dev_free(d_tile_start);
+    dev_free(d_tile_cells);
+    dev_free(d_mesh_first_tile);
+    dev_free(d_tile_info);
+    dev_free(d_halo_id);
+    dev_free(d_cell_ln);
     if (cap_stream) cudaStreamDestroy(cap_stream);
     cap_stream = nullptr;
     uploaded = false;
@@ -977,13 +1002,85 @@ void batch_ensure_device(fv_batch* b, cudaStream_t s) {
   FV_CUDA(cudaMemcpyAsync(b->d_uinf_f, uinf_f.data(), 4 * M * sizeof(float),
                           cudaMemcpyHostToDevice, s));
   FV_CUDA(cudaMemsetAsync(b->d_work, 0, n * b->rec_bytes(), s));
+  if (b->tiles_ok) {
+    const size_t nt = b->tile_mesh.size(), nh = std::max<size_t>(b->halo_id.size(), 1);
+    FV_CUDA(cudaMalloc((void**)&b->d_tile_mesh, nt * sizeof(int)));
+    FV_CUDA(cudaMalloc((void**)&b->d_tile_start, nt * sizeof(int64_t)));
+    FV_CUDA(cudaMalloc((void**)&b->d_tile_cells, nt * sizeof(int)));
+    FV_CUDA(cudaMalloc((void**)&b->d_mesh_first_tile, M * sizeof(int)));
+    FV_CUDA(cudaMalloc((void**)&b->d_tile_info, b->tile_info.size() * sizeof(int)));
+    FV_CUDA(cudaMalloc((void**)&b->d_halo_id, nh * sizeof(int)));
+    FV_CUDA(cudaMalloc((void**)&b->d_cell_ln, n * sizeof(uint2)));
+    FV_CUDA(cudaMemcpyAsync(b->d_tile_mesh, b->tile_mesh.data(), nt * sizeof(int),
+                            cudaMemcpyHostToDevice, s));
+    FV_CUDA(cudaMemcpyAsync(b->d_tile_start, b->tile_start.data(), nt * sizeof(int64_t),
+                            cudaMemcpyHostToDevice, s));
+    FV_CUDA(cudaMemcpyAsync(b->d_tile_cells, b->tile_cells.data(), nt * sizeof(int),
+                            cudaMemcpyHostToDevice, s));
+    FV_CUDA(cudaMemcpyAsync(b->d_mesh_first_tile, b->mesh_first_tile.data(), M * sizeof(int),
+                            cudaMemcpyHostToDevice, s));
+    FV_CUDA(cudaMemcpyAsync(b->d_tile_info, b->tile_info.data(), b->tile_info.size() * sizeof(int),
+                            cudaMemcpyHostToDevice, s));
+    if (!b->halo_id.empty())
+      FV_CUDA(cudaMemcpyAsync(b->d_halo_id, b->halo_id.data(), b->halo_id.size() * sizeof(int),
+                              cudaMemcpyHostToDevice, s));
+    FV_CUDA(cudaMemcpyAsync(b->d_cell_ln, b->cell_ln.data(), n * sizeof(uint2),
+                            cudaMemcpyHostToDevice, s));
+  }
   FV_CUDA(cudaStreamSynchronize(s));
   b->device = dev;
   b->uploaded = true;
+  if (b->variant < 0) {
+    int optin = 0;
+    FV_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const bool fits =
+        b->tiles_ok && fv::tile_smem_bytes(b->f64(), b->t1_cap) <= (size_t)optin;
+    b->variant = fits ? fv::kTileVariant : 0;
+  }
+}
+
+// Tiles of kBatchTile cells within each mesh of a batch (shape 6), in the
+// batch numbering; a mesh whose tiles cannot be built leaves shape 6 off.
+void build_batch_tiles(fv_batch* b, fv_mesh* const* meshes) {
+  b->cell_ln.assign(2 * (size_t)b->n, 0u);
+  b->mesh_first_tile.assign(b->n_meshes, 0);
+  try {
+    for (int k = 0; k < b->n_meshes; ++k) {
+      const fv_mesh* m = meshes[k];
+      const int64_t off = b->offsets[k];
+      b->mesh_first_tile[k] = (int32_t)b->tile_mesh.size();
+      if (m->h.n == 0) continue;
+      const fv::PairTiles L = fv::build_pair_tiles(m->h, kBatchTile);
+      const int64_t hbase = (int64_t)b->halo_id.size();
+      if (hbase + (int64_t)L.halo_id.size() > INT32_MAX) invalid("batch halos too large");
+      for (int64_t j = 0; j < L.n_tiles; ++j) {
+        b->tile_mesh.push_back(k);
+        b->tile_start.push_back(off + j * kBatchTile);
+        b->tile_cells.push_back((int32_t)std::min<int64_t>(kBatchTile, m->h.n - j * kBatchTile));
+        b->tile_info.push_back((int32_t)(hbase + L.tile_info[2 * j]));
+        b->tile_info.push_back(L.tile_info[2 * j + 1]);
+      }
+      for (int32_t x : L.halo_id) b->halo_id.push_back((int32_t)(x + off));
+      std::copy(L.cell_ln.begin(), L.cell_ln.end(), b->cell_ln.begin() + 2 * off);
+      b->t1_cap = std::max(b->t1_cap, L.t1_cap);
+    }
+    b->tile_info.push_back((int32_t)b->halo_id.size());
+    b->tile_info.push_back(0);
+    b->tiles_ok = true;
+  } catch (const fv::Error&) {
+    b->tiles_ok = false;
+    b->tile_mesh.clear();
+    b->tile_start.clear();
+    b->tile_cells.clear();
+    b->tile_info.clear();
+    b->halo_id.clear();
+    b->cell_ln.clear();
+  }
 }
 
 cudaError_t batch_launch(const fv_batch* b, int mode, const fv::BatchArgs& a, cudaStream_t s) {
   if (b->variant == 5) return fv::launch_batch_step_tma(b->f64(), mode, a, s);
+  if (b->variant == fv::kTileVariant) return fv::launch_batch_step_tile(b->f64(), mode, a, s);
   return fv::launch_batch_step(b->f64(), mode, a, b->n_blocks(), s);
 }
 
@@ -1015,6 +1112,19 @@ void batch_enqueue_steps(fv_batch* b, void* U, int64_t j0, int64_t count, double
     a.slot_reset = (int)((j + 2) % 3);
     a.t_read = (int)(j % 2);
     a.t_write = (int)((j + 1) % 2);
+    if (b->variant == fv::kTileVariant) {
+      a.s.cell_ln = b->d_cell_ln;
+      a.s.tile_info = b->d_tile_info;
+      a.s.halo_id = b->d_halo_id;
+      a.s.tile = kBatchTile;
+      a.s.t1_cap = b->t1_cap;
+      a.s.chained = true;
+      a.tile_mesh = b->d_tile_mesh;
+      a.tile_start = b->d_tile_start;
+      a.tile_cells = b->d_tile_cells;
+      a.mesh_first_tile = b->d_mesh_first_tile;
+      a.n_tiles = (int)b->tile_mesh.size();
+    }
     if (scheme == FV_SCHEME_FE) {
       const bool even = (j % 2) == 0;
       a.s.U = even ? U : b->d_work;
@@ -1089,6 +1199,7 @@ int fv_batch_create(fv_mesh* const* meshes, int32_t n_meshes, fv_batch** out) {
           b->block_mesh[blk] = k;
       }
       b->first_block[n_meshes] = (int32_t)(n / fv::kBlock);
+      build_batch_tiles(b, meshes);
     } catch (...) {
       delete b;
       throw;
@@ -1124,7 +1235,19 @@ int fv_batch_info(const fv_batch* batch, int64_t* n_cells_padded, int64_t* offse
 int fv_batch_set_variant(fv_batch* batch, int32_t variant) {
   return guarded([&] {
     check_batch(batch);
-    if (variant != 0 && variant != 5) invalid("batch kernel shape must be 0 or 5");
+    if (variant != 0 && variant != 5 && variant != fv::kTileVariant)
+      invalid("batch kernel shape must be 0, 5 or 6");
+    if (variant == fv::kTileVariant) {
+      if (!batch->tiles_ok)
+        invalid("a mesh of the batch has tiles whose halos exceed 65533 cells; renumber it "
+                "with a compact order (Hilbert)");
+      int dev = 0, optin = 0;
+      FV_CUDA(cudaGetDevice(&dev));
+      FV_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+      if (fv::tile_smem_bytes(batch->f64(), batch->t1_cap) > (size_t)optin)
+        invalid("a tile of the batch with its neighbour ring does not fit in shared memory; "
+                "renumber the meshes with a compact order (Hilbert)");
+    }
     batch->variant = variant;
     batch->drop_graph();
   });
@@ -1164,7 +1287,8 @@ int fv_batch_step(fv_batch* batch, void* U, int64_t nsteps, double cfl, double t
       const int64_t chunks = nsteps / kGraphSteps;
       if (chunks > 0) {
         if (!batch->graph || batch->g_U != U || batch->g_scheme != scheme ||
-            batch->g_cfl != cfl || batch->g_tstop != t_stop || batch->g_comp != batch->use_lo()) {
+            batch->g_cfl != cfl || batch->g_tstop != t_stop || batch->g_comp != batch->use_lo() ||
+            batch->g_variant != batch->variant) {
           batch->drop_graph();
           cudaGraph_t g = nullptr;
           FV_CUDA(cudaStreamBeginCapture(batch->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -1184,6 +1308,7 @@ int fv_batch_step(fv_batch* batch, void* U, int64_t nsteps, double cfl, double t
           batch->g_cfl = cfl;
           batch->g_tstop = t_stop;
           batch->g_comp = batch->use_lo();
+          batch->g_variant = batch->variant;
         }
         for (int64_t k = 0; k < chunks; ++k) FV_CUDA(cudaGraphLaunch(batch->graph, s));
       }

@@ -93,6 +93,15 @@ struct BatchArgs {
   int n_meshes;
   int slot_read, slot_write, slot_reset;
   int t_read, t_write;
+  // tiles of the shared-memory shape (6): per tile its mesh, first cell and
+  // cell count; per mesh its first tile.  The tile-local neighbours, halo
+  // offsets and ids and the capacity are in s (cell_ln, tile_info, halo_id,
+  // t1_cap; s.tile = the largest tile).
+  const int* tile_mesh;
+  const int64_t* tile_start;
+  const int* tile_cells;
+  const int* mesh_first_tile;
+  int n_tiles;
 };
 
 // Learned dissipation scale (closure.cu): MLP 8 -> 32 -> 32 -> 1 with
@@ -140,6 +149,7 @@ inline size_t tile_smem_bytes(bool f64, int t1_cap) {
   return (size_t)t1_cap * 2 * (f64 ? 32 : 16);
 }
 cudaError_t launch_step_tile(bool f64, int mode, const StepArgs& a, cudaStream_t s);
+cudaError_t launch_batch_step_tile(bool f64, int mode, const BatchArgs& b, cudaStream_t s);
 // Library-owned per-cell arrays are allocated in whole tiles of this many
 // cells (the TMA-staged variant copies whole tiles of them).
 constexpr int64_t kPadCells = 256;

@@ -82,6 +82,101 @@ __global__ void __launch_bounds__(THREADS) k_step_tile(StepArgs a) {
   }
 }
 
+// Many meshes: each block is one tile of one mesh (tiles never span meshes)
+// and uses that mesh's dt, time, far field and CFL-minimum slot; the mesh's
+// first tile advances its time and clears its next slot.
+template <typename R, int MODE, bool COMP, int THREADS, int KMAX>
+__global__ void __launch_bounds__(THREADS) k_step_tile_batch(BatchArgs b) {
+  chain_entry();
+  const StepArgs& a = b.s;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  rec_t<R>* sU = reinterpret_cast<rec_t<R>*>(smem_raw);  // [t1_cap] states
+  rec_t<R>* sP = sU + a.t1_cap;                            // [t1_cap] (u, v, p, c)
+  const rec_t<R>* __restrict__ U = static_cast<const rec_t<R>*>(a.U);
+  const rec_t<R>* __restrict__ geom = static_cast<const rec_t<R>*>(a.geom);
+  rec_t<R>* out = static_cast<rec_t<R>*>(a.out);
+  const int tile = blockIdx.x;
+  const int m = __ldg(b.tile_mesh + tile);
+  const int64_t t0 = __ldg(b.tile_start + tile);
+  const int nt = __ldg(b.tile_cells + tile);
+  const int hs = __ldg(a.tile_info + 2 * tile);
+  const int h1 = __ldg(a.tile_info + 2 * tile + 1);
+  __shared__ double s_t, s_dt;
+  if (threadIdx.x == 0 && MODE != kModeResidual) {
+    const double t = b.t[b.t_read * b.n_meshes + m];
+    const unsigned long long bits = b.bmin[b.slot_read * b.n_meshes + m];
+    double dt = a.cfl > 0.0 ? a.cfl * __longlong_as_double((long long)bits) : -a.cfl;
+    if (a.t_stop > 0.0) {
+      const double rem = a.t_stop - t;
+      if (rem < dt) dt = rem;
+      if (!(dt > 0.0)) dt = 0.0;
+    }
+    s_t = t;
+    s_dt = dt;
+  }
+  for (int e = threadIdx.x; e < nt + h1; e += THREADS) {
+    const int64_t g = e < nt ? t0 + e : (int64_t)__ldg(a.halo_id + hs + (e - nt));
+    const rec_t<R> u = Rec<R>::ld(U + g);
+    sU[e] = u;
+    sP[e] = prim_rec<R>(primitive<R>(u));
+  }
+  __syncthreads();
+  const double t = MODE != kModeResidual ? s_t : 0.0, dt = MODE != kModeResidual ? s_dt : 0.0;
+  const R dtR = R(dt);
+  const R* uinf = batch_far_field<R>(b, m);
+  R bmin = R(INFINITY);
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < KMAX; ++k) {
+    const int e = threadIdx.x + k * THREADS;
+    if (e < nt) {
+      const int64_t i = t0 + e;
+      CellIn<R> c;
+      c.g0 = Rec<R>::ld(geom + 2 * i);
+      c.g1 = Rec<R>::ld(geom + 2 * i + 1);
+      c.U = sU[e];
+      if (MODE == kModeRK2b) c.base = static_cast<const rec_t<R>*>(a.Ubase)[i];
+      if (COMP && MODE != kModeResidual) c.lo = a.lo[i];
+      if (COMP && MODE == kModeRK2b) c.lo_stage = a.lo_stage[i];
+      const uint2 ln = __ldg(a.cell_ln + i);
+      R acc[4] = {R(0), R(0), R(0), R(0)};
+      const R perim = cell_fluxes<R>(c.g0, c.g1, ln, c.U, rec_prim<R>(sP[e]), sU, sP, uinf, acc);
+      finish_cell<R, MODE, COMP>(a, out, i, c, acc, perim, dtR, bmin, ok);
+    }
+  }
+  if (MODE == kModeFE || MODE == kModeRK2b) {
+    if (!ok) atomicOr(a.err, 1);
+    const double mn = (double)block_min<R>(bmin);
+    if (threadIdx.x == 0) {
+      atomicMin(&b.bmin[b.slot_write * b.n_meshes + m], (unsigned long long)__double_as_longlong(mn));
+      if (tile == __ldg(b.mesh_first_tile + m)) {
+        b.t[b.t_write * b.n_meshes + m] = t + dt;
+        b.bmin[b.slot_reset * b.n_meshes + m] = kInfBits;
+      }
+    }
+  }
+}
+
+template <typename R, int MODE, bool COMP, int THREADS, int KMAX>
+cudaError_t launch_tile_batch_t(const BatchArgs& b, cudaStream_t s) {
+  auto k = k_step_tile_batch<R, MODE, COMP, THREADS, KMAX>;
+  const size_t smem = tile_smem_bytes(sizeof(R) == 8, b.s.t1_cap);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return launch_chained(k, (unsigned)b.n_tiles, THREADS, smem, s, b.s.chained, b);
+}
+
+template <typename R, bool COMP>
+cudaError_t launch_tile_batch_mode(int mode, const BatchArgs& b, cudaStream_t s) {
+  if (b.s.tile != 1024) return cudaErrorInvalidValue;
+  switch (mode) {
+    case kModeFE: return launch_tile_batch_t<R, kModeFE, COMP, 256, 4>(b, s);
+    case kModeRK2a: return launch_tile_batch_t<R, kModeRK2a, COMP, 256, 4>(b, s);
+    case kModeRK2b: return launch_tile_batch_t<R, kModeRK2b, COMP, 256, 4>(b, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <typename R, int MODE, bool COMP, int THREADS, int KMAX>
 cudaError_t launch_tile_t(const StepArgs& a, cudaStream_t s) {
   auto k = k_step_tile<R, MODE, COMP, THREADS, KMAX>;
@@ -114,6 +209,14 @@ cudaError_t launch_tile_mode(int mode, const StepArgs& a, cudaStream_t s) {
 }
 
 }  // namespace
+
+cudaError_t launch_batch_step_tile(bool f64, int mode, const BatchArgs& b, cudaStream_t s) {
+  if (b.n_tiles <= 0) return cudaSuccess;
+  if (!b.s.cell_ln || !b.s.tile_info || !b.s.halo_id || !b.tile_mesh) return cudaErrorInvalidValue;
+  if (f64) return launch_tile_batch_mode<double, false>(mode, b, s);
+  if (b.s.lo) return launch_tile_batch_mode<float, true>(mode, b, s);
+  return launch_tile_batch_mode<float, false>(mode, b, s);
+}
 
 cudaError_t launch_step_tile(bool f64, int mode, const StepArgs& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;

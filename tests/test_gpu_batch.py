@@ -71,7 +71,7 @@ def solo_and_batch(items, prec, nsteps, scheme, t_stop=0.0, comp=True, variant=5
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 @pytest.mark.parametrize("scheme", ["fe", "rk2"])
-@pytest.mark.parametrize("variant", [5, 0])
+@pytest.mark.parametrize("variant", [5, 0, 6])
 def test_batch_equals_solo_bitwise(prec, scheme, variant):
     items = make_set(5)
     solo, batch, flat, tb = solo_and_batch(items, prec, 131, scheme, variant=variant)

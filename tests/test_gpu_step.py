@@ -415,3 +415,4 @@ def test_launch_chaining_leaves_results_unchanged(big_square, prec):
             g.close()
         assert outs[0][0] == outs[1][0]
         assert torch.equal(outs[0][1], outs[1][1]), v
+
