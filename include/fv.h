@@ -64,6 +64,10 @@ extern "C" {
 #define FV_SCHEME_FE 0  /* forward Euler, Eq. 6 and the update equation of Sec. 6.2.2 */
 #define FV_SCHEME_RK2 1 /* two-stage Heun (SSP-RK2) with the same dt; not in the paper */
 
+/* Wave speed in the Lax-Friedrichs dissipation (fv_mesh_set_wave_speed) */
+#define FV_WAVE_AVERAGE 0 /* |average normal velocity| + average sound speed (Sec. 6.2.2) */
+#define FV_WAVE_MAX 1     /* max over both sides of |normal velocity| + sound speed */
+
 typedef struct fv_mesh fv_mesh;
 typedef struct fv_batch fv_batch;
 typedef struct fv_closure fv_closure;
@@ -168,6 +172,18 @@ int fv_mesh_autotune(fv_mesh* mesh, const void* U, int32_t scheme, void* stream,
  * fv_step / fv_mesh_status return FV_ETIMEOUT; the state is then not valid.
  * Default 2^24.  A limit of 0 forces the timeout path (for tests). */
 int fv_mesh_set_wait_limit(fv_mesh* mesh, uint32_t polls);
+
+/* Wave speed of the dissipation term of Eq. 5.  FV_WAVE_AVERAGE (default) is
+ * the paper's: the absolute interface-average normal velocity plus the
+ * average sound speed.  FV_WAVE_MAX takes the larger one-sided
+ * |u_n| + c of the two cells (the Rusanov form).  The paper's averages can
+ * fall below the one-sided speeds in strong expansions, where the first-order
+ * update then loses positivity (the corner of the Mach 3 forward-facing step
+ * on fine meshes); the maximum keeps it positive under the same CFL bound.
+ * With FV_WAVE_MAX the step runs shape 0, 1 or 6 (shapes 2-5 run as 1);
+ * fv_step returns FV_EINVAL with a closure or two steps per launch, and
+ * fv_batch_create with such a mesh.  FV_EINVAL for an unknown mode. */
+int fv_mesh_set_wave_speed(fv_mesh* mesh, int32_t mode);
 
 /* Launch chaining of the step kernels (default 1 = on): each step kernel of
  * fv_step is launched with programmatic dependent launch, so the next step's

@@ -60,6 +60,8 @@ def _load():
             lib.orc_build_mesh.restype = ctypes.c_int
             lib.orc_build_mesh.argtypes = [ctypes.c_int64, _d, ctypes.c_int64, _i32, _i32,
                                            ctypes.c_int64, _i32, ctypes.c_int32, _i32, _d, _d]
+            lib.orc_set_wave_speed.restype = None
+            lib.orc_set_wave_speed.argtypes = [ctypes.c_int32]
             lib.orc_face_flux.restype = None
             lib.orc_face_flux.argtypes = [_d, _d, _d, ctypes.c_double, _d]
             lib.orc_ghost.restype = None
@@ -212,6 +214,13 @@ class Mesh:
 
 
 # -- single-face helpers -------------------------------------------------------
+def set_wave_speed(mode: str):
+    """Wave speed of the dissipation for every later oracle call: 'average'
+    (the paper's interface averages, the default) or 'max' (larger one-sided
+    |u_n| + c)."""
+    _load().orc_set_wave_speed({"average": 0, "max": 1}[mode])
+
+
 def face_flux(UL, UR, n, scale=1.0):
     UL, UR, n = _f64(UL), _f64(UR), _f64(n)
     F = np.empty(4, np.float64)

@@ -253,6 +253,13 @@ static void orc_to_face_frame(const double* U, double nx, double ny, orc_face_st
   s->c = orc_sound_speed(s->rho, s->p);
 }
 
+/* Wave speed of the dissipation: 0 = the paper's interface averages (reading */
+/* R2), 1 = the larger one-sided |u_n| + c (Rusanov), an alternative reading  */
+/* of the same passage kept for sensitivity checks.  Process-wide setting.    */
+static int orc_wave_mode = 0;
+
+void orc_set_wave_speed(int32_t mode) { orc_wave_mode = mode; }
+
 void orc_face_flux(const double* UL, const double* UR, const double* n, double scale, double* F) {
   double len = sqrt(n[0] * n[0] + n[1] * n[1]);
   double nx = n[0] / len, ny = n[1] / len;
@@ -261,7 +268,13 @@ void orc_face_flux(const double* UL, const double* UR, const double* n, double s
   orc_to_face_frame(UR, nx, ny, &R);
   double ubar = 0.5 * (L.un + R.un);
   double cbar = 0.5 * (L.c + R.c);
-  double a = scale * (fabs(ubar) + cbar);
+  double a;
+  if (orc_wave_mode == 0) {
+    a = scale * (fabs(ubar) + cbar);
+  } else {
+    double aL = fabs(L.un) + L.c, aR = fabs(R.un) + R.c;
+    a = scale * (aL > aR ? aL : aR);
+  }
   /* Eq. 7a-7d, face frame */
   double f_rho = 0.5 * (L.rho * L.un + R.rho * R.un) - 0.5 * a * (R.rho - L.rho);
   double f_mn = 0.5 * ((L.rho * L.un * L.un + L.p) + (R.rho * R.un * R.un + R.p)) -

@@ -71,6 +71,7 @@ def load():
             "fv_mesh_set_wait_limit": (ctypes.c_int, [_vp, ctypes.c_uint32]),
             "fv_mesh_set_blocking": (ctypes.c_int, [_vp, _i32, _i32, _i32]),
             "fv_mesh_set_launch_chaining": (ctypes.c_int, [_vp, _i32]),
+            "fv_mesh_set_wave_speed": (ctypes.c_int, [_vp, _i32]),
             "fv_mesh_tile_halo": (ctypes.c_int, [_vp, _i32, _i64, _vp, _i64, _P(_i64), _P(_i64)]),
             "fv_mesh_autotune": (ctypes.c_int, [_vp, _vp, _i32, _vp, _P(_i32), _P(_dbl)]),
             "fv_step": (ctypes.c_int, [_vp, _vp, _i64, _dbl, _dbl, _i32, _vp, _vp, _P(_dbl)]),
@@ -231,6 +232,11 @@ class Mesh:
 
     def set_wait_limit(self, polls: int):
         _check(load().fv_mesh_set_wait_limit(self._h, int(polls)))
+
+    def set_wave_speed(self, mode: str):
+        """'average' (the paper's interface averages, default) or 'max'
+        (larger one-sided |u_n| + c, Rusanov)."""
+        _check(load().fv_mesh_set_wave_speed(self._h, {"average": 0, "max": 1}[mode]))
 
     def set_launch_chaining(self, enable: bool):
         """Programmatic dependent launch of the step kernels (default on)."""

@@ -116,6 +116,7 @@ struct fv_mesh {
   int pair_tile = 1024;
   int pair_staged = 0;  // 1: bulk-copy staged two-step kernel
   bool chained = true;  // programmatic dependent launch of the step kernels
+  int wave = FV_WAVE_AVERAGE;  // wave speed of the dissipation (fv_mesh_set_wave_speed)
   int tiles_built = 0;  // tile size of the arrays below (0: none)
   uint2* d_cell_ln = nullptr;
   int* d_tile_info = nullptr;
@@ -290,6 +291,7 @@ fv::StepArgs base_args(const fv_mesh* m) {
   a.wait_limit = m->wait_limit;
   a.drain_limit = fv::kDefaultWaitLimit;
   a.chained = m->chained;
+  a.wave = m->wave == FV_WAVE_MAX ? fv::kWaveMax : fv::kWaveAverage;
   if (m->tiles_built) {
     a.cell_ln = m->d_cell_ln;
     a.tile_info = m->d_tile_info;
@@ -604,6 +606,15 @@ int fv_mesh_tile_halo(const fv_mesh* mesh, int32_t tile_cells, int64_t tile, int
   });
 }
 
+int fv_mesh_set_wave_speed(fv_mesh* mesh, int32_t mode) {
+  return guarded([&] {
+    check_mesh(mesh);
+    if (mode != FV_WAVE_AVERAGE && mode != FV_WAVE_MAX) invalid("unknown wave-speed mode");
+    mesh->wave = mode;
+    mesh->drop_graph();
+  });
+}
+
 int fv_mesh_set_launch_chaining(fv_mesh* mesh, int32_t enable) {
   return guarded([&] {
     check_mesh(mesh);
@@ -732,6 +743,8 @@ int fv_step(fv_mesh* mesh, void* U, int64_t nsteps, double cfl, double t_stop, i
     if (closure && mesh->f64()) invalid("the learned closure runs on FV_F32 meshes only");
     if (mesh->blocking == 2 && (scheme != FV_SCHEME_FE || closure))
       invalid("two steps per launch apply to forward Euler without a closure");
+    if (mesh->wave != FV_WAVE_AVERAGE && (closure || mesh->blocking == 2))
+      invalid("the maximum wave speed runs without a closure, one step per launch");
     if (!U && nsteps > 0 && mesh->h.n > 0) invalid("null state");
     cudaStream_t s = as_stream(stream);
     ensure_device(mesh, s);
@@ -792,6 +805,8 @@ int fv_residual(fv_mesh* mesh, const void* U, void* R, const fv_closure* closure
     if (closure && mesh->f64()) invalid("the learned closure runs on FV_F32 meshes only");
     if (mesh->h.n == 0) return;
     if (!U || !R) invalid("null state or residual");
+    if (closure && mesh->wave != FV_WAVE_AVERAGE)
+      invalid("the maximum wave speed runs without a closure");
     if (U == R) invalid("R must not alias U");
     cudaStream_t s = as_stream(stream);
     ensure_device(mesh, s);
@@ -1164,6 +1179,7 @@ int fv_batch_create(fv_mesh* const* meshes, int32_t n_meshes, fv_batch** out) {
         const fv_mesh* m = meshes[k];
         if (!m) invalid("null mesh in batch");
         if (m->precision != b->precision) invalid("all meshes of a batch need one precision");
+        if (m->wave != FV_WAVE_AVERAGE) invalid("batches use the averaged wave speed");
         const int64_t padded = (m->h.n + fv::kBlock - 1) / fv::kBlock * fv::kBlock;
         b->offsets[k + 1] = b->offsets[k] + padded;
       }

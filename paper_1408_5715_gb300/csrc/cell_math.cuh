@@ -166,14 +166,22 @@ __device__ __forceinline__ rec_t<R> neighbour_state(const rec_t<R>& UL, int nb, 
 
 // Flux of one face given both states and their primitives; s scales the
 // dissipation (the learned closure; SCALED = false is the paper's flux).
-template <typename R, bool SCALED>
+// WAVE selects the wave speed of the dissipation: kWaveAverage the paper's
+// interface averages |u-bar_n| + c-bar; kWaveMax the larger one-sided speed
+// max(|u_nL| + c_L, |u_nR| + c_R) (Rusanov), which keeps the first-order
+// update positive in strong expansions.  Both are symmetric in L <-> R.
+template <typename R, bool SCALED, int WAVE = kWaveAverage>
 __device__ __forceinline__ void face_flux_acc(const rec_t<R>& UL, const Prim<R>& L,
                                               const rec_t<R>& UR, const Prim<R>& W, R nx, R ny,
                                               R len, R s, R acc[4]) {
   const R qL = fma_(L.u, nx, mul(L.v, ny));
   const R qR = fma_(W.u, nx, mul(W.v, ny));
-  // a = |n| (|u-bar_n| + c-bar) / 2
-  R na = mul(R(-0.25), fma_(len, add(L.c, W.c), fabs(add(qL, qR))));
+  // a = |n| (wave speed) / 2
+  R na;
+  if (WAVE == kWaveAverage)
+    na = mul(R(-0.25), fma_(len, add(L.c, W.c), fabs(add(qL, qR))));
+  else
+    na = mul(R(-0.5), fmax(fma_(len, L.c, fabs(qL)), fma_(len, W.c, fabs(qR))));
   if (SCALED) na = mul(s, na);
   const R h = R(0.5);
   acc[0] = add(acc[0], fma_(na, sub(UR.x, UL.x), mul(h, fma_(UL.x, qL, mul(UR.x, qR)))));
@@ -185,14 +193,14 @@ __device__ __forceinline__ void face_flux_acc(const rec_t<R>& UL, const Prim<R>&
                             mul(h, fma_(add(UL.w, L.p), qL, mul(add(UR.w, W.p), qR)))));
 }
 
-template <typename R>
+template <typename R, int WAVE = kWaveAverage>
 __device__ __forceinline__ R add_face_flux(const rec_t<R>& UL, const Prim<R>& L, int nb, R nx,
                                            R ny, const rec_t<R>* __restrict__ Ucur,
                                            const R* uinf, R acc[4]) {
   const rec_t<R> UR = neighbour_state<R>(UL, nb, nx, ny, Ucur, uinf);
   const Prim<R> W = primitive<R>(UR);
   const R len = face_len<R>(nx, ny);
-  face_flux_acc<R, false>(UL, L, UR, W, nx, ny, len, R(1), acc);
+  face_flux_acc<R, false, WAVE>(UL, L, UR, W, nx, ny, len, R(1), acc);
   return len;
 }
 

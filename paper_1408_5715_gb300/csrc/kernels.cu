@@ -32,16 +32,16 @@ namespace fv {
 
 namespace {
 
-template <typename R, int MODE, bool COMP>
+template <typename R, int MODE, bool COMP, int WAVE = kWaveAverage>
 __device__ __forceinline__ void update_cell(const StepArgs& a, const rec_t<R>* __restrict__ U,
                                             rec_t<R>* out, int64_t i, const CellIn<R>& c, R dt,
                                             const R* uinf, R& bmin, bool& ok) {
   const rec_t<R>& UL = c.U;
   const Prim<R> L = primitive<R>(UL);
   R acc[4] = {R(0), R(0), R(0), R(0)};
-  R perim = add_face_flux<R>(UL, L, c.n0, c.g0.x, c.g0.y, U, uinf, acc);
-  perim = add(perim, add_face_flux<R>(UL, L, c.n1, c.g0.z, c.g0.w, U, uinf, acc));
-  perim = add(perim, add_face_flux<R>(UL, L, c.n2, c.g1.x, c.g1.y, U, uinf, acc));
+  R perim = add_face_flux<R, WAVE>(UL, L, c.n0, c.g0.x, c.g0.y, U, uinf, acc);
+  perim = add(perim, add_face_flux<R, WAVE>(UL, L, c.n1, c.g0.z, c.g0.w, U, uinf, acc));
+  perim = add(perim, add_face_flux<R, WAVE>(UL, L, c.n2, c.g1.x, c.g1.y, U, uinf, acc));
   finish_cell<R, MODE, COMP>(a, out, i, c, acc, perim, dt, bmin, ok);
 }
 
@@ -58,7 +58,7 @@ __device__ __forceinline__ void update_cell(const StepArgs& a, const rec_t<R>* _
 constexpr bool var_persistent(int v) { return v == 1 || v == 2; }
 constexpr int var_min_blocks(int v) { return v == 2 ? 4 : v == 3 ? 6 : v == 4 ? 8 : 1; }
 
-template <typename R, int MODE, bool COMP, int VAR>
+template <typename R, int MODE, bool COMP, int VAR, int WAVE>
 __global__ void __launch_bounds__(kBlock, var_min_blocks(VAR)) k_step(StepArgs a) {
   chain_entry();
   const rec_t<R>* __restrict__ U = static_cast<const rec_t<R>*>(a.U);
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(kBlock, var_min_blocks(VAR)) k_step(StepArgs a
     if (i < a.n) {
       CellIn<R> cur;
       load_cell<R, MODE, COMP>(a, U, geom, i, cur);
-      update_cell<R, MODE, COMP>(a, U, out, i, cur, dtR, far_field<R>(a), bmin, ok);
+      update_cell<R, MODE, COMP, WAVE>(a, U, out, i, cur, dtR, far_field<R>(a), bmin, ok);
     }
   } else {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(kBlock, var_min_blocks(VAR)) k_step(StepArgs a
     for (; i < a.n; i += stride) {
       const int64_t j = i + stride;
       if (j < a.n) load_cell<R, MODE, COMP>(a, U, geom, j, nxt);
-      update_cell<R, MODE, COMP>(a, U, out, i, cur, dtR, far_field<R>(a), bmin, ok);
+      update_cell<R, MODE, COMP, WAVE>(a, U, out, i, cur, dtR, far_field<R>(a), bmin, ok);
       cur = nxt;
     }
   }
@@ -334,9 +334,9 @@ unsigned resident_blocks(K kernel) {
   return (unsigned)cached;
 }
 
-template <typename R, int MODE, bool COMP, int VAR>
+template <typename R, int MODE, bool COMP, int VAR, int WAVE = kWaveAverage>
 cudaError_t launch_one(const StepArgs& a, cudaStream_t s) {
-  auto kernel = k_step<R, MODE, COMP, VAR>;
+  auto kernel = k_step<R, MODE, COMP, VAR, WAVE>;
   const int64_t want = a.n > 0 ? (a.n + kBlock - 1) / kBlock : 1;  // a time step always runs its scalars
   unsigned g = (unsigned)want;
   if (var_persistent(VAR)) {
@@ -348,6 +348,9 @@ cudaError_t launch_one(const StepArgs& a, cudaStream_t s) {
 
 template <typename R, int MODE, bool COMP>
 cudaError_t launch_var(int var, const StepArgs& a, cudaStream_t s) {
+  if (a.wave == kWaveMax)  // the Rusanov wave speed is built for shapes 0 and 1
+    return var == 0 ? launch_one<R, MODE, COMP, 0, kWaveMax>(a, s)
+                    : launch_one<R, MODE, COMP, 1, kWaveMax>(a, s);
   switch (var) {
     case 0: return launch_one<R, MODE, COMP, 0>(a, s);
     case 1: return launch_one<R, MODE, COMP, 1>(a, s);
@@ -365,7 +368,9 @@ cudaError_t launch_step_t(int mode, int var, const StepArgs& a, cudaStream_t s) 
     case kModeFE: return launch_var<R, kModeFE, COMP>(var, a, s);
     case kModeRK2a: return launch_var<R, kModeRK2a, COMP>(var, a, s);
     case kModeRK2b: return launch_var<R, kModeRK2b, COMP>(var, a, s);
-    case kModeResidual: return launch_one<R, kModeResidual, false, 0>(a, s);
+    case kModeResidual:
+      return a.wave == kWaveMax ? launch_one<R, kModeResidual, false, 0, kWaveMax>(a, s)
+                                : launch_one<R, kModeResidual, false, 0>(a, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -373,6 +378,7 @@ cudaError_t launch_step_t(int mode, int var, const StepArgs& a, cudaStream_t s) 
 }  // namespace
 
 cudaError_t launch_step(bool f64, int mode, int variant, const StepArgs& a, cudaStream_t s) {
+  if (variant == 5 && a.wave == kWaveMax) variant = 1;  // the staged shape has the averages only
   if (variant == 5 && mode != kModeResidual && a.n > 0) return launch_step_tma(f64, mode, a, s);
   if (variant == kTileVariant && a.cell_ln) return launch_step_tile(f64, mode, a, s);
   if (variant == 5 || variant == kTileVariant) variant = 0;

@@ -11,6 +11,10 @@ namespace fv {
 constexpr int kBlock = 256;        // threads per block of the cell kernels
 constexpr int kTotalsBlocks = 1024; // fixed grid of the deterministic totals
 
+// Wave speed of the Lax-Friedrichs dissipation (StepArgs::wave).
+constexpr int kWaveAverage = 0;  // interface averages (Sec. 6.2.2, the default)
+constexpr int kWaveMax = 1;      // larger one-sided speed (Rusanov)
+
 // Step modes of the fused cell kernel.
 enum StepMode : int {
   kModeFE = 0,       // U^{n+1} = U^n + dt R(U^n), plus the next-dt bound
@@ -78,6 +82,8 @@ struct StepArgs {
   int t1_cap;
   // launch as part of a programmatic chain (launch_util.cuh)
   bool chained;
+  // kWaveAverage or kWaveMax (shapes 0, 1 and 6; the others run shape 1)
+  int wave;
 };
 
 // Arguments of the batched step kernel: many meshes concatenated into one

@@ -25,7 +25,7 @@ __device__ __forceinline__ Prim<R> rec_prim(const rec_t<R>& p) {
 }
 
 // One face of a cell whose neighbour state and primitives are in shared memory.
-template <typename R>
+template <typename R, int WAVE = kWaveAverage>
 __device__ __forceinline__ R smem_face(const rec_t<R>& UL, const Prim<R>& L, unsigned v, R nx, R ny,
                                        const rec_t<R>* sU, const rec_t<R>* sP, const R* uinf,
                                        R acc[4]) {
@@ -39,18 +39,18 @@ __device__ __forceinline__ R smem_face(const rec_t<R>& UL, const Prim<R>& L, uns
     W = primitive<R>(UR);
   }
   const R len = face_len<R>(nx, ny);
-  face_flux_acc<R, false>(UL, L, UR, W, nx, ny, len, R(1), acc);
+  face_flux_acc<R, false, WAVE>(UL, L, UR, W, nx, ny, len, R(1), acc);
   return len;
 }
 
 // Residual sum of one cell (faces in the order 0, 1, 2) and its perimeter.
-template <typename R>
+template <typename R, int WAVE = kWaveAverage>
 __device__ __forceinline__ R cell_fluxes(const rec_t<R>& g0, const rec_t<R>& g1, uint2 ln,
                                          const rec_t<R>& UL, const Prim<R>& L, const rec_t<R>* sU,
                                          const rec_t<R>* sP, const R* uinf, R acc[4]) {
-  R perim = smem_face<R>(UL, L, ln.x & 0xffffu, g0.x, g0.y, sU, sP, uinf, acc);
-  perim = add(perim, smem_face<R>(UL, L, ln.x >> 16, g0.z, g0.w, sU, sP, uinf, acc));
-  perim = add(perim, smem_face<R>(UL, L, ln.y, g1.x, g1.y, sU, sP, uinf, acc));
+  R perim = smem_face<R, WAVE>(UL, L, ln.x & 0xffffu, g0.x, g0.y, sU, sP, uinf, acc);
+  perim = add(perim, smem_face<R, WAVE>(UL, L, ln.x >> 16, g0.z, g0.w, sU, sP, uinf, acc));
+  perim = add(perim, smem_face<R, WAVE>(UL, L, ln.y, g1.x, g1.y, sU, sP, uinf, acc));
   return perim;
 }
 

@@ -23,7 +23,7 @@ namespace fv {
 
 namespace {
 
-template <typename R, int MODE, bool COMP, int THREADS, int KMAX>
+template <typename R, int MODE, bool COMP, int THREADS, int KMAX, int WAVE>
 __global__ void __launch_bounds__(THREADS) k_step_tile(StepArgs a) {
   chain_entry();
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -64,8 +64,8 @@ __global__ void __launch_bounds__(THREADS) k_step_tile(StepArgs a) {
       if (COMP && MODE == kModeRK2b) c.lo_stage = a.lo_stage[i];
       const uint2 ln = __ldg(a.cell_ln + i);
       R acc[4] = {R(0), R(0), R(0), R(0)};
-      const R perim =
-          cell_fluxes<R>(c.g0, c.g1, ln, c.U, rec_prim<R>(sP[e]), sU, sP, far_field<R>(a), acc);
+      const R perim = cell_fluxes<R, WAVE>(c.g0, c.g1, ln, c.U, rec_prim<R>(sP[e]), sU, sP,
+                                           far_field<R>(a), acc);
       finish_cell<R, MODE, COMP>(a, out, i, c, acc, perim, dtR, bmin, ok);
     }
   }
@@ -179,7 +179,8 @@ cudaError_t launch_tile_batch_mode(int mode, const BatchArgs& b, cudaStream_t s)
 
 template <typename R, int MODE, bool COMP, int THREADS, int KMAX>
 cudaError_t launch_tile_t(const StepArgs& a, cudaStream_t s) {
-  auto k = k_step_tile<R, MODE, COMP, THREADS, KMAX>;
+  auto k = a.wave == kWaveMax ? k_step_tile<R, MODE, COMP, THREADS, KMAX, kWaveMax>
+                              : k_step_tile<R, MODE, COMP, THREADS, KMAX, kWaveAverage>;
   const size_t smem = tile_smem_bytes(sizeof(R) == 8, a.t1_cap);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -416,3 +416,55 @@ def test_launch_chaining_leaves_results_unchanged(big_square, prec):
         assert outs[0][0] == outs[1][0]
         assert torch.equal(outs[0][1], outs[1][1]), v
 
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_max_wave_speed_matches_oracle_on_all_shapes(orc, prec):
+    # the Rusanov wave speed on the Mach 3 step (far-field inflow,
+    # extrapolation outflow, slip walls), 200 steps: FP64 against the oracle
+    # with the same reading, every shape bitwise the same, FP32 close to FP64
+    mi = W.forward_step(12, 42, 9, 36, seed=6)
+    prim = W.mach3_inflow()
+    U0 = W.uniform_state(mi.n_tri, prim)
+    outs = []
+    for v in (0, 1, 3, 6):
+        g = B.Mesh.from_input(mi, prec)
+        g.set_freestream(*prim)
+        perm = g.renumber("hilbert")
+        g.set_wave_speed("max")
+        g.set_variant(v)
+        U = dev(U0[perm], torch.float64 if prec == "f64" else torch.float32)
+        t = g.step(U, 200, 0.4)
+        out = np.empty_like(U0)
+        out[perm] = U.double().cpu().numpy()
+        outs.append((t, out))
+        g.close()
+    for t, out in outs[1:]:
+        assert t == outs[0][0]
+        assert np.array_equal(out, outs[0][1])
+    orc.set_wave_speed("max")
+    try:
+        om = orc.Mesh(mi.xy, mi.tri, mi.canon, mi.bnd, mi.default_bc, W.conserved(*prim))
+        Uo, to, _, bad = om.run(U0, 200, 0.4)
+    finally:
+        orc.set_wave_speed("average")
+    assert not bad
+    if prec == "f64":
+        assert outs[0][0] == pytest.approx(to, rel=1e-13)
+        assert rel_err_max(outs[0][1], Uo) <= 1e-12
+    else:
+        assert rel_l2(outs[0][1][:, 0], Uo[:, 0]) <= 1e-5
+
+
+def test_max_wave_speed_refuses_closure_and_pairs():
+    mi = W.periodic_square(16, 8, seed=2)
+    g = B.Mesh.from_input(mi, "f32")
+    g.set_wave_speed("max")
+    U = dev(W.uniform_state(mi.n_tri, (1.0, 0.3, 0.0, 1.0)), torch.float32)
+    g.set_blocking(2)
+    with pytest.raises(B.FVError, match="wave"):
+        g.step(U, 2, 0.4)
+    g.set_blocking(1)
+    g.step(U, 2, 0.4)
+    with pytest.raises(B.FVError):
+        B.Batch([g])

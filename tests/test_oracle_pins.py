@@ -276,6 +276,109 @@ def test_rotation_invariance(orc):
     np.testing.assert_allclose(R1[:, 1:3], R0[:, 1:3] @ Rm.T, atol=1e-12 * scale[1:3].max())
 
 
+@pytest.fixture
+def max_wave(orc):
+    orc.set_wave_speed("max")
+    try:
+        yield orc
+    finally:
+        orc.set_wave_speed("average")
+
+
+def test_max_wave_speed_two_cell_flux_by_hand(max_wave):
+    # the two-cell case of the averaged pin with the one-sided maximum:
+    # both cells are at rest, so the wave speed is max(c_L, c_R) = sqrt(1.4);
+    # |n| = sqrt(2), jumps rho: -0.875, E: -2.25; pressure flux 1.1/2 n
+    orc = max_wave
+    UL = np.array([1.0, 0.0, 0.0, 2.5])
+    UR = np.array([0.125, 0.0, 0.0, 0.25])
+    F = orc.face_flux(UL, UR, np.array([-1.0, 1.0]))
+    a_n = math.sqrt(1.4) * math.sqrt(2.0)
+    expect = [0.5 * a_n * 0.875, -0.55, 0.55, 0.5 * a_n * 2.25]
+    np.testing.assert_allclose(F, expect, rtol=1e-15, atol=1e-15)
+    # swapped cells and normal: the exact negation
+    G_ = orc.face_flux(UR, UL, np.array([1.0, -1.0]))
+    assert np.array_equal(G_, -F)
+
+
+def test_max_wave_speed_at_least_the_average(orc):
+    # the dissipation coefficient of the maximum form is never below the
+    # averaged one (|a + b| / 2 + (c + d) / 2 <= max(|a| + c, |b| + d))
+    rng = np.random.default_rng(21)
+    for _ in range(200):
+        UL, UR = random_state(rng), random_state(rng)
+        n = rng.normal(size=2)
+        orc.set_wave_speed("average")
+        Fa0 = orc.face_flux(UL, UR, n, scale=0.0)
+        Fa1 = orc.face_flux(UL, UR, n)
+        orc.set_wave_speed("max")
+        try:
+            Fm1 = orc.face_flux(UL, UR, n)
+        finally:
+            orc.set_wave_speed("average")
+        jump = UR[0] - UL[0]
+        if abs(jump) > 1e-3:
+            da = (Fa1[0] - Fa0[0]) / -jump  # = |n| a_avg / 2
+            dm = (Fm1[0] - Fa0[0]) / -jump  # = |n| a_max / 2
+            assert dm >= da * (1 - 1e-12)
+
+
+def test_double_rarefaction_positivity(orc):
+    # two halves of a strip moving apart at twice the sound speed: the exact
+    # solution keeps a positive pressure (no vacuum below 2 c / (gamma - 1)
+    # = 5 c on each side).  With the paper's averaged wave speed the central
+    # face sees u-bar_n = 0 and the update drives the pressure negative within
+    # a few steps; the one-sided maximum keeps it positive.
+    mi = W.shock_tube_strip(40, 2, seed=1)
+    cen = mi.centroids()
+    c = math.sqrt(G)
+    u = np.where(cen[:, 0] < 0.5, -2.0 * c, 2.0 * c)
+    U0 = W.conserved(np.ones(mi.n_tri), u, np.zeros(mi.n_tri), np.ones(mi.n_tri))
+    results = {}
+    for mode in ("average", "max"):
+        orc.set_wave_speed(mode)
+        try:
+            om = build(orc, mi, W.conserved(1.0, 0.0, 0.0, 1.0))
+            results[mode] = om.run(U0, 40, 0.4)
+        finally:
+            orc.set_wave_speed("average")
+    assert results["average"][3]  # lost positivity
+    Um, _, steps, bad = results["max"]
+    assert not bad and steps == 40
+    assert prim(Um)[3].min() > 0.0 and Um[:, 0].min() > 0.0
+
+
+def test_vortex_is_advected_with_the_free_stream(orc):
+    # an isentropic vortex in a uniform stream is a steady solution of the
+    # Euler equations translated with velocity u_inf: after time t its centre
+    # (the density minimum) sits at x0 + u_inf t (periodically).  The first-
+    # order scheme damps the vortex but must carry it at the stream speed.
+    mi = W.periodic_square(64, 32, seed=4)
+    cen = mi.centroids()
+    mach = 0.5
+    u_inf = mach * math.sqrt(G)
+    U0 = W.isentropic_vortex(cen, mach=mach, beta=5.0)
+    mesh = build(orc, mi, W.conserved(1.0, u_inf, 0.0, 1.0))
+    t_end = 0.5 / u_inf  # half a flow-through: the centre moves to x = 1.0 = 0.0
+    U, t, _, bad = mesh.run(U0, 10 ** 6, 0.4, t_stop=t_end)
+    assert not bad and t == pytest.approx(t_end, rel=1e-12)
+    rho = U[:, 0]
+    deficit = np.clip(rho.max() - rho, 0.0, None)
+    # deficit-weighted centre, x taken on the circle (periodic)
+    ang = 2.0 * math.pi * cen[:, 0]
+    xc = (math.atan2((deficit * np.sin(ang)).sum(), (deficit * np.cos(ang)).sum())
+          / (2.0 * math.pi)) % 1.0
+    yc = (deficit * cen[:, 1]).sum() / deficit.sum()
+    x_expect = (0.5 + u_inf * t_end) % 1.0
+    dx, dy = 1.0 / 64, 1.0 / 32
+    gap = min(abs(xc - x_expect), 1.0 - abs(xc - x_expect))
+    assert gap <= 2 * dx and abs(yc - 0.5) <= 2 * dy
+    # the minimum has not been smeared away: the vortex is still there
+    assert rho.min() < 0.95 * rho.max()
+    # a wrong stream speed (a dropped or doubled advection term) is caught
+    assert min(abs(xc - 0.5), 1.0 - abs(xc - 0.5)) > 10 * dx
+
+
 def test_dt_matches_brute_force(orc, c1):
     mi, mesh = c1
     U = W.isentropic_vortex(mi.centroids(), mach=0.5)
