@@ -67,6 +67,8 @@ def parse_args():
                    help="cells per tile with --blocking 2")
     p.add_argument("--staged", action="store_true",
                    help="with --blocking 2: tile records by bulk copies (512 or 1024 cells)")
+    p.add_argument("--closure", action="store_true",
+                   help="step with the learned dissipation scale (untrained initial weights)")
     p.add_argument("--variant", type=int, default=None,
                    help="force a step-kernel shape instead of autotuning")
     return p.parse_args()
@@ -214,7 +216,7 @@ def choose_variant(m, U, variant, scheme="fe"):
 
 
 def timed_loop(m, U, U0dev, time_steps, steps, warmup, scheme, cfl=0.4, flush=None,
-               dist=None):
+               dist=None, closure=None):
     """Runs warmup + steps benchmark steps; returns per-step device times (s)."""
     import torch
     times = []
@@ -228,7 +230,7 @@ def timed_loop(m, U, U0dev, time_steps, steps, warmup, scheme, cfl=0.4, flush=No
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
-        m.step(U, time_steps, cfl, scheme=scheme, sync=False)
+        m.step(U, time_steps, cfl, scheme=scheme, closure=closure, sync=False)
         m.totals(U)  # FP64 totals; synchronises
         e1.record()
         torch.cuda.synchronize()
@@ -272,6 +274,12 @@ def run_ours(args):
     U0p = U0[perm]
     U0dev = torch.tensor(U0p, dtype=tdt, device="cuda")
     U = torch.empty_like(U0dev)
+    closure = None
+    if args.closure:
+        if prec != "f32" or args.blocking != 1:
+            raise SystemExit("--closure runs FP32, one step per launch")
+        from paper_1408_5715_gb300 import closure_training as CT
+        closure = B.Closure(CT.initial_theta(1, 0.3))
     if args.blocking == 2:
         if prec != "f32" or args.scheme != "fe":
             raise SystemExit("--blocking 2 runs FP32 forward Euler")
@@ -282,7 +290,7 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     with ClockSampler(gpu_smi_id()) as clk:
         times = timed_loop(m, U, U0dev, S, args.steps, args.warmup, args.scheme, flush=flush,
-                           dist=dist)
+                           dist=dist, closure=closure)
     total = sum(times)
     if dist is not None:
         t = torch.tensor([total], device="cuda", dtype=torch.float64)
@@ -301,12 +309,14 @@ def run_ours(args):
     else:
         algo = ALGO_BYTES[prec]
         kbytes = ALGO_BYTES[prec] + (COMP_BYTES if prec == "f32" else 0)
-        kname = (f"k_step<{'float' if prec == 'f32' else 'double'}, "
+        kfun = ("k_step_closure" if args.closure else
+                {5: "k_step_tma", 6: "k_step_tile"}.get(tune["variant"], "k_step"))
+        kname = (f"{kfun}<{'float' if prec == 'f32' else 'double'}, "
                  f"{'RK2' if stages == 2 else 'FE'}, "
-                 f"{'compensated' if prec == 'f32' else 'plain'}, variant {tune['variant']}>")
+                 f"{'compensated' if prec == 'f32' else 'plain'}, shape {tune['variant']}>")
     achieved = algo * n / avg_launch / 1e9  # GB/s of one step-kernel launch
     U_final = U.double().cpu().numpy()
-    e2e = e2e_leg(args, m, U0p, n, S, dist)
+    e2e = e2e_leg(args, m, U0p, n, S, dist, closure)
     out = {
         "metric": "cell updates/s",
         "value": value,
@@ -324,6 +334,8 @@ def run_ours(args):
                    "time_steps_per_step": S, "scheme": args.scheme, "cfl": 0.4, "order": order,
                    "dt": "CFL bound of the state at the start of each pair" if args.blocking == 2
                          else "CFL bound of the state at the start of each step",
+                   "closure": "learned dissipation scale, initial weights" if args.closure
+                              else None,
                    "parallelism": f"replicas{world}" if world > 1 else "single",
                    "kernel_shape": tune,
                    "l2": "256 MB written between steps (L2 flushed); state+geometry "
@@ -351,7 +363,7 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def e2e_leg(args, m, U0p, n, S, dist=None):
+def e2e_leg(args, m, U0p, n, S, dist=None, closure=None):
     """The same metric end to end through the public API: every step copies
     the state in from pinned host memory, steps, reads the totals and copies
     the state back."""
@@ -369,7 +381,7 @@ def e2e_leg(args, m, U0p, n, S, dist=None):
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
         Ud.copy_(host_in, non_blocking=True)
-        m.step(Ud, S, 0.4, scheme=args.scheme, sync=False)
+        m.step(Ud, S, 0.4, scheme=args.scheme, closure=closure, sync=False)
         tot = m.totals(Ud)
         host_out.copy_(Ud, non_blocking=True)
         e1.record()
@@ -627,18 +639,26 @@ def learned_leg(B, time_steps=2000):
     mi = W.channel_bump(625, 200, seed=5)
     m = B.Mesh.from_input(mi, "f32")
     m.set_freestream(*W.freestream(0.5))
-    m.renumber("rcm")
+    m.renumber("hilbert")
     cl = B.Closure(CT.initial_theta(1, 0.3))
     cost = CT.step_cost(m, cl, steps=time_steps)
     n = mi.n_tri
-    # tensor-core work per face evaluation: layer 1 (K padded 8 -> 16) and layer 2
+    # MLP rows per step: a face shared by two cells of one warp (32 consecutive
+    # cells) is evaluated once
+    nbr, _, _ = m.export()
+    cell = np.arange(n)[:, None]
+    base = (cell // 32) * 32
+    shared = int(((nbr >= base) & (nbr < cell)).sum())
+    rows = 3 * n - shared
+    # tensor-core work per MLP row: layer 1 (K padded 8 -> 16) and layer 2
     mma_flops = 2 * (16 * 32 + 32 * 32)
-    res = {"cells": n, "time_steps": time_steps, "us_per_step_plain": cost["plain"],
-           "us_per_step_learned": cost["learned"],
+    res = {"cells": n, "order": "hilbert", "time_steps": time_steps,
+           "us_per_step_plain": cost["plain"], "us_per_step_learned": cost["learned"],
            "value": n / (cost["learned"] * 1e-6), "unit": "cell-updates/s",
            "overhead": cost["learned"] / cost["plain"],
-           "mma_flops_per_cell": 3 * mma_flops,
-           "mma_tflops": 3 * mma_flops * n / (cost["learned"] * 1e-6) / 1e12,
+           "mlp_rows_per_cell": rows / n,
+           "mma_flops_per_cell": mma_flops * rows / n,
+           "mma_tflops": mma_flops * rows / (cost["learned"] * 1e-6) / 1e12,
            "kernel": "k_step_closure<FE, compensated> (mma.sync m16n8k16 bf16)"}
     m.close()
     cl.close()

@@ -161,8 +161,10 @@ int fv_mesh_set_variant(fv_mesh* mesh, int32_t variant);
  * fastest for later fv_step calls and reports it in *best (nullable);
  * us_per_step (nullable, host, [7]) receives the measured microseconds per
  * step of each shape (infinity for shape 6 when its tiles do not fit).
- * Allocates and frees one state-sized device buffer and synchronises the
- * stream. */
+ * Shape 6 is timed with tiles of 512, 1024 and 2048 cells and reported at its
+ * best; when it wins, that tile size is kept (the tile size is shared with
+ * fv_mesh_set_blocking).  Allocates and frees one state-sized device buffer
+ * and synchronises the stream. */
 int fv_mesh_autotune(fv_mesh* mesh, const void* U, int32_t scheme, void* stream, int32_t* best,
                      double* us_per_step);
 

@@ -648,25 +648,15 @@ int fv_mesh_autotune(fv_mesh* mesh, const void* U, int32_t scheme, void* stream,
     FV_CUDA(cudaMalloc(&tmp, n * mesh->rec_bytes()));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     double times[fv::kStepVariants];
-    const int keep = mesh->variant;
+    const int keep = mesh->variant, keep_tile = mesh->pair_tile;
+    int best_tile = keep_tile;
     try {
       FV_CUDA(cudaEventCreate(&e0));
       FV_CUDA(cudaEventCreate(&e1));
       // a negligible fixed dt: the kernels do their full work, the state barely moves
       const double cfl = -1e-30;
       const int64_t steps = std::max<int64_t>(8, std::min<int64_t>(64, (int64_t)(4e7 / (double)n)));
-      for (int v = 0; v < fv::kStepVariants; ++v) {
-        mesh->variant = v;
-        if (v == fv::kTileVariant) {
-          // tiles that do not fit (a long-band order) leave this shape out
-          try {
-            ensure_tiles(mesh, s);
-            check_tile_smem(mesh, fv::tile_smem_bytes(mesh->f64(), mesh->p_t1_cap));
-          } catch (const fv::Error&) {
-            times[v] = INFINITY;
-            continue;
-          }
-        }
+      auto time_shape = [&]() {
         FV_CUDA(cudaMemcpyAsync(tmp, U, n * mesh->rec_bytes(), cudaMemcpyDeviceToDevice, s));
         if (mesh->use_lo()) FV_CUDA(cudaMemsetAsync(mesh->d_lo, 0, n * sizeof(uint2), s));
         FV_CUDA(fv::launch_init_scalars(mesh->d_scal, s));
@@ -677,10 +667,35 @@ int fv_mesh_autotune(fv_mesh* mesh, const void* U, int32_t scheme, void* stream,
         FV_CUDA(cudaEventSynchronize(e1));
         float ms = 0.f;
         FV_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        times[v] = 1e3 * ms / (double)steps;
+        return 1e3 * ms / (double)steps;
+      };
+      for (int v = 0; v < fv::kStepVariants; ++v) {
+        mesh->variant = v;
+        if (v != fv::kTileVariant) {
+          times[v] = time_shape();
+          continue;
+        }
+        // the tile shape at each tile size; tiles that do not fit (a
+        // long-band order) leave that size out
+        times[v] = INFINITY;
+        for (int tile : {512, 1024, 2048}) {
+          mesh->pair_tile = tile;
+          try {
+            ensure_tiles(mesh, s);
+            check_tile_smem(mesh, fv::tile_smem_bytes(mesh->f64(), mesh->p_t1_cap));
+          } catch (const fv::Error&) {
+            continue;
+          }
+          const double us = time_shape();
+          if (us < times[v]) {
+            times[v] = us;
+            best_tile = tile;
+          }
+        }
       }
     } catch (...) {
       mesh->variant = keep;
+      mesh->pair_tile = keep_tile;
       if (e0) cudaEventDestroy(e0);
       if (e1) cudaEventDestroy(e1);
       cudaFree(tmp);
@@ -694,6 +709,8 @@ int fv_mesh_autotune(fv_mesh* mesh, const void* U, int32_t scheme, void* stream,
     for (int v = 1; v < fv::kStepVariants; ++v)
       if (times[v] < times[b]) b = v;
     mesh->variant = b;
+    // the tile size of the tiled shapes: the fastest for shape 6 when it wins
+    mesh->pair_tile = b == fv::kTileVariant ? best_tile : keep_tile;
     mesh->drop_graph();
     if (best) *best = b;
     if (us_per_step)

@@ -167,11 +167,13 @@ __device__ __forceinline__ void tile_output(const float g[4][4], const float* w3
   z1 += b3;
 }
 
-// Scales of the warp's 96 rows, from the features in w.feat into w.s.
+// Scales of the warp's first 16 * ntile rows, from the features in w.feat
+// into w.s.
 __device__ __forceinline__ void warp_mlp(ClWarpSmem& w, const ClFrag& fr, const float* b1,
-                                         const float* b2, const float* w3, float b3) {
+                                         const float* b2, const float* w3, float b3,
+                                         int ntile = kRows / 16) {
   const int lane = threadIdx.x & 31, r = lane >> 2, c = lane & 3;
-  for (int t = 0; t < kRows / 16; ++t) {
+  for (int t = 0; t < ntile; ++t) {
     float a1[4][4], g[4][4];
     unsigned A2[2][4];
     tile_forward(w, t, fr, b1, b2, a1, A2, g);
@@ -206,7 +208,11 @@ __device__ __forceinline__ void cell_normals(const CellIn<float>& c, float nx[3]
 }
 
 // The fused step with the learned scale (FP32 meshes).  Persistent grid of
-// resident blocks; each warp takes 32 consecutive cells at a time.
+// resident blocks; each warp takes 32 consecutive cells at a time.  A face
+// between two of the warp's cells is one MLP row, evaluated by the cell with
+// the lower number; the other cell reads that row's scale (the features, and
+// so the scale, are the same bits from either side).  In Hilbert or RCM order
+// about a third of a warp's 96 faces are such shared faces.
 template <int MODE, bool COMP>
 __global__ void __launch_bounds__(kClThreads) k_step_closure(StepArgs a, ClosureParams cp) {
   __shared__ ClShared sh;
@@ -229,35 +235,73 @@ __global__ void __launch_bounds__(kClThreads) k_step_closure(StepArgs a, Closure
     CellIn<float> c;
     float4 UR[3];
     Prim<float> L, W[3];
-    float nx[3], ny[3], len[3];
+    float nx[3] = {0.f, 0.f, 0.f}, ny[3] = {0.f, 0.f, 0.f}, len[3];
+    int nb[3] = {-1, -1, -1};
+    unsigned own = 0u;  // bit k: this cell evaluates face k's row
     if (valid) {
       load_cell<float, MODE, COMP>(a, U, geom, i, c);
       L = primitive<float>(c.U);
       cell_normals(c, nx, ny);
-      const int nb[3] = {c.n0, c.n1, c.n2};
+      nb[0] = c.n0, nb[1] = c.n1, nb[2] = c.n2;
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         UR[k] = neighbour_state<float>(c.U, nb[k], nx[k], ny[k], U, a.uinf_f);
         W[k] = primitive<float>(UR[k]);
         len[k] = face_len<float>(nx[k], ny[k]);
-        float f[8];
-        face_features(c.U, L, UR[k], W[k], nx[k], ny[k], len[k], f);
-        w.feat[k * 32 + lane] = pack_features(f);
+        if (!(nb[k] >= base && nb[k] < i)) own |= 1u << k;
       }
-    } else {
-#pragma unroll
-      for (int k = 0; k < 3; ++k) w.feat[k * 32 + lane] = make_uint4(0u, 0u, 0u, 0u);
     }
+    // the warp's rows, compacted: this lane's come at off .. off + popc(own)
+    const int cnt = __popc(own);
+    int off = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, off, d);
+      if (lane >= d) off += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, off, 31);
+    off -= cnt;
+    if (valid) {
+      int r = off;
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        if ((own >> k) & 1u) {
+          float f[8];
+          face_features(c.U, L, UR[k], W[k], nx[k], ny[k], len[k], f);
+          w.feat[r++] = pack_features(f);
+        }
+    }
+    const int ntile = (total + 15) >> 4;
+    for (int j = total + lane; j < 16 * ntile; j += 32) w.feat[j] = make_uint4(0u, 0u, 0u, 0u);
     __syncwarp();
-    warp_mlp(w, fr, sh.b1, sh.b2, sh.w3, cp.b3);
+    warp_mlp(w, fr, sh.b1, sh.b2, sh.w3, cp.b3, ntile);
     __syncwarp();
+    // each face's row: its own, or the one the neighbouring lane evaluated for
+    // the same face (the neighbour's face pointing back with the negated normal)
+    int row[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const bool borrowed = valid && !((own >> k) & 1u);
+      const int src = borrowed ? (int)(nb[k] - base) : lane;
+      const int off_s = __shfl_sync(0xffffffffu, off, src);
+      const unsigned own_s = __shfl_sync(0xffffffffu, own, src);
+      int kk = 0;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const int nq = __shfl_sync(0xffffffffu, nb[q], src);
+        const float xq = __shfl_sync(0xffffffffu, nx[q], src);
+        const float yq = __shfl_sync(0xffffffffu, ny[q], src);
+        if (nq == (int)i && xq == -nx[k] && yq == -ny[k]) kk = q;
+      }
+      row[k] = borrowed ? off_s + __popc(own_s & ((1u << kk) - 1u))
+                        : off + __popc(own & ((1u << k) - 1u));
+    }
     if (valid) {
       float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
       float perim = 0.0f;
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        face_flux_acc<float, true>(c.U, L, UR[k], W[k], nx[k], ny[k], len[k], w.s[k * 32 + lane],
-                                   acc);
+        face_flux_acc<float, true>(c.U, L, UR[k], W[k], nx[k], ny[k], len[k], w.s[row[k]], acc);
         perim = add(perim, len[k]);
       }
       finish_cell<float, MODE, COMP>(a, out, i, c, acc, perim, (float)dt, bmin, ok);
