@@ -342,6 +342,7 @@ def run_ours(args):
                          f"{n * (ALGO_BYTES[prec] + 8) / 1e6:.0f} MB"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind,
+                     "frac_of_nominal_7900": achieved / 7900.0,
                      "bytes_per_launch_per_cell": algo,
                      "kernel_bytes_per_launch_per_cell": kbytes,
                      "updates_per_launch": args.blocking,
@@ -562,6 +563,21 @@ def batched_leg(B, time_steps=1000):
     best = min(by_shape, key=by_shape.get)
     cells = int(sum(batch.sizes))
     v = cells * time_steps / by_shape[best]
+    # FP32 error against the FP64 path on the smallest and the largest mesh
+    # (U holds the batch state after the last timed run)
+    got = batch.unpack(U.cpu().numpy())
+    errs = {}
+    for k in (int(np.argmin(batch.sizes)), int(np.argmax(batch.sizes))):
+        mi, prim, U0 = items[k]
+        m64 = B.Mesh.from_input(mi, "f64")
+        m64.set_freestream(*prim)
+        perm = m64.renumber("hilbert")
+        U64 = torch.tensor(U0[perm], dtype=torch.float64, device="cuda")
+        m64.step(U64, time_steps, 0.4)
+        r64 = U64[:, 0].cpu().numpy()
+        errs[f"mesh_{k}_{mi.n_tri}_cells"] = float(np.linalg.norm(got[k][:, 0] - r64) /
+                                                    np.linalg.norm(r64))
+        m64.close()
     peak, _ = measured_peaks()
     gbs = (ALGO_BYTES["f32"] + COMP_BYTES) * v / 1e9
     res = {"value": v, "unit": "cell-updates/s", "meshes": batch.n_meshes, "cells": cells,
@@ -572,6 +588,7 @@ def batched_leg(B, time_steps=1000):
                       0: "k_step_batch<float, FE, compensated>"}[best],
            "shape": best,
            "value_by_shape": {k: cells * time_steps / t for k, t in by_shape.items()},
+           "fp32_rel_l2_rho_vs_fp64": errs, "tolerance": 1e-5,
            "achieved_gbs_kernel_bytes": gbs, "frac_of_measured_hbm": gbs / peak,
            "launches_per_step": time_steps + 4}
     batch.close()

@@ -107,3 +107,39 @@ def test_batch_rejects_mixed_precision():
     b = B.Mesh.from_input(W.periodic_square(4, 4, seed=1), "f64")
     with pytest.raises(B.FVError):
         B.Batch([a, b])
+
+
+def test_full_size_batch_matches_solo_on_sampled_meshes(orc):
+    # the benchmark's 256-mesh batch (13.1M cells, Hilbert order, the default
+    # tiled shape): sampled meshes advance bit for bit as they do alone, and
+    # the smallest sampled one matches the FP64 oracle's run in FP32 tolerance
+    items = W.vortex_batch()
+    meshes, states = [], []
+    for mi, prim, U0 in items:
+        m = B.Mesh.from_input(mi, "f32")
+        m.set_freestream(*prim)
+        perm = m.renumber("hilbert")
+        meshes.append(m)
+        states.append(U0[perm])
+    batch = B.Batch(meshes)
+    flat = torch.tensor(batch.pack(states), dtype=torch.float32, device="cuda")
+    tb = batch.step(flat, 20, 0.4)
+    got = batch.unpack(flat.cpu().numpy())
+    rng = np.random.default_rng(11)
+    sample = sorted(set(rng.choice(len(items), size=4, replace=False).tolist()) |
+                    {int(np.argmin(batch.sizes))})
+    for k in sample:
+        U = torch.tensor(states[k], dtype=torch.float32, device="cuda")
+        t = meshes[k].step(U, 20, 0.4)
+        assert t == tb[k]
+        assert np.array_equal(U.cpu().numpy(), got[k]), k
+    k = int(np.argmin(batch.sizes))
+    mi, prim, U0 = items[k]
+    om = orc.Mesh(mi.xy, mi.tri, mi.canon, mi.bnd, mi.default_bc, W.conserved(*prim))
+    Uo, to, _, bad = om.run(U0, 20, 0.4)
+    assert not bad and tb[k] == pytest.approx(to, rel=1e-6)
+    perm = B.Mesh.from_input(mi, "f32").renumber("hilbert")
+    mine = np.empty_like(Uo)
+    mine[perm] = got[k]
+    assert np.linalg.norm(mine[:, 0] - Uo[:, 0]) / np.linalg.norm(Uo[:, 0]) <= 1e-5
+    batch.close()

@@ -203,3 +203,22 @@ def test_staged_pairs_on_a_large_mesh_match_single_steps():
     a.step(Ua, 20, -dt)
     b.step(Ub, 20, -dt)
     assert torch.equal(Ua, Ub)
+
+
+def test_pairs_on_the_16m_square_match_single_steps():
+    # the benchmark's 16.8M-cell square in its launch configuration (tile 1024,
+    # Hilbert): four steps with a fixed dt as two pairs, bitwise against four
+    # single steps of the tiled one-step shape
+    mi = W.vortex_square_16m()
+    U0 = W.isentropic_vortex(mi.centroids(), mach=0.5)
+    prim = (1.0, 0.5 * np.sqrt(1.4), 0.0, 1.0)
+    a, perm = mesh(mi, prim)
+    b, _ = mesh(mi, prim)
+    a.set_variant(6)
+    b.set_blocking(2, 1024)
+    Ua = dev(U0[perm])
+    dt = a.compute_dt(Ua, 0.4)
+    Ub = Ua.clone()
+    a.step(Ua, 4, -dt)
+    b.step(Ub, 4, -dt)
+    assert torch.equal(Ua, Ub)
