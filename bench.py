@@ -63,7 +63,7 @@ def parse_args():
     p.add_argument("--blocking", type=int, default=1, choices=[1, 2],
                    help="time steps per kernel launch (2: tiles staged in shared memory, "
                         "dt evaluated once per pair)")
-    p.add_argument("--tile", type=int, default=1024, choices=[512, 1024, 2048],
+    p.add_argument("--tile", type=int, default=1024, choices=[512, 768, 1024, 2048],
                    help="cells per tile with --blocking 2")
     p.add_argument("--staged", action="store_true",
                    help="with --blocking 2: tile records by bulk copies (512 or 1024 cells)")
@@ -503,8 +503,8 @@ def pair_leg(B, time_steps=1000):
         ts = timed_loop(m, U, U0d, time_steps, 2, 1, "fe", flush=flush)
         v1 = mi.n_tri * time_steps / statistics.mean(ts)
         by_tile = {}
-        for tile, staged in ((512, False), (1024, False), (2048, False), (512, True),
-                             (1024, True)):
+        for tile, staged in ((512, False), (768, False), (1024, False), (2048, False),
+                             (512, True), (1024, True)):
             m.set_blocking(2, tile, staged)
             tt = timed_loop(m, U, U0d, time_steps, 2, 1, "fe", flush=flush)
             by_tile[f"{tile}{'-staged' if staged else ''}"] = (

@@ -161,7 +161,7 @@ int fv_mesh_set_variant(fv_mesh* mesh, int32_t variant);
  * fastest for later fv_step calls and reports it in *best (nullable);
  * us_per_step (nullable, host, [7]) receives the measured microseconds per
  * step of each shape (infinity for shape 6 when its tiles do not fit).
- * Shape 6 is timed with tiles of 512, 1024 and 2048 cells and reported at its
+ * Shape 6 is timed with tiles of 512, 768, 1024 and 2048 cells and reported at its
  * best; when it wins, that tile size is kept (the tile size is shared with
  * fv_mesh_set_blocking).  Allocates and frees one state-sized device buffer
  * and synchronises the stream. */
@@ -200,7 +200,7 @@ int fv_mesh_set_launch_chaining(fv_mesh* mesh, int32_t enable);
  * without another pass through memory (Sec. 7).  FV_F32 meshes, forward
  * Euler, no closure.
  *   steps_per_launch  1 (default: one fused kernel per step) or 2.
- *   tile_cells        0 (= 1024), 512, 1024 or 2048: cells per tile.
+ *   tile_cells        0 (= 1024), 512, 768, 1024 or 2048: cells per tile.
  *   staged            0: one block per tile, records loaded through the
  *                     caches; 1: persistent blocks whose tile records arrive
  *                     by bulk copies into double-buffered shared memory

@@ -576,8 +576,9 @@ int fv_mesh_set_blocking(fv_mesh* mesh, int32_t steps_per_launch, int32_t tile_c
     if (tile_cells == 0) tile_cells = 1024;
     bool known = false;
     for (int t : fv::kPairTiles) known = known || t == tile_cells;
-    if (!known) invalid("tile_cells must be 0, 512, 1024 or 2048");
-    if (staged && tile_cells == 2048) invalid("the staged kernel takes tiles of 512 or 1024 cells");
+    if (!known) invalid("tile_cells must be 0, 512, 768, 1024 or 2048");
+    if (staged && tile_cells != 512 && tile_cells != 1024)
+      invalid("the staged kernel takes tiles of 512 or 1024 cells");
     if (steps_per_launch == 2 && mesh->f64())
       invalid("two steps per launch are built for FV_F32 meshes (the FP64 step is bound by "
               "arithmetic, not by memory)");
@@ -678,7 +679,7 @@ int fv_mesh_autotune(fv_mesh* mesh, const void* U, int32_t scheme, void* stream,
         // the tile shape at each tile size; tiles that do not fit (a
         // long-band order) leave that size out
         times[v] = INFINITY;
-        for (int tile : {512, 1024, 2048}) {
+        for (int tile : fv::kPairTiles) {
           mesh->pair_tile = tile;
           try {
             ensure_tiles(mesh, s);

@@ -195,7 +195,7 @@ struct PairArgs {
   bool chained;  // launch as part of a programmatic chain (launch_util.cuh)
 };
 // tile sizes with a kernel instantiation (the staged kernel: 512 and 1024)
-constexpr int kPairTiles[3] = {512, 1024, 2048};
+constexpr int kPairTiles[4] = {512, 768, 1024, 2048};
 // dynamic shared memory of one block for the given capacities; the staged
 // kernel adds two stages of the tile's own records (64 bytes a cell each)
 inline size_t pair_smem_bytes(int e_cap, int t1_cap, int tile, bool staged) {

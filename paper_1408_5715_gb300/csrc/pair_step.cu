@@ -181,25 +181,6 @@ __device__ __forceinline__ void pair_finish(const PairArgs& a, float bmin, bool 
   }
 }
 
-// A tile cell's own records (geometry, local neighbours, remainder at the
-// start of the pair when `with_lo`); nothing is loaded past the tile's end.
-struct CellRecs {
-  float4 g0, g1;
-  uint2 ln, lo;
-};
-
-template <bool COMP>
-__device__ __forceinline__ void load_recs(const PairArgs& a, int64_t t0, int e, int nt,
-                                          bool with_lo, CellRecs& r) {
-  if (e < nt) {
-    const int64_t g = t0 + e;
-    r.g0 = __ldg(a.geom + 2 * g);
-    r.g1 = __ldg(a.geom + 2 * g + 1);
-    r.ln = __ldg(a.cell_ln + g);
-    r.lo = (COMP && with_lo) ? __ldg(a.lo_in + g) : make_uint2(0u, 0u);
-  }
-}
-
 template <int THREADS, int KMAX, bool COMP>
 __global__ void __launch_bounds__(THREADS) k_step_pair(PairArgs a) {
   chain_entry();
@@ -226,24 +207,21 @@ __global__ void __launch_bounds__(THREADS) k_step_pair(PairArgs a) {
   __syncthreads();
   const float dt1f = sdt.dt1f, dt2f = sdt.dt2f;
 
-  // step 1: tile cells (remainders stay in registers), then the first halo.
-  // Each thread's next tile cell's records are loaded while it computes the
-  // current one, so one global latency is exposed per phase, not per cell.
+  // step 1: tile cells (remainders stay in registers), then the first halo
   bool ok = true;
   uint2 lo1[KMAX];
-  CellRecs cur, nxt;
-  load_recs<COMP>(a, t0, threadIdx.x, nt, true, cur);
 #pragma unroll
   for (int k = 0; k < KMAX; ++k) {
     const int e = threadIdx.x + k * THREADS;
-    if (k + 1 < KMAX) load_recs<COMP>(a, t0, e + THREADS, nt, true, nxt);
     lo1[k] = make_uint2(0u, 0u);
-    if (e < nt)
-      lo1[k] = step1_cell<COMP>(cur.g0, cur.g1, cur.ln, cur.lo, e, sU0, sP0, sU1, sP1, a.uinf,
-                                dt1f, true, ok);
-    if (k + 1 < KMAX) cur = nxt;
+    if (e < nt) {
+      const int64_t g = t0 + e;
+      const uint2 lo0 = COMP ? __ldg(a.lo_in + g) : make_uint2(0u, 0u);
+      lo1[k] = step1_cell<COMP>(__ldg(a.geom + 2 * g), __ldg(a.geom + 2 * g + 1),
+                                __ldg(a.cell_ln + g), lo0, e, sU0, sP0, sU1, sP1, a.uinf, dt1f,
+                                true, ok);
+    }
   }
-  load_recs<COMP>(a, t0, threadIdx.x, nt, false, cur);  // step 2's first cell
   step1_halo<THREADS, COMP>(a, nt, hs, h1, sU0, sP0, sU1, sP1, dt1f);
   __syncthreads();
 
@@ -252,15 +230,15 @@ __global__ void __launch_bounds__(THREADS) k_step_pair(PairArgs a) {
 #pragma unroll
   for (int k = 0; k < KMAX; ++k) {
     const int e = threadIdx.x + k * THREADS;
-    if (k + 1 < KMAX) load_recs<COMP>(a, t0, e + THREADS, nt, false, nxt);
     if (e < nt) {
+      const int64_t g = t0 + e;
       uint2 lo2;
-      const float4 U2 = step2_cell<COMP>(cur.g0, cur.g1, cur.ln, lo1[k], e, sU1, sP1, a.uinf,
-                                         dt2f, lo2, bmin, ok);
-      a.out[t0 + e] = U2;
-      if (COMP) a.lo_out[t0 + e] = lo2;
+      const float4 U2 = step2_cell<COMP>(__ldg(a.geom + 2 * g), __ldg(a.geom + 2 * g + 1),
+                                         __ldg(a.cell_ln + g), lo1[k], e, sU1, sP1, a.uinf, dt2f,
+                                         lo2, bmin, ok);
+      a.out[g] = U2;
+      if (COMP) a.lo_out[g] = lo2;
     }
-    if (k + 1 < KMAX) cur = nxt;
   }
   pair_finish(a, bmin, ok, sdt.t, sdt.dt1, sdt.dt2);
 }
@@ -456,6 +434,7 @@ cudaError_t launch_step_pair(const PairArgs& a, int staged, cudaStream_t s) {
   }
   switch (a.tile) {
     case 512: return launch_plain<256, 2>(a, s);
+    case 768: return launch_plain<256, 3>(a, s);
     case 1024: return launch_plain<256, 4>(a, s);
     case 2048: return launch_plain<512, 4>(a, s);
     default: return cudaErrorInvalidValue;

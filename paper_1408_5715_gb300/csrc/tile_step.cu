@@ -192,6 +192,7 @@ template <typename R, int MODE, bool COMP>
 cudaError_t launch_tile_size(const StepArgs& a, cudaStream_t s) {
   switch (a.tile) {
     case 512: return launch_tile_t<R, MODE, COMP, 256, 2>(a, s);
+    case 768: return launch_tile_t<R, MODE, COMP, 256, 3>(a, s);
     case 1024: return launch_tile_t<R, MODE, COMP, 256, 4>(a, s);
     case 2048: return launch_tile_t<R, MODE, COMP, 512, 4>(a, s);
     default: return cudaErrorInvalidValue;

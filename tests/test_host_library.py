@@ -225,8 +225,9 @@ def test_two_step_blocking_validation():
         m64.set_blocking(2)
     m64.set_blocking(1)
     m32 = B.Mesh.from_input(W.periodic_square(8, 8, seed=1), "f32")
-    for bad in [(3, 0), (0, 0), (2, 100), (2, 4096), (2, 2048, True)]:
+    for bad in [(3, 0), (0, 0), (2, 100), (2, 4096), (2, 2048, True), (2, 768, True)]:
         with pytest.raises(B.FVError):
             m32.set_blocking(*bad)
     m32.set_blocking(2, 512)
     m32.set_blocking(2, 1024, True)
+    m32.set_blocking(2, 768)
