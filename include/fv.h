@@ -46,8 +46,8 @@ extern "C" {
 #define FV_F32 0
 #define FV_F64 1
 
-/* ---- boundary tags of fv_mesh_create's bnd_edges (reading of Sec. 7: "ghost
- * nodes ... implement inflow, outflow or wall boundary conditions") ---------- */
+/* ---- boundary tags of fv_mesh_create's bnd_edges (reading of Sec. 7, where
+ * ghost cells carry the inflow, outflow and wall conditions) ---------------- */
 #define FV_BC_NONE 0     /* no default: an unmatched edge is an error */
 #define FV_BC_WALL 1     /* slip wall: ghost mirrors the normal momentum */
 #define FV_BC_FARFIELD 2 /* far field: ghost is the free stream of fv_set_freestream */

@@ -70,8 +70,14 @@ class Problem:
         self.kids = 4 ** cfg.levels
         self.mc = B.Mesh.from_input(self.mi_c, "f32")
         self.mf = B.Mesh.from_input(self.mi_f, "f64")
-        self.perm_c = self.mc.renumber("rcm")
-        self.perm_f = self.mf.renumber("rcm")
+        # Hilbert order: compact warps share MLP rows (coarse) and compact
+        # tiles serve the shared-memory shape (fine); the fine shape is tuned
+        self.perm_c = self.mc.renumber("hilbert")
+        self.perm_f = self.mf.renumber("hilbert")
+        U = torch.tensor(W.uniform_state(self.mf.n, W.freestream(0.5)), dtype=torch.float64,
+                         device="cuda")
+        self.fine_shape, _ = self.mf.autotune(U)
+        del U
         _, _, area_c = self.mc.export()
         _, _, area_f = self.mf.export()
         dev = "cuda"
@@ -222,6 +228,7 @@ def train_and_evaluate(cfg: TrainConfig = TrainConfig(), log=None):
     scales = cl.scales(prob.mc, Ul).cpu().numpy()
     report = {
         "config": asdict(cfg), "coarse_cells": prob.n_c, "fine_cells": prob.n_f,
+        "fine_kernel_shape": prob.fine_shape,
         "dt_coarse": dt_c, "train_machs": [float(x) for x in train_m],
         "test_machs": [float(x) for x in test_m], "samples": len(samples),
         "loss_weights": w, "loss_first": loss0, "loss_history": history,
