@@ -54,7 +54,7 @@ def parse_args():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="channel_bump_1m",
-                   choices=["channel_bump_1m", "square_16m", "vortex_square_small"])
+                   choices=["channel_bump_1m", "square_16m", "batch_256", "vortex_square_small"])
     p.add_argument("--precision", default="f32", choices=["f32", "f64"])
     p.add_argument("--scheme", default="fe", choices=["fe", "rk2"])
     p.add_argument("--order", default=None, choices=["identity", "shuffle", "rcm", "hilbert", "am1"])
@@ -81,6 +81,9 @@ WORKLOADS = {
     "square_16m": dict(make=W.vortex_square_16m, init="vortex", mach=0.5, time_steps=1000,
                        order="hilbert", desc="periodic unit square, 4096x2048 quads, jitter 20%, "
                        "isentropic vortex beta=5 M=0.5"),
+    "batch_256": dict(make=W.vortex_batch, batch=True, time_steps=1000, order="hilbert",
+                      desc="256 periodic jittered squares, 4,900-200,704 triangles each "
+                           "(log-uniform), vortex or uniform flow, Mach U(0.3, 0.8)"),
     "vortex_square_small": dict(make=W.vortex_square_small, init="vortex", mach=0.5,
                                 time_steps=100, order="shuffle",
                                 desc="periodic unit square, 64x32 quads, vortex"),
@@ -263,6 +266,8 @@ def run_ours(args):
     B.load()
 
     spec = WORKLOADS[args.workload]
+    if spec.get("batch"):
+        return run_batch(args, B, spec, dist, world, rank)
     S = args.time_steps or spec["time_steps"]
     order = args.order or spec["order"]
     mi = spec["make"]()
@@ -357,6 +362,117 @@ def run_ours(args):
     }
     if rank == 0 and not args.no_extras and world == 1:
         extras(args, B, spec, mi, U0, U0p, perm, m, S, U_final, out)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_batch(args, B, spec, dist, world, rank):
+    """Many meshes of uneven size stepped together (one launch per time step
+    for the whole batch): the same contract as the single-mesh line."""
+    import torch
+    if args.blocking != 1 or args.closure or args.scheme != "fe":
+        raise SystemExit("the batch workload runs forward Euler, one step per launch")
+    S = args.time_steps or spec["time_steps"]
+    prec = args.precision
+    tdt = torch.float32 if prec == "f32" else torch.float64
+    items = spec["make"]()
+    meshes, states = [], []
+    for mi, prim, U0 in items:
+        m = B.Mesh.from_input(mi, prec)
+        m.set_freestream(*prim)
+        perm = m.renumber(args.order or spec["order"], seed=1)
+        meshes.append(m)
+        states.append(U0[perm])
+    batch = B.Batch(meshes)
+    for m in meshes:
+        m.close()
+    if args.variant is not None:
+        batch.set_variant(args.variant)
+    host0 = batch.pack(states)
+    flat0 = torch.tensor(host0, dtype=tdt, device="cuda")
+    U = torch.empty_like(flat0)
+    cells = int(sum(batch.sizes))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    times = []
+    with ClockSampler(gpu_smi_id()) as clk:
+        for it in range(args.warmup + args.steps):
+            U.copy_(flat0)
+            flush.fill_(float(it))
+            torch.cuda.synchronize()
+            if dist is not None:
+                dist.barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            batch.step(U, S, 0.4, sync=False)
+            batch.totals(U)
+            e1.record()
+            torch.cuda.synchronize()
+            if it >= args.warmup:
+                times.append(e0.elapsed_time(e1) / 1e3)
+    batch.step(U, 0, 0.4)  # collects the error flag of the timed runs
+    total = sum(times)
+    if dist is not None:
+        t = torch.tensor([total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+    shape = batch.variant()
+    avg_launch = total / (args.steps * S)
+    peak, peak_kind = measured_peaks()
+    kbytes = ALGO_BYTES[prec] + (COMP_BYTES if prec == "f32" else 0)
+    achieved = ALGO_BYTES[prec] * cells / avg_launch / 1e9
+    kname = {5: "k_step_tma", 6: "k_step_tile_batch", 0: "k_step_batch"}[shape]
+    # end to end: the flat state in from pinned host memory and back, every step
+    host_in = torch.tensor(host0, dtype=tdt).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    te = []
+    for it in range(2):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        U.copy_(host_in, non_blocking=True)
+        batch.step(U, S, 0.4, sync=False)
+        tot = batch.totals(U)
+        host_out.copy_(U, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        if it > 0:
+            te.append(e0.elapsed_time(e1) / 1e3)
+    assert np.isfinite(tot).all()
+    nb = host_in.numel() * host_in.element_size()
+    out = {
+        "metric": "cell updates/s", "value": cells * S * args.steps * world / total,
+        "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": prec, "data": "synthetic",
+        "config": {"workload": args.workload, "mesh": spec["desc"], "cells": cells,
+                   "padded_cells": batch.n_padded, "meshes": batch.n_meshes,
+                   "time_steps_per_step": S, "scheme": "fe", "cfl": 0.4,
+                   "order": args.order or spec["order"],
+                   "dt": "per mesh: CFL bound of its state at the start of each step",
+                   "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "kernel_shape": {"variant": shape, "autotuned": False},
+                   "l2": "256 MB written between steps (L2 flushed); state+geometry "
+                         f"{cells * (ALGO_BYTES[prec] + 8) / 1e6:.0f} MB"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind,
+                     "frac_of_nominal_7900": achieved / 7900.0,
+                     "bytes_per_launch_per_cell": ALGO_BYTES[prec],
+                     "kernel_bytes_per_launch_per_cell": kbytes, "updates_per_launch": 1,
+                     "frac_with_kernel_bytes": kbytes * cells / avg_launch / 1e9 / peak,
+                     "kernel": f"{kname}<{'float' if prec == 'f32' else 'double'}, FE>",
+                     "traffic": profiled_traffic(f"step_{prec}_{args.workload}.md")},
+        "e2e": {"value": cells * S / statistics.mean(te), "unit": "cell-updates/s",
+                "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb + 32 * batch.n_meshes,
+                "api": "fv_batch_step + fv_batch_totals on host-copied state"},
+        "gpu_launches": args.steps * (S + 4),
+        "clocks": clk.summary(),
+    }
+    batch.close()
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:
@@ -720,9 +836,16 @@ def run_reference(args):
     import oracle
     oracle.build()
     spec = WORKLOADS[args.workload]
-    mi = spec["make"]()
-    U0 = initial_state(spec, mi)
-    uinf = W.conserved(*W.freestream(spec["mach"]))
+    if spec.get("batch"):
+        # a bounded sample of the batch: its largest mesh (every mesh of the
+        # batch is stepped the same way, one after another on the CPU)
+        items = spec["make"]()
+        mi, prim, U0 = max(items, key=lambda it: it[0].n_tri)
+        uinf = W.conserved(*prim)
+    else:
+        mi = spec["make"]()
+        U0 = initial_state(spec, mi)
+        uinf = W.conserved(*W.freestream(spec["mach"]))
     om = oracle.Mesh(mi.xy, mi.tri, mi.canon, mi.bnd, mi.default_bc, uinf)
     per_step = 2  # time steps per benchmark step: a bounded sample of the workload
     for _ in range(args.warmup):
@@ -741,8 +864,9 @@ def run_reference(args):
            "config": {"workload": args.workload, "mesh": spec["desc"], "cells": mi.n_tri,
                       "time_steps_per_step": per_step, "scheme": "fe", "cfl": 0.4},
            "cpu_baseline": {"value": v, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
-                            "sample": f"{per_step} FP64 forward-Euler steps of the full mesh per "
-                                      "benchmark step, single thread", "cpu": cpu_model()},
+                            "sample": f"{per_step} FP64 forward-Euler steps of the full mesh "
+                                      f"({mi.n_tri} cells) per benchmark step, single thread",
+                            "cpu": cpu_model()},
            "e2e": {"value": v, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)

@@ -376,6 +376,10 @@ int fv_batch_info(const fv_batch* batch, int64_t* n_cells_padded, int64_t* offse
  * device call).  All give bitwise identical results. */
 int fv_batch_set_variant(fv_batch* batch, int32_t variant);
 
+/* The batch's kernel shape in *variant: 0, 5 or 6, or -1 while the default
+ * is still to be decided at the first device call. */
+int fv_batch_get_variant(const fv_batch* batch, int32_t* variant);
+
 /* Compensated float update for FV_F32 batches (see fv_mesh_set_compensation). */
 int fv_batch_set_compensation(fv_batch* batch, int32_t enable);
 

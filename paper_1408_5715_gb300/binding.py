@@ -94,6 +94,7 @@ def load():
             "fv_batch_info": (ctypes.c_int, [_vp, _P(_i64), _vp]),
             "fv_batch_set_compensation": (ctypes.c_int, [_vp, _i32]),
             "fv_batch_set_variant": (ctypes.c_int, [_vp, _i32]),
+            "fv_batch_get_variant": (ctypes.c_int, [_vp, _P(_i32)]),
             "fv_batch_step": (ctypes.c_int, [_vp, _vp, _i64, _dbl, _dbl, _i32, _vp, _vp]),
             "fv_batch_totals": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
         }
@@ -428,6 +429,12 @@ class Batch:
 
     def set_variant(self, variant: int):
         _check(load().fv_batch_set_variant(self._h, int(variant)))
+
+    def variant(self) -> int:
+        """Kernel shape of the batch (-1 until the first device call)."""
+        v = _i32()
+        _check(load().fv_batch_get_variant(self._h, ctypes.byref(v)))
+        return int(v.value)
 
     def step(self, U, nsteps, cfl, t_stop=0.0, scheme="fe", stream=None, sync=True):
         """Advances the flattened CUDA state U in place; returns each mesh's

@@ -1287,6 +1287,14 @@ int fv_batch_set_variant(fv_batch* batch, int32_t variant) {
   });
 }
 
+int fv_batch_get_variant(const fv_batch* batch, int32_t* variant) {
+  return guarded([&] {
+    check_batch(batch);
+    if (!variant) invalid("null variant");
+    *variant = batch->variant;
+  });
+}
+
 int fv_batch_set_compensation(fv_batch* batch, int32_t enable) {
   return guarded([&] {
     check_batch(batch);
