@@ -76,3 +76,28 @@ def test_fp32_tracks_fp64_before_the_shock_interacts(step_case):
     assert ta == pytest.approx(0.2, rel=1e-12) and tb == pytest.approx(0.2, rel=1e-12)
     x, y = A.double().cpu().numpy()[:, 0], Bt.cpu().numpy()[:, 0]
     assert np.linalg.norm(x - y) / np.linalg.norm(y) <= 1e-5
+
+
+def test_paper_size_step_with_max_wave_speed_matches_oracle(orc):
+    # the 410,400-cell mesh (the paper's largest size) with the one-sided
+    # maximum wave speed, FP64, 30 steps from the Mach 3 start: the oracle
+    # with the same reading, cell by cell
+    mi = W.forward_step_394k()
+    prim = W.mach3_inflow()
+    U0 = W.uniform_state(mi.n_tri, prim)
+    g = mesh(mi, prim, "f64")
+    g.set_wave_speed("max")
+    perm = g.renumber("hilbert")
+    g.autotune(torch.tensor(U0[perm], device="cuda"))
+    U = torch.tensor(U0[perm], device="cuda")
+    t = g.step(U, 30, 0.4)
+    orc.set_wave_speed("max")
+    try:
+        om = orc.Mesh(mi.xy, mi.tri, None, mi.bnd, 0, W.conserved(*prim))
+        Uo, to, _, bad = om.run(U0, 30, 0.4)
+    finally:
+        orc.set_wave_speed("average")
+    assert not bad and t == pytest.approx(to, rel=1e-13)
+    out = np.empty_like(Uo)
+    out[perm] = U.cpu().numpy()
+    assert rel_err_max(out, Uo) <= 1e-12

@@ -231,3 +231,17 @@ def test_two_step_blocking_validation():
     m32.set_blocking(2, 512)
     m32.set_blocking(2, 1024, True)
     m32.set_blocking(2, 768)
+
+
+def test_tile_halo_limit_is_reported():
+    # tile-local ids are 16 bits: a tile whose rings exceed 65533 cells (a
+    # huge tile in a shuffled numbering) is refused, not wrapped
+    mi = W.periodic_square(300, 200, seed=6)  # 120,000 cells
+    m = B.Mesh.from_input(mi, "f32")
+    m.renumber("shuffle", seed=2)
+    with pytest.raises(B.FVError, match="65533") as e:
+        m.tile_halo(40000, 0)
+    assert e.value.code == B.FV_EINVAL
+    m.renumber("hilbert")
+    h1, h2 = m.tile_halo(40000, 0)  # a compact order keeps the same tile legal
+    assert 0 < h1.size < 2000 and 0 < h2.size < 2000
