@@ -45,6 +45,10 @@ FALLBACK_HBM_GBS = 6800.0
 # updates: state in and out (32), geometry (32), tile-local neighbours (8),
 # remainder in and out (16); halo reads are re-reads of other tiles' cells.
 PAIR_BYTES = 32 + 32 + 8 + 16
+# Normals from vertex coordinates (FP32): own state read and written, 3
+# neighbour ids and 3 node ids, and the node coordinates (8 bytes per node,
+# half a node per triangle) instead of 28 bytes of stored geometry.
+VERTEX_BYTES = 16 + 16 + 12 + 12 + 4
 
 
 def parse_args():
@@ -71,6 +75,8 @@ def parse_args():
                    help="step with the learned dissipation scale (untrained initial weights)")
     p.add_argument("--variant", type=int, default=None,
                    help="force a step-kernel shape instead of autotuning")
+    p.add_argument("--geometry", default="stored", choices=["stored", "vertex"],
+                   help="stored normals, or normals formed from node coordinates on a grid")
     return p.parse_args()
 
 
@@ -215,7 +221,8 @@ def choose_variant(m, U, variant, scheme="fe"):
         m.set_variant(variant)
         return {"variant": variant, "autotuned": False}
     best, us = m.autotune(U, scheme=scheme)
-    return {"variant": best, "autotuned": True, "us_per_step_by_variant": us}
+    return {"variant": best, "tile": m.tiling()[1] if best == 6 else None, "autotuned": True,
+            "us_per_step_by_variant": us}
 
 
 def timed_loop(m, U, U0dev, time_steps, steps, warmup, scheme, cfl=0.4, flush=None,
@@ -285,6 +292,10 @@ def run_ours(args):
             raise SystemExit("--closure runs FP32, one step per launch")
         from paper_1408_5715_gb300 import closure_training as CT
         closure = B.Closure(CT.initial_theta(1, 0.3))
+    if args.geometry == "vertex":
+        if prec != "f32" or args.blocking != 1 or args.closure:
+            raise SystemExit("--geometry vertex runs FP32, one step per launch, no closure")
+        m.set_geometry("vertex")
     if args.blocking == 2:
         if prec != "f32" or args.scheme != "fe":
             raise SystemExit("--blocking 2 runs FP32 forward Euler")
@@ -312,13 +323,14 @@ def run_ours(args):
         kname = (f"{'k_step_pair_tma' if args.staged else 'k_step_pair'}"
                  f"<tile {args.tile}, compensated>")
     else:
-        algo = ALGO_BYTES[prec]
-        kbytes = ALGO_BYTES[prec] + (COMP_BYTES if prec == "f32" else 0)
+        algo = VERTEX_BYTES if args.geometry == "vertex" else ALGO_BYTES[prec]
+        kbytes = algo + (COMP_BYTES if prec == "f32" else 0)
         kfun = ("k_step_closure" if args.closure else
                 {5: "k_step_tma", 6: "k_step_tile"}.get(tune["variant"], "k_step"))
         kname = (f"{kfun}<{'float' if prec == 'f32' else 'double'}, "
                  f"{'RK2' if stages == 2 else 'FE'}, "
-                 f"{'compensated' if prec == 'f32' else 'plain'}, shape {tune['variant']}>")
+                 f"{'compensated' if prec == 'f32' else 'plain'}, shape {tune['variant']}"
+                 f"{', vertex geometry' if args.geometry == 'vertex' else ''}>")
     achieved = algo * n / avg_launch / 1e9  # GB/s of one step-kernel launch
     U_final = U.double().cpu().numpy()
     e2e = e2e_leg(args, m, U0p, n, S, dist, closure)
@@ -337,6 +349,8 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": args.workload, "mesh": spec["desc"], "cells": n,
                    "time_steps_per_step": S, "scheme": args.scheme, "cfl": 0.4, "order": order,
+                   "geometry": ("normals from node coordinates on a grid of 2^%d" %
+                                m.nodes()[1]) if args.geometry == "vertex" else "stored normals",
                    "dt": "CFL bound of the state at the start of each pair" if args.blocking == 2
                          else "CFL bound of the state at the start of each step",
                    "closure": "learned dissipation scale, initial weights" if args.closure
@@ -355,6 +369,7 @@ def run_ours(args):
                      "kernel": kname,
                      "traffic": profiled_traffic(
                          f"step_pair_{args.workload}.md" if args.blocking == 2
+                         else f"step_vertex_{args.workload}.md" if args.geometry == "vertex"
                          else f"step_{prec}_{args.workload}.md")},
         "e2e": e2e,
         "gpu_launches": args.steps * (launches + 4),
@@ -573,6 +588,8 @@ def extras(args, B, spec, mi, U0, U0p, perm, m32, S, U32_final, out):
     # ---- the same loop with each step launched only after the previous one
     if args.precision == "f32" and args.blocking == 1:
         leg("unchained", lambda B_: unchained_leg(m32, U0p, S, args.scheme, out["value"]))
+    # ---- normals from node coordinates against stored normals
+    leg("vertex_geometry", vertex_leg)
     # ---- two steps per launch (temporal blocking) on the same workloads
     leg("pairs", pair_leg)
     # ---- many meshes in one launch per step (256 periodic squares, 5k-200k cells)
@@ -598,6 +615,53 @@ def unchained_leg(m, U0p, S, scheme, chained_value):
         m.set_launch_chaining(True)
     v = U0p.shape[0] * S / statistics.mean(tt)
     return {"value": v, "unit": "cell-updates/s", "chained_over_unchained": chained_value / v}
+
+
+def vertex_leg(B, time_steps=1000):
+    """Normals formed from node coordinates (Sec. 7's alternative to stored
+    normals) against stored normals: FP32 compensated, Hilbert order,
+    autotuned shape, CFL 0.4.  The vertex form runs on the nodes snapped to
+    its grid; the density difference between the two runs measures what the
+    snapping moves (the vertex form is bitwise the stored records of the
+    snapped mesh, checked by the tests)."""
+    import torch
+    peak, _ = measured_peaks()
+    res = {}
+    for name in ("channel_bump_1m", "square_16m"):
+        spec = WORKLOADS[name]
+        mi = spec["make"]()
+        U0 = initial_state(spec, mi)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        r = {"cells": mi.n_tri, "order": "hilbert", "time_steps": time_steps}
+        finals = {}
+        for geom in ("stored", "vertex"):
+            m, perm = make_mesh(B, spec, mi, "f32", "hilbert")
+            if geom == "vertex":
+                m.set_geometry("vertex")
+                r["grid_exponent"] = m.nodes()[1]
+            U0d = torch.tensor(U0[perm], dtype=torch.float32, device="cuda")
+            U = torch.empty_like(U0d)
+            tune = choose_variant(m, U0d, None)
+            tt = timed_loop(m, U, U0d, time_steps, 3, 2, "fe", flush=flush)
+            v = mi.n_tri * time_steps / statistics.median(tt)
+            algo = VERTEX_BYTES if geom == "vertex" else ALGO_BYTES["f32"]
+            gbs = algo * v / 1e9
+            r[geom] = {"value": v, "unit": "cell-updates/s", "kernel_shape": tune,
+                       "bytes_per_update": algo, "achieved_gbs": gbs,
+                       "frac_of_measured_hbm": gbs / peak,
+                       "traffic": profiled_traffic(f"step_vertex_{name}.md" if geom == "vertex"
+                                                   else f"step_f32_{name}.md")}
+            out = np.empty(U0.shape)
+            out[perm] = U.double().cpu().numpy()
+            finals[geom] = out
+            del U, U0d
+            m.close()
+        r["speedup_vertex_over_stored"] = r["vertex"]["value"] / r["stored"]["value"]
+        a, b = finals["vertex"][:, 0], finals["stored"][:, 0]
+        r["rel_l2_rho_vertex_vs_stored"] = float(np.linalg.norm(a - b) / np.linalg.norm(b))
+        res[name] = r
+        del flush
+    return res
 
 
 def pair_leg(B, time_steps=1000):

@@ -64,6 +64,10 @@ extern "C" {
 #define FV_SCHEME_FE 0  /* forward Euler, Eq. 6 and the update equation of Sec. 6.2.2 */
 #define FV_SCHEME_RK2 1 /* two-stage Heun (SSP-RK2) with the same dt; not in the paper */
 
+/* Where the step kernel takes face normals and areas from (fv_mesh_set_geometry) */
+#define FV_GEOM_STORED 0 /* per-cell records computed on the host (Sec. 7: precomputed) */
+#define FV_GEOM_VERTEX 1 /* formed from node coordinates on a fixed-point grid (Sec. 7) */
+
 /* Wave speed in the Lax-Friedrichs dissipation (fv_mesh_set_wave_speed) */
 #define FV_WAVE_AVERAGE 0 /* |average normal velocity| + average sound speed (Sec. 6.2.2) */
 #define FV_WAVE_MAX 1     /* max over both sides of |normal velocity| + sound speed */
@@ -187,6 +191,43 @@ int fv_mesh_set_wait_limit(fv_mesh* mesh, uint32_t polls);
  * fv_batch_create with such a mesh.  FV_EINVAL for an unknown mode. */
 int fv_mesh_set_wave_speed(fv_mesh* mesh, int32_t mode);
 
+/* Normals from vertex coordinates: the alternative the paper weighs against
+ * stored normals for its FPGA design (Sec. 7), trading bytes per cell for
+ * arithmetic.  FV_F32 meshes; the tile shape (6) of the step kernel.
+ *   form  FV_GEOM_STORED (default): every step kernel reads each cell's
+ *         precomputed normals and 1/V (32 bytes per cell in FP32).
+ *         FV_GEOM_VERTEX: the tile kernel stages the grid coordinates of its
+ *         tile's nodes in shared memory (8 bytes per node, about half a node
+ *         per cell) and forms each cell's three normals and 1/V from them,
+ *         reading 4 bytes of node ids per cell instead of 32 of geometry.
+ * The first FV_GEOM_VERTEX call snaps every node of the mesh to a grid of
+ * spacing s = 2^e, the finest with the mesh's extent E within 2^31 - 16
+ * steps (so a node moves by at most s, s <= E / (2^31 - 16)); a periodic node
+ * copy keeps the offset of its canonical node in whole steps.  Normals and
+ * areas of the mesh are then those of the snapped nodes for every shape,
+ * every later call and any batch made from the mesh: normals are exact
+ * integer edge vectors converted with one rounding, 2V is an exact 64-bit
+ * cross product, and the FP32 1/V is 2^(1-2e) times the correctly rounded
+ * reciprocal of 2V in grid units rounded to FP32, as the kernel forms them,
+ * so all shapes still give bitwise the same states.  The snapping stays when
+ * the form goes back to FV_GEOM_STORED.  fv_mesh_nodes returns the snapped
+ * coordinates.  Selecting FV_GEOM_VERTEX also selects shape 6; fv_mesh_autotune
+ * then times shape 6 at each tile size only.
+ * FV_EINVAL: an FV_F64 mesh, an unknown form, or a mesh that the grid cannot
+ * hold (extent outside 2^-62 .. 2^62 times 2^31, coordinates too far from the
+ * origin for exact FP64 grid points, a triangle that collapses on the grid,
+ * or a face whose two sides are not exact opposites after snapping, e.g. an
+ * inconsistent periodic identification); the mesh is unchanged then. */
+int fv_mesh_set_geometry(fv_mesh* mesh, int32_t form);
+
+/* Node coordinates of the mesh as its geometry uses them: those given to
+ * fv_mesh_create, or after FV_GEOM_VERTEX their grid points (nodes that no
+ * triangle uses keep their coordinates).  All outputs nullable, host.
+ *   n_nodes        number of nodes.
+ *   xy             [2*n_nodes] (x, y) per node.
+ *   grid_exponent  e of the grid spacing 2^e, or INT32_MIN if not snapped. */
+int fv_mesh_nodes(const fv_mesh* mesh, int64_t* n_nodes, double* xy, int32_t* grid_exponent);
+
 /* Launch chaining of the step kernels (default 1 = on): each step kernel of
  * fv_step is launched with programmatic dependent launch, so the next step's
  * launch is prepared while the current step runs and its blocks wait in
@@ -200,7 +241,11 @@ int fv_mesh_set_launch_chaining(fv_mesh* mesh, int32_t enable);
  * without another pass through memory (Sec. 7).  FV_F32 meshes, forward
  * Euler, no closure.
  *   steps_per_launch  1 (default: one fused kernel per step) or 2.
- *   tile_cells        0 (= 1024), 512, 768, 1024 or 2048: cells per tile.
+ *   tile_cells        cells per tile: 0 (= 1024), 512, 768, 1024 or 2048
+ *                     with 2; with 1, 0 or any size from 32 to 2048 for the
+ *                     one-step tile shape (6), which fv_mesh_autotune also
+ *                     sets (it times sizes that fill whole waves of resident
+ *                     blocks besides the standard four).
  *   staged            0: one block per tile, records loaded through the
  *                     caches; 1: persistent blocks whose tile records arrive
  *                     by bulk copies into double-buffered shared memory
@@ -216,10 +261,15 @@ int fv_mesh_set_launch_chaining(fv_mesh* mesh, int32_t enable);
  * single step.  Halos must fit in shared memory: renumber with a compact
  * order first (FV_ORDER_HILBERT); fv_step returns FV_EINVAL otherwise.
  * fv_step then also returns FV_EINVAL for RK2 or a closure.  Returns
- * FV_EINVAL for FV_F64 meshes with 2, an unknown tile size, or tiles of
- * 2048 cells with staged = 1. */
+ * FV_EINVAL for FV_F64 meshes with 2, a tile size outside those above, or
+ * tiles of 2048 cells with staged = 1. */
 int fv_mesh_set_blocking(fv_mesh* mesh, int32_t steps_per_launch, int32_t tile_cells,
                          int32_t staged);
+
+/* The step-kernel shape (0-6) and the tile size in cells of the tiled shapes
+ * that the mesh runs now (set by fv_mesh_set_variant, fv_mesh_set_blocking,
+ * fv_mesh_set_geometry or fv_mesh_autotune).  Outputs nullable, host. */
+int fv_mesh_get_tiling(const fv_mesh* mesh, int32_t* variant, int32_t* tile_cells);
 
 /* Host diagnostics of the two-step tiles: the halos of tile `tile` (cells
  * [tile*tile_cells, (tile+1)*tile_cells) of the current numbering).

@@ -72,6 +72,9 @@ def load():
             "fv_mesh_set_blocking": (ctypes.c_int, [_vp, _i32, _i32, _i32]),
             "fv_mesh_set_launch_chaining": (ctypes.c_int, [_vp, _i32]),
             "fv_mesh_set_wave_speed": (ctypes.c_int, [_vp, _i32]),
+            "fv_mesh_set_geometry": (ctypes.c_int, [_vp, _i32]),
+            "fv_mesh_get_tiling": (ctypes.c_int, [_vp, _P(_i32), _P(_i32)]),
+            "fv_mesh_nodes": (ctypes.c_int, [_vp, _P(_i64), _vp, _P(_i32)]),
             "fv_mesh_tile_halo": (ctypes.c_int, [_vp, _i32, _i64, _vp, _i64, _P(_i64), _P(_i64)]),
             "fv_mesh_autotune": (ctypes.c_int, [_vp, _vp, _i32, _vp, _P(_i32), _P(_dbl)]),
             "fv_step": (ctypes.c_int, [_vp, _vp, _i64, _dbl, _dbl, _i32, _vp, _vp, _P(_dbl)]),
@@ -239,16 +242,38 @@ class Mesh:
         (larger one-sided |u_n| + c, Rusanov)."""
         _check(load().fv_mesh_set_wave_speed(self._h, {"average": 0, "max": 1}[mode]))
 
+    def set_geometry(self, form: str):
+        """'stored' (precomputed normals and 1/V, default) or 'vertex'
+        (normals and 1/V formed from node coordinates on a fixed-point grid;
+        FP32, tile shape).  The first 'vertex' snaps the nodes to the grid."""
+        _check(load().fv_mesh_set_geometry(self._h, {"stored": 0, "vertex": 1}[form]))
+
+    def nodes(self):
+        """(node coordinates [n_nodes, 2] as the geometry uses them, grid
+        exponent e of the spacing 2^e or None when not snapped)."""
+        nn, e = _i64(), _i32()
+        _check(load().fv_mesh_nodes(self._h, ctypes.byref(nn), None, None))
+        xy = np.zeros((max(nn.value, 1), 2), np.float64)
+        _check(load().fv_mesh_nodes(self._h, ctypes.byref(nn), _np_ptr(xy), ctypes.byref(e)))
+        return xy[:nn.value].copy(), (None if e.value == -2**31 else int(e.value))
+
     def set_launch_chaining(self, enable: bool):
         """Programmatic dependent launch of the step kernels (default on)."""
         _check(load().fv_mesh_set_launch_chaining(self._h, int(bool(enable))))
 
     def set_blocking(self, steps_per_launch: int, tile_cells: int = 0, staged: bool = False):
         """1: one launch per step; 2: two forward-Euler steps per launch on
-        shared-memory tiles of `tile_cells` cells (0 = 1024); staged: tile
-        records by bulk copies into double-buffered shared memory."""
+        shared-memory tiles of `tile_cells` cells (0 = 1024; with 1, the tile
+        size of the one-step tile shape, 32..2048); staged: tile records by
+        bulk copies into double-buffered shared memory."""
         _check(load().fv_mesh_set_blocking(self._h, int(steps_per_launch), int(tile_cells),
                                            int(bool(staged))))
+
+    def tiling(self):
+        """(step-kernel shape, tile size in cells of the tiled shapes)."""
+        v, t = _i32(), _i32()
+        _check(load().fv_mesh_get_tiling(self._h, ctypes.byref(v), ctypes.byref(t)))
+        return int(v.value), int(t.value)
 
     def tile_halo(self, tile_cells: int, tile: int):
         """(first halo, second halo) of a two-step tile, as global cell ids."""

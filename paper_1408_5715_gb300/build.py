@@ -19,7 +19,8 @@ OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libfvgb300.so")
 BUILD_DIR = os.path.join(PKG, "_build")
 
-SOURCES = ["host_mesh.cpp", "renumber.cpp", "partition.cpp", "tiles.cpp", "kernels.cu", "tma_step.cu",
+SOURCES = ["host_mesh.cpp", "renumber.cpp", "partition.cpp", "tiles.cpp", "vertex_geom.cpp",
+           "kernels.cu", "tma_step.cu",
            "tile_step.cu",
            "pair_step.cu", "closure.cu",
            "capi.cu", "totals_noalloc.cu"]

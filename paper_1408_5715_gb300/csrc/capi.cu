@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <iterator>
 #include <new>
 #include <string>
 #include <vector>
@@ -123,6 +124,14 @@ struct fv_mesh {
   int* d_halo_id = nullptr;
   uint2* d_halo_ln = nullptr;
   int p_e_cap = 0, p_t1_cap = 0;
+  // normals from vertex coordinates (fv_mesh_set_geometry): tile nodes
+  int geometry = FV_GEOM_STORED;
+  bool tiles_vertex = false;  // the tile arrays above carry the vertex layout
+  unsigned* d_cell_vl = nullptr;
+  int* d_tile_voff = nullptr;
+  int2* d_tile_vq = nullptr;
+  float* d_inv_vol = nullptr;  // FP32 1/V per cell
+  int p_v_cap = 0;
   unsigned wait_limit = fv::kDefaultWaitLimit;  // bounded device waits (variant 5)
   fv::LoopScalars* d_scal = nullptr;
   double* d_partials = nullptr;
@@ -163,8 +172,16 @@ struct fv_mesh {
     dev_free(d_tile_info);
     dev_free(d_halo_id);
     dev_free(d_halo_ln);
+    dev_free(d_cell_vl);
+    dev_free(d_tile_voff);
+    dev_free(d_tile_vq);
+    dev_free(d_inv_vol);
     tiles_built = 0;
+    tiles_vertex = false;
+    p_v_cap = 0;
   }
+
+  bool vertex_tiles() const { return geometry == FV_GEOM_VERTEX; }
 
   void free_device() {
     drop_graph();
@@ -191,10 +208,32 @@ namespace {
 bool uses_tiles(const fv_mesh* m) { return m->blocking == 2 || m->variant == fv::kTileVariant; }
 
 void ensure_tiles(fv_mesh* m, cudaStream_t s) {
-  if (!uses_tiles(m) || m->h.n == 0 || m->tiles_built == m->pair_tile) return;
+  if (!uses_tiles(m) || m->h.n == 0 ||
+      (m->tiles_built == m->pair_tile && m->tiles_vertex == m->vertex_tiles()))
+    return;
   m->free_tiles();
   m->drop_graph();
-  const fv::PairTiles L = fv::build_pair_tiles(m->h, m->pair_tile);
+  fv::PairTiles L = fv::build_pair_tiles(m->h, m->pair_tile);
+  fv::TileVertices V;
+  if (m->vertex_tiles()) {
+    V = fv::build_tile_vertices(m->h, m->pair_tile);
+    for (int64_t c = 0; c < m->h.n; ++c) L.cell_ln[2 * c + 1] |= (uint32_t)V.v0[c] << 16;
+    const size_t ncells = (size_t)m->h.n;
+    FV_CUDA(cudaMalloc((void**)&m->d_cell_vl, ncells * sizeof(unsigned)));
+    FV_CUDA(cudaMalloc((void**)&m->d_inv_vol, ncells * sizeof(float)));
+    V.inv_vol.resize(ncells);  // the FP32 1/V of the geometry records
+    for (size_t c = 0; c < ncells; ++c) V.inv_vol[c] = (float)(1.0 / m->h.vol[c]);
+    FV_CUDA(cudaMemcpyAsync(m->d_inv_vol, V.inv_vol.data(), ncells * sizeof(float),
+                            cudaMemcpyHostToDevice, s));
+    FV_CUDA(cudaMalloc((void**)&m->d_tile_voff, V.voff.size() * sizeof(int32_t)));
+    FV_CUDA(cudaMalloc((void**)&m->d_tile_vq, std::max<size_t>(V.vq.size(), 2) * sizeof(int32_t)));
+    FV_CUDA(cudaMemcpyAsync(m->d_cell_vl, V.cell_vl.data(), ncells * sizeof(unsigned),
+                            cudaMemcpyHostToDevice, s));
+    FV_CUDA(cudaMemcpyAsync(m->d_tile_voff, V.voff.data(), V.voff.size() * sizeof(int32_t),
+                            cudaMemcpyHostToDevice, s));
+    FV_CUDA(cudaMemcpyAsync(m->d_tile_vq, V.vq.data(), V.vq.size() * sizeof(int32_t),
+                            cudaMemcpyHostToDevice, s));
+  }
   // whole 256-cell tiles: the staged kernel copies an even number of records
   const size_t ncells = (size_t)((m->h.n + fv::kPadCells - 1) / fv::kPadCells * fv::kPadCells);
   FV_CUDA(cudaMalloc((void**)&m->d_cell_ln, ncells * sizeof(uint2)));
@@ -215,7 +254,14 @@ void ensure_tiles(fv_mesh* m, cudaStream_t s) {
   FV_CUDA(cudaStreamSynchronize(s));  // L is a local staging buffer
   m->p_e_cap = L.e_cap;
   m->p_t1_cap = L.t1_cap;
+  m->p_v_cap = V.v_cap;
+  m->tiles_vertex = m->vertex_tiles();
   m->tiles_built = m->pair_tile;
+}
+
+// Shared memory of the one-step tile kernel of this mesh.
+size_t tile_smem(const fv_mesh* m) {
+  return fv::tile_smem_bytes(m->f64(), m->p_t1_cap, m->tiles_vertex ? m->p_v_cap : 0);
 }
 
 // Shared memory a tiled kernel of this mesh needs, checked against the device.
@@ -227,6 +273,25 @@ void check_tile_smem(const fv_mesh* m, size_t smem) {
     invalid("a tile with its halos needs " + std::to_string(smem) + " bytes of shared memory (" +
             std::to_string(optin) + " available); renumber the cells with a compact order "
             "(Hilbert) or use smaller tiles");
+}
+
+// Tile sizes the autotuner times for the one-step tile shape: the standard
+// ones, and on a mesh of a few waves of resident blocks the sizes that fill
+// whole waves (w waves of b blocks per SM), which avoid a last, partly
+// filled wave.
+std::vector<int> tile_candidates(int64_t n) {
+  std::vector<int> t(std::begin(fv::kPairTiles), std::end(fv::kPairTiles));
+  int dev = 0, sms = 0;
+  FV_CUDA(cudaGetDevice(&dev));
+  FV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  for (int b : {5, 4, 2})  // resident blocks per SM of the FP32 / FP64 shapes
+    for (int w = 1; w <= 3; ++w) {
+      const int64_t slots = (int64_t)w * b * sms;
+      const int64_t c = ((n + slots - 1) / slots + 31) / 32 * 32;
+      if (c >= 64 && c <= fv::kMaxTileCells && std::find(t.begin(), t.end(), (int)c) == t.end())
+        t.push_back((int)c);
+    }
+  return t;
 }
 
 size_t pair_smem(const fv_mesh* m) {
@@ -298,6 +363,14 @@ fv::StepArgs base_args(const fv_mesh* m) {
     a.halo_id = m->d_halo_id;
     a.tile = m->tiles_built;
     a.t1_cap = m->p_t1_cap;
+    if (m->tiles_vertex) {
+      a.cell_vl = m->d_cell_vl;
+      a.tile_voff = m->d_tile_voff;
+      a.tile_vq = m->d_tile_vq;
+      a.inv_vol = m->d_inv_vol;
+      a.v_cap = m->p_v_cap;
+      a.vscale = (float)std::ldexp(1.0, m->h.grid_e);
+    }
   }
   return a;
 }
@@ -314,7 +387,7 @@ void enqueue_steps(fv_mesh* m, void* U, int64_t j0, int64_t count, double cfl, d
                    bool lo_alt = false) {
   fv::LoopScalars* sc = m->d_scal;
   if (!cl && m->variant == fv::kTileVariant && count > 0)
-    check_tile_smem(m, fv::tile_smem_bytes(m->f64(), m->p_t1_cap));
+    check_tile_smem(m, tile_smem(m));
   for (int64_t j = j0; j < j0 + count; ++j) {
     fv::StepArgs a = base_args(m);
     a.bmin_read = &sc->bmin[j % 3];
@@ -576,7 +649,10 @@ int fv_mesh_set_blocking(fv_mesh* mesh, int32_t steps_per_launch, int32_t tile_c
     if (tile_cells == 0) tile_cells = 1024;
     bool known = false;
     for (int t : fv::kPairTiles) known = known || t == tile_cells;
-    if (!known) invalid("tile_cells must be 0, 512, 768, 1024 or 2048");
+    if (steps_per_launch == 2 && !known)
+      invalid("with two steps per launch tile_cells must be 0, 512, 768, 1024 or 2048");
+    if (tile_cells < 32 || tile_cells > fv::kMaxTileCells)
+      invalid("tile_cells must be 0 or 32 .. 2048");
     if (staged && tile_cells != 512 && tile_cells != 1024)
       invalid("the staged kernel takes tiles of 512 or 1024 cells");
     if (steps_per_launch == 2 && mesh->f64())
@@ -587,6 +663,14 @@ int fv_mesh_set_blocking(fv_mesh* mesh, int32_t steps_per_launch, int32_t tile_c
     mesh->pair_tile = tile_cells;
     mesh->pair_staged = staged;
     mesh->drop_graph();
+  });
+}
+
+int fv_mesh_get_tiling(const fv_mesh* mesh, int32_t* variant, int32_t* tile_cells) {
+  return guarded([&] {
+    check_mesh(mesh);
+    if (variant) *variant = mesh->variant;
+    if (tile_cells) *tile_cells = mesh->pair_tile;
   });
 }
 
@@ -604,6 +688,37 @@ int fv_mesh_tile_halo(const fv_mesh* mesh, int32_t tile_cells, int64_t tile, int
       if (capacity < h12) invalid("halo_ids capacity too small");
       std::memcpy(halo_ids, L.halo_id.data() + hs, h12 * sizeof(int32_t));
     }
+  });
+}
+
+int fv_mesh_set_geometry(fv_mesh* mesh, int32_t form) {
+  return guarded([&] {
+    check_mesh(mesh);
+    if (form == FV_GEOM_STORED) {
+      mesh->geometry = form;
+    } else if (form == FV_GEOM_VERTEX) {
+      if (mesh->f64())
+        invalid("vertex geometry is built for FV_F32 meshes (the FP64 step is bound by "
+                "arithmetic, not by memory)");
+      if (!mesh->h.snapped()) {
+        fv::snap_to_vertex_grid(mesh->h);  // throws before changing the mesh
+        mesh->dirty = true;                // geometry records of the snapped mesh
+      }
+      mesh->geometry = form;
+      mesh->variant = fv::kTileVariant;
+    } else {
+      invalid("unknown geometry form");
+    }
+    mesh->drop_graph();
+  });
+}
+
+int fv_mesh_nodes(const fv_mesh* mesh, int64_t* n_nodes, double* xy, int32_t* grid_exponent) {
+  return guarded([&] {
+    check_mesh(mesh);
+    if (n_nodes) *n_nodes = (int64_t)mesh->h.node_xy.size() / 2;
+    if (xy) std::memcpy(xy, mesh->h.node_xy.data(), mesh->h.node_xy.size() * sizeof(double));
+    if (grid_exponent) *grid_exponent = mesh->h.snapped() ? mesh->h.grid_e : INT32_MIN;
   });
 }
 
@@ -673,17 +788,18 @@ int fv_mesh_autotune(fv_mesh* mesh, const void* U, int32_t scheme, void* stream,
       for (int v = 0; v < fv::kStepVariants; ++v) {
         mesh->variant = v;
         if (v != fv::kTileVariant) {
-          times[v] = time_shape();
+          // vertex geometry is a layout of the tile shape
+          times[v] = mesh->vertex_tiles() ? INFINITY : time_shape();
           continue;
         }
         // the tile shape at each tile size; tiles that do not fit (a
         // long-band order) leave that size out
         times[v] = INFINITY;
-        for (int tile : fv::kPairTiles) {
+        for (int tile : tile_candidates(n)) {
           mesh->pair_tile = tile;
           try {
             ensure_tiles(mesh, s);
-            check_tile_smem(mesh, fv::tile_smem_bytes(mesh->f64(), mesh->p_t1_cap));
+            check_tile_smem(mesh, tile_smem(mesh));
           } catch (const fv::Error&) {
             continue;
           }
@@ -706,8 +822,8 @@ int fv_mesh_autotune(fv_mesh* mesh, const void* U, int32_t scheme, void* stream,
     cudaEventDestroy(e1);
     FV_CUDA(cudaStreamSynchronize(s));
     cudaFree(tmp);
-    int b = 0;
-    for (int v = 1; v < fv::kStepVariants; ++v)
+    int b = mesh->vertex_tiles() ? fv::kTileVariant : 0;
+    for (int v = 0; v < fv::kStepVariants; ++v)
       if (times[v] < times[b]) b = v;
     mesh->variant = b;
     // the tile size of the tiled shapes: the fastest for shape 6 when it wins
@@ -831,10 +947,13 @@ int fv_residual(fv_mesh* mesh, const void* U, void* R, const fv_closure* closure
     fv::StepArgs a = base_args(mesh);
     a.U = U;
     a.out = R;
+    // one thread per cell; the tile shape with vertex geometry (same bits)
+    const int shape = mesh->vertex_tiles() ? fv::kTileVariant : 0;
+    if (shape == fv::kTileVariant) check_tile_smem(mesh, tile_smem(mesh));
     if (closure)
       FV_CUDA(fv::launch_step_closure(fv::kModeResidual, a, closure->params(), s));
     else
-      FV_CUDA(fv::launch_step(mesh->f64(), fv::kModeResidual, 0, a, s));
+      FV_CUDA(fv::launch_step(mesh->f64(), fv::kModeResidual, shape, a, s));
   });
 }
 

@@ -25,6 +25,16 @@ struct HostMesh {
   std::vector<double> vol;      // [n]  triangle area V_T
   std::vector<double> inradius; // [n]  2 V_T / P_T (P_T perimeter): CFL length scale
   std::vector<double> cen;      // [2n] centroid (for the Hilbert order)
+  std::vector<int32_t> vtx;     // [3n] nodes of each cell, counter-clockwise: face k runs
+                                //      from vtx[3c+k] to vtx[3c+(k+1)%3]
+  // nodes as given to fv_mesh_create (snapped by fv_mesh_set_geometry)
+  std::vector<double> node_xy;     // [2 n_nodes]
+  std::vector<int32_t> node_canon; // [n_nodes] periodic identification; empty: identity
+  // vertex geometry (empty / 0 until the nodes are snapped to the grid)
+  std::vector<int32_t> node_q;     // [2 n_nodes] grid coordinates: x = grid_cx + q * 2^grid_e
+  int32_t grid_e = 0;
+  double grid_cx = 0.0, grid_cy = 0.0;
+  bool snapped() const { return !node_q.empty(); }
 };
 
 // Builds the host mesh; throws fv::Error{FV_EINVAL, ...} for malformed input.
@@ -49,6 +59,12 @@ struct DeviceLayout {
 };
 DeviceLayout pack_layout(const int32_t* nbr, const double* nrm, const double* vol,
                          const double* inradius, int64_t n, int32_t meta, bool f64);
+
+// Snaps the cells' nodes to a grid of spacing 2^e (vertex_geom.cpp) and
+// rebuilds normals and areas from the grid coordinates; throws FV_EINVAL when
+// the mesh does not fit the grid's 31-bit range or a face pair loses its
+// exact negation.
+void snap_to_vertex_grid(HostMesh& m);
 
 // Partitioning into contiguous ranges of the current numbering (partition.cpp).
 struct PartRange {
@@ -82,6 +98,20 @@ struct PairTiles {
   int32_t t1_cap = 0;  // max over tiles of tile + first halo
 };
 PairTiles build_pair_tiles(const HostMesh& m, int32_t tile);
+
+// The nodes of each tile for normals formed from vertex coordinates
+// (vertex_geom.cpp).  Tile b's nodes are vq[2 voff[b] ..] (grid coordinates,
+// duplicated where tiles share nodes); each cell's three nodes are 16-bit
+// tile-local ids v0 (the high half of cell_ln's second word) and v1 | v2 << 16.
+struct TileVertices {
+  std::vector<int32_t> voff;      // [n_tiles + 1]
+  std::vector<int32_t> vq;        // [2 voff[n_tiles]]
+  std::vector<uint32_t> cell_vl;  // [n] v1 | v2 << 16
+  std::vector<uint16_t> v0;       // [n]
+  std::vector<float> inv_vol;     // [n] FP32 1/V (filled at upload)
+  int32_t v_cap = 0;              // max nodes of a tile
+};
+TileVertices build_tile_vertices(const HostMesh& m, int32_t tile);
 
 // Sec. 4.1 diagnostics on the cell graph of the current numbering.
 int64_t graph_bandwidth(const HostMesh& m);

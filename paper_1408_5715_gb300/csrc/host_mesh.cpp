@@ -48,6 +48,14 @@ void build_host_mesh(const double* xy, int64_t n_nodes, const int32_t* tri, int6
   m.vol.assign(n, 0.0);
   m.inradius.assign(n, 0.0);
   m.cen.assign(2 * n, 0.0);
+  m.node_xy.assign(xy, xy + 2 * (n_tri > 0 ? n_nodes : 0));
+  if (canon && n_tri > 0)
+    m.node_canon.assign(canon, canon + n_nodes);
+  else
+    m.node_canon.clear();
+  m.node_q.clear();
+  m.grid_e = 0;
+  m.grid_cx = m.grid_cy = 0.0;
 
   // oriented vertex triples
   std::vector<int32_t> v(3 * n);
@@ -140,6 +148,7 @@ void build_host_mesh(const double* xy, int64_t n_nodes, const int32_t* tri, int6
     for (int k = 0; k < 3; ++k) perim += std::hypot(m.nrm[6 * c + 2 * k], m.nrm[6 * c + 2 * k + 1]);
     m.inradius[c] = 2.0 * m.vol[c] / perim;
   }
+  m.vtx = std::move(v);
 }
 
 DeviceLayout pack_layout(const int32_t* nbr, const double* nrm, const double* vol,

@@ -80,6 +80,18 @@ struct StepArgs {
   const int* halo_id;
   int tile;
   int t1_cap;
+  // Vertex geometry of the tile variant (FP32; vertex_geom.cpp), or nullptr:
+  // normals formed from grid coordinates of the tile's nodes and 1/V read
+  // from inv_vol instead of the geom records.  tile_vq[2 tile_voff[b] ..]
+  // are tile b's nodes (int32 x, y); a cell's nodes are tile-local ids
+  // cell_ln[i].y >> 16 and the two halves of cell_vl[i]; v_cap is the most
+  // nodes of a tile.  Normal = grid edge rotated, times vscale = 2^e.
+  const unsigned* cell_vl;
+  const int* tile_voff;
+  const int2* tile_vq;
+  const float* inv_vol;
+  int v_cap;
+  float vscale;
   // launch as part of a programmatic chain (launch_util.cuh)
   bool chained;
   // kWaveAverage or kWaveMax (shapes 0, 1 and 6; the others run shape 1)
@@ -151,8 +163,8 @@ cudaError_t launch_pack_closure(const float* theta, unsigned* w1, unsigned* w2, 
 constexpr int kStepVariants = 7;
 constexpr int kTileVariant = 6;
 // shared memory of the tile variant: state and primitives of tile + halo
-inline size_t tile_smem_bytes(bool f64, int t1_cap) {
-  return (size_t)t1_cap * 2 * (f64 ? 32 : 16);
+inline size_t tile_smem_bytes(bool f64, int t1_cap, int v_cap = 0) {
+  return (size_t)t1_cap * 2 * (f64 ? 32 : 16) + (size_t)v_cap * 8;
 }
 cudaError_t launch_step_tile(bool f64, int mode, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_batch_step_tile(bool f64, int mode, const BatchArgs& b, cudaStream_t s);
@@ -196,6 +208,8 @@ struct PairArgs {
 };
 // tile sizes with a kernel instantiation (the staged kernel: 512 and 1024)
 constexpr int kPairTiles[4] = {512, 768, 1024, 2048};
+// The one-step tile shape takes any tile size from 1 to this many cells.
+constexpr int kMaxTileCells = 2048;
 // dynamic shared memory of one block for the given capacities; the staged
 // kernel adds two stages of the tile's own records (64 bytes a cell each)
 inline size_t pair_smem_bytes(int e_cap, int t1_cap, int tile, bool staged) {

@@ -294,6 +294,13 @@ void apply_permutation(HostMesh& m, const std::vector<int32_t>& perm) {
   r.vol.resize(n);
   r.inradius.resize(n);
   r.cen.resize(2 * n);
+  r.vtx.resize(m.vtx.size());
+  r.node_xy = std::move(m.node_xy);
+  r.node_canon = std::move(m.node_canon);
+  r.node_q = std::move(m.node_q);
+  r.grid_e = m.grid_e;
+  r.grid_cx = m.grid_cx;
+  r.grid_cy = m.grid_cy;
   for (int64_t i = 0; i < n; ++i) {
     int64_t o = perm[i];
     for (int k = 0; k < 3; ++k) {
@@ -305,6 +312,8 @@ void apply_permutation(HostMesh& m, const std::vector<int32_t>& perm) {
     r.inradius[i] = m.inradius[o];
     r.cen[2 * i] = m.cen[2 * o];
     r.cen[2 * i + 1] = m.cen[2 * o + 1];
+    if (!r.vtx.empty())
+      for (int k = 0; k < 3; ++k) r.vtx[3 * i + k] = m.vtx[3 * o + k];
   }
   m = std::move(r);
 }

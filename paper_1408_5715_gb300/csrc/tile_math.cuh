@@ -50,8 +50,27 @@ __device__ __forceinline__ R cell_fluxes(const rec_t<R>& g0, const rec_t<R>& g1,
                                          const rec_t<R>* sP, const R* uinf, R acc[4]) {
   R perim = smem_face<R, WAVE>(UL, L, ln.x & 0xffffu, g0.x, g0.y, sU, sP, uinf, acc);
   perim = add(perim, smem_face<R, WAVE>(UL, L, ln.x >> 16, g0.z, g0.w, sU, sP, uinf, acc));
-  perim = add(perim, smem_face<R, WAVE>(UL, L, ln.y, g1.x, g1.y, sU, sP, uinf, acc));
+  // the high half of ln.y holds a node id in the vertex-geometry layout
+  perim = add(perim, smem_face<R, WAVE>(UL, L, ln.y & 0xffffu, g1.x, g1.y, sU, sP, uinf, acc));
   return perim;
+}
+
+// Normals of a cell from the grid coordinates of its nodes q0, q1, q2
+// (counter-clockwise; vertex_geom.cpp): face k's normal is its integer edge
+// (dx, dy) rotated to (dy, -dx), converted with one rounding and scaled by
+// the grid spacing vscale = 2^e -- bitwise the stored FP32 normals of the
+// snapped mesh.  1/V is read (inv_vol), as stored for the snapped mesh;
+// g1.w, unused here, is 0.
+__device__ __forceinline__ void vertex_geometry(int2 q0, int2 q1, int2 q2, float vscale,
+                                                float inv_vol, float4& g0, float4& g1) {
+  g0.x = mul(__int2float_rn(q1.y - q0.y), vscale);
+  g0.y = mul(__int2float_rn(q0.x - q1.x), vscale);
+  g0.z = mul(__int2float_rn(q2.y - q1.y), vscale);
+  g0.w = mul(__int2float_rn(q1.x - q2.x), vscale);
+  g1.x = mul(__int2float_rn(q0.y - q2.y), vscale);
+  g1.y = mul(__int2float_rn(q2.x - q0.x), vscale);
+  g1.z = inv_vol;
+  g1.w = 0.0f;
 }
 
 }  // namespace

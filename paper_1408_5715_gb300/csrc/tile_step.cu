@@ -23,12 +23,60 @@ namespace fv {
 
 namespace {
 
-template <typename R, int MODE, bool COMP, int THREADS, int KMAX, int WAVE>
-__global__ void __launch_bounds__(THREADS) k_step_tile(StepArgs a) {
+// Loads the states of a tile (nt cells from t0) and of its first halo (h1
+// cells whose ids are halo[0 .. h1)) into shared memory with their primitive
+// variables.  With PA > 0 each thread issues the loads of its first PA
+// entries before it uses any, so it waits for about one memory round trip
+// (two for halo cells, whose ids come first) rather than one per entry.
+template <typename R, int THREADS, int PA>
+__device__ __forceinline__ void stage_states(const rec_t<R>* __restrict__ U, int64_t t0, int nt,
+                                             int h1, const int* __restrict__ halo, rec_t<R>* sU,
+                                             rec_t<R>* sP) {
+  const int ne = nt + h1;
+  int e0 = threadIdx.x;
+  if constexpr (PA > 0) {
+    rec_t<R> u[PA];
+#pragma unroll
+    for (int k = 0; k < PA; ++k) {
+      const int e = threadIdx.x + k * THREADS;
+      if (e < ne) u[k] = Rec<R>::ld(U + (e < nt ? t0 + e : (int64_t)__ldg(halo + (e - nt))));
+    }
+#pragma unroll
+    for (int k = 0; k < PA; ++k) {
+      const int e = threadIdx.x + k * THREADS;
+      if (e < ne) {
+        sU[e] = u[k];
+        sP[e] = prim_rec<R>(primitive<R>(u[k]));
+      }
+    }
+    e0 += PA * THREADS;
+  }
+  for (int e = e0; e < ne; e += THREADS) {
+    const rec_t<R> u = Rec<R>::ld(U + (e < nt ? t0 + e : (int64_t)__ldg(halo + (e - nt))));
+    sU[e] = u;
+    sP[e] = prim_rec<R>(primitive<R>(u));
+  }
+}
+
+// Loads per thread issued together by stage_states: FP32 tiles with a ring
+// of up to two block-widths of halo cells in one batch; FP64 (bound by its
+// arithmetic, with twice the registers per state) one at a time.
+template <typename R, int KMAX>
+constexpr int kStageBatch = sizeof(R) == 4 ? KMAX + 2 : 0;
+
+// VTX (FP32 only): normals from the grid coordinates of the tile's nodes,
+// staged in shared memory after the states (vertex_geom.cpp), and 1/V from a
+// 4-byte array, instead of each cell's 32-byte geometry record.
+// FP32 keeps 1280 threads per SM resident (five blocks of 256: at most 48
+// registers); FP64 needs its registers.
+template <typename R, int MODE, bool COMP, int THREADS, int KMAX, int WAVE, bool VTX>
+__global__ void __launch_bounds__(THREADS, sizeof(R) == 4 ? 1280 / THREADS : 1)
+    k_step_tile(StepArgs a) {
   chain_entry();
   extern __shared__ __align__(128) unsigned char smem_raw[];
   rec_t<R>* sU = reinterpret_cast<rec_t<R>*>(smem_raw);  // [t1_cap] states
   rec_t<R>* sP = sU + a.t1_cap;                            // [t1_cap] (u, v, p, c)
+  int2* sQ = reinterpret_cast<int2*>(sP + a.t1_cap);       // [v_cap] node grid coordinates
   const rec_t<R>* __restrict__ U = static_cast<const rec_t<R>*>(a.U);
   const rec_t<R>* __restrict__ geom = static_cast<const rec_t<R>*>(a.geom);
   rec_t<R>* out = static_cast<rec_t<R>*>(a.out);
@@ -39,11 +87,27 @@ __global__ void __launch_bounds__(THREADS) k_step_tile(StepArgs a) {
   // dt formed once per block (FP64 scalar work), read after the barrier
   __shared__ double s_t, s_dt;
   if (threadIdx.x == 0 && MODE != kModeResidual) block_dt(a, s_t, s_dt);
-  for (int e = threadIdx.x; e < nt + h1; e += THREADS) {
-    const int64_t g = e < nt ? t0 + e : (int64_t)__ldg(a.halo_id + hs + (e - nt));
-    const rec_t<R> u = Rec<R>::ld(U + g);
-    sU[e] = u;
-    sP[e] = prim_rec<R>(primitive<R>(u));
+  // the tile's node coordinates: loads issued with the states', stored after
+  constexpr int VA = KMAX / 2 + 1;  // per thread: 3 x 256 for the ~600 nodes of 1024 cells
+  int2 qv[VTX ? VA : 1];
+  int vb = 0, nv = 0;
+  if constexpr (VTX) {
+    vb = __ldg(a.tile_voff + blockIdx.x);
+    nv = __ldg(a.tile_voff + blockIdx.x + 1) - vb;
+#pragma unroll
+    for (int k = 0; k < VA; ++k) {
+      const int e = threadIdx.x + k * THREADS;
+      if (e < nv) qv[k] = __ldg(a.tile_vq + vb + e);
+    }
+  }
+  stage_states<R, THREADS, kStageBatch<R, KMAX>>(U, t0, nt, h1, a.halo_id + hs, sU, sP);
+  if constexpr (VTX) {
+#pragma unroll
+    for (int k = 0; k < VA; ++k) {
+      const int e = threadIdx.x + k * THREADS;
+      if (e < nv) sQ[e] = qv[k];
+    }
+    for (int e = threadIdx.x + VA * THREADS; e < nv; e += THREADS) sQ[e] = __ldg(a.tile_vq + vb + e);
   }
   __syncthreads();
   const double t = MODE != kModeResidual ? s_t : 0.0, dt = MODE != kModeResidual ? s_dt : 0.0;
@@ -56,13 +120,19 @@ __global__ void __launch_bounds__(THREADS) k_step_tile(StepArgs a) {
     if (e < nt) {
       const int64_t i = t0 + e;
       CellIn<R> c;
-      c.g0 = Rec<R>::ld(geom + 2 * i);
-      c.g1 = Rec<R>::ld(geom + 2 * i + 1);
+      const uint2 ln = __ldg(a.cell_ln + i);
+      if constexpr (VTX) {
+        const unsigned vl = __ldg(a.cell_vl + i);
+        vertex_geometry(sQ[ln.y >> 16], sQ[vl & 0xffffu], sQ[vl >> 16], a.vscale,
+                        __ldg(a.inv_vol + i), c.g0, c.g1);
+      } else {
+        c.g0 = Rec<R>::ld(geom + 2 * i);
+        c.g1 = Rec<R>::ld(geom + 2 * i + 1);
+      }
       c.U = sU[e];
       if (MODE == kModeRK2b) c.base = static_cast<const rec_t<R>*>(a.Ubase)[i];
       if (COMP && MODE != kModeResidual) c.lo = a.lo[i];
       if (COMP && MODE == kModeRK2b) c.lo_stage = a.lo_stage[i];
-      const uint2 ln = __ldg(a.cell_ln + i);
       R acc[4] = {R(0), R(0), R(0), R(0)};
       const R perim = cell_fluxes<R, WAVE>(c.g0, c.g1, ln, c.U, rec_prim<R>(sP[e]), sU, sP,
                                            far_field<R>(a), acc);
@@ -114,12 +184,7 @@ __global__ void __launch_bounds__(THREADS) k_step_tile_batch(BatchArgs b) {
     s_t = t;
     s_dt = dt;
   }
-  for (int e = threadIdx.x; e < nt + h1; e += THREADS) {
-    const int64_t g = e < nt ? t0 + e : (int64_t)__ldg(a.halo_id + hs + (e - nt));
-    const rec_t<R> u = Rec<R>::ld(U + g);
-    sU[e] = u;
-    sP[e] = prim_rec<R>(primitive<R>(u));
-  }
+  stage_states<R, THREADS, kStageBatch<R, KMAX>>(U, t0, nt, h1, a.halo_id + hs, sU, sP);
   __syncthreads();
   const double t = MODE != kModeResidual ? s_t : 0.0, dt = MODE != kModeResidual ? s_dt : 0.0;
   const R dtR = R(dt);
@@ -177,35 +242,35 @@ cudaError_t launch_tile_batch_mode(int mode, const BatchArgs& b, cudaStream_t s)
   }
 }
 
-template <typename R, int MODE, bool COMP, int THREADS, int KMAX>
+template <typename R, int MODE, bool COMP, int THREADS, int KMAX, bool VTX>
 cudaError_t launch_tile_t(const StepArgs& a, cudaStream_t s) {
-  auto k = a.wave == kWaveMax ? k_step_tile<R, MODE, COMP, THREADS, KMAX, kWaveMax>
-                              : k_step_tile<R, MODE, COMP, THREADS, KMAX, kWaveAverage>;
-  const size_t smem = tile_smem_bytes(sizeof(R) == 8, a.t1_cap);
+  auto k = a.wave == kWaveMax ? k_step_tile<R, MODE, COMP, THREADS, KMAX, kWaveMax, VTX>
+                              : k_step_tile<R, MODE, COMP, THREADS, KMAX, kWaveAverage, VTX>;
+  const size_t smem = tile_smem_bytes(sizeof(R) == 8, a.t1_cap, VTX ? a.v_cap : 0);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int64_t tiles = (a.n + a.tile - 1) / a.tile;
   return launch_chained(k, (unsigned)tiles, THREADS, smem, s, a.chained, a);
 }
 
-template <typename R, int MODE, bool COMP>
+// Any tile size up to 2048 cells: the block shape whose KMAX x THREADS cells
+// cover it (the cells of a tile beyond nt are skipped).
+template <typename R, int MODE, bool COMP, bool VTX>
 cudaError_t launch_tile_size(const StepArgs& a, cudaStream_t s) {
-  switch (a.tile) {
-    case 512: return launch_tile_t<R, MODE, COMP, 256, 2>(a, s);
-    case 768: return launch_tile_t<R, MODE, COMP, 256, 3>(a, s);
-    case 1024: return launch_tile_t<R, MODE, COMP, 256, 4>(a, s);
-    case 2048: return launch_tile_t<R, MODE, COMP, 512, 4>(a, s);
-    default: return cudaErrorInvalidValue;
-  }
+  if (a.tile < 1 || a.tile > kMaxTileCells) return cudaErrorInvalidValue;
+  if (a.tile <= 512) return launch_tile_t<R, MODE, COMP, 256, 2, VTX>(a, s);
+  if (a.tile <= 768) return launch_tile_t<R, MODE, COMP, 256, 3, VTX>(a, s);
+  if (a.tile <= 1024) return launch_tile_t<R, MODE, COMP, 256, 4, VTX>(a, s);
+  return launch_tile_t<R, MODE, COMP, 512, 4, VTX>(a, s);
 }
 
-template <typename R, bool COMP>
+template <typename R, bool COMP, bool VTX = false>
 cudaError_t launch_tile_mode(int mode, const StepArgs& a, cudaStream_t s) {
   switch (mode) {
-    case kModeFE: return launch_tile_size<R, kModeFE, COMP>(a, s);
-    case kModeRK2a: return launch_tile_size<R, kModeRK2a, COMP>(a, s);
-    case kModeRK2b: return launch_tile_size<R, kModeRK2b, COMP>(a, s);
-    case kModeResidual: return launch_tile_size<R, kModeResidual, false>(a, s);
+    case kModeFE: return launch_tile_size<R, kModeFE, COMP, VTX>(a, s);
+    case kModeRK2a: return launch_tile_size<R, kModeRK2a, COMP, VTX>(a, s);
+    case kModeRK2b: return launch_tile_size<R, kModeRK2b, COMP, VTX>(a, s);
+    case kModeResidual: return launch_tile_size<R, kModeResidual, false, VTX>(a, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -223,6 +288,11 @@ cudaError_t launch_batch_step_tile(bool f64, int mode, const BatchArgs& b, cudaS
 cudaError_t launch_step_tile(bool f64, int mode, const StepArgs& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
   if (!a.cell_ln || !a.tile_info || !a.halo_id) return cudaErrorInvalidValue;
+  if (a.tile_vq) {
+    if (f64 || !a.cell_vl || !a.tile_voff || !a.inv_vol) return cudaErrorInvalidValue;
+    if (a.lo) return launch_tile_mode<float, true, true>(mode, a, s);
+    return launch_tile_mode<float, false, true>(mode, a, s);
+  }
   if (f64) return launch_tile_mode<double, false>(mode, a, s);
   if (a.lo) return launch_tile_mode<float, true>(mode, a, s);
   return launch_tile_mode<float, false>(mode, a, s);

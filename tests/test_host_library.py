@@ -225,12 +225,20 @@ def test_two_step_blocking_validation():
         m64.set_blocking(2)
     m64.set_blocking(1)
     m32 = B.Mesh.from_input(W.periodic_square(8, 8, seed=1), "f32")
-    for bad in [(3, 0), (0, 0), (2, 100), (2, 4096), (2, 2048, True), (2, 768, True)]:
+    for bad in [(3, 0), (0, 0), (2, 100), (2, 4096), (2, 2048, True), (2, 768, True),
+                (2, 672), (1, 16), (1, 4096)]:
         with pytest.raises(B.FVError):
             m32.set_blocking(*bad)
     m32.set_blocking(2, 512)
     m32.set_blocking(2, 1024, True)
     m32.set_blocking(2, 768)
+    # one step per launch: the tile shape takes any size from 32 to 2048 cells
+    m32.set_variant(6)
+    for tile in (32, 672, 1344, 2048):
+        m32.set_blocking(1, tile)
+        assert m32.tiling() == (6, tile)
+    m32.set_blocking(1, 0)
+    assert m32.tiling() == (6, 1024)
 
 
 def test_tile_halo_limit_is_reported():
@@ -245,3 +253,99 @@ def test_tile_halo_limit_is_reported():
     m.renumber("hilbert")
     h1, h2 = m.tile_halo(40000, 0)  # a compact order keeps the same tile legal
     assert 0 < h1.size < 2000 and 0 < h2.size < 2000
+
+
+# -- normals from vertex coordinates (fixed-point node grid) --------------------------------
+
+def _vertex_case(kind):
+    return {"periodic": lambda: W.periodic_square(12, 10, seed=3),
+            "channel": lambda: W.channel_bump(20, 9, seed=4),
+            "step": lambda: W.forward_step(4, 14, 3, 12, seed=6),
+            "two": lambda: W.two_cells()}[kind]()
+
+
+@pytest.mark.parametrize("kind", ["periodic", "channel", "step", "two"])
+def test_vertex_grid_snaps_nodes_and_rebuilds_the_geometry(orc, kind):
+    mi = _vertex_case(kind)
+    m = B.Mesh.from_input(mi, "f32")
+    xy0, e0 = m.nodes()
+    assert e0 is None
+    np.testing.assert_array_equal(xy0, mi.xy)
+    m.set_geometry("vertex")
+    xy, e = m.nodes()
+    s = 2.0 ** e
+    used = np.unique(mi.tri)
+    q = xy[used] / s
+    assert np.array_equal(q, np.round(q))  # grid points
+    ext = max(np.ptp(mi.xy[used, 0]), np.ptp(mi.xy[used, 1]))
+    assert ext / s <= 2**31 - 16 < 2 * ext / s  # the finest spacing that holds the extent
+    assert np.abs(xy[used] - mi.xy[used]).max() <= s  # each node moves by at most one step
+    # the library's geometry is now the snapped mesh's, as the oracle builds
+    # it from the grid points by definition: normals exactly (integer edges
+    # times a power of two), areas to the rounding of the cross product
+    nbr, nrm, area = m.export()
+    om = orc.Mesh(xy, mi.tri, mi.canon, mi.bnd, mi.default_bc)
+    np.testing.assert_array_equal(nbr, om.nbr)
+    np.testing.assert_array_equal(nrm, om.nrm)
+    np.testing.assert_allclose(area, om.vol, rtol=2.0**-52, atol=0)
+    # every interior face: the neighbour's face back has the exact opposite normal
+    c, k = np.nonzero(nbr >= 0)
+    d = nbr[c, k]
+    back = np.zeros(c.size, bool)
+    for k2 in range(3):
+        back |= (nbr[d, k2] == c) & (nrm[d, k2] == -nrm[c, k]).all(-1)
+    assert back.all()
+    # a second call keeps the grid; going back to stored records keeps the nodes
+    m.set_geometry("vertex")
+    m.set_geometry("stored")
+    xy2, e2 = m.nodes()
+    assert e2 == e
+    np.testing.assert_array_equal(xy2, xy)
+
+
+def test_vertex_grid_keeps_periodic_offsets_after_renumbering(orc):
+    mi = W.periodic_square(16, 12, seed=8)
+    m = B.Mesh.from_input(mi, "f32")
+    perm = m.renumber("hilbert")
+    m.set_geometry("vertex")
+    xy, e = m.nodes()
+    # a copy sits a whole number of periods from its canonical node
+    s = 2.0 ** e
+    off = (xy - xy[mi.canon]) / s
+    np.testing.assert_array_equal(off, np.round(off))
+    nbr, nrm, area = m.export()
+    om = orc.Mesh(xy, mi.tri, mi.canon, mi.bnd, mi.default_bc).permuted(perm)
+    np.testing.assert_array_equal(nbr, om.nbr)
+    np.testing.assert_array_equal(nrm, om.nrm)
+
+
+def test_vertex_grid_refusals_leave_the_mesh_unchanged():
+    with pytest.raises(B.FVError, match="FV_F32"):
+        B.Mesh.from_input(W.two_cells(), "f64").set_geometry("vertex")
+    # a sliver thinner than a grid step collapses on the grid
+    xy = np.array([[0.0, 0.0], [1.0, 0.0], [0.5, 1e-12], [0.5, -1.0]])
+    tri = np.array([[0, 1, 2], [0, 3, 1]])
+    m = B.Mesh(xy, tri, default_bc=B.FV_BC_WALL)
+    before = m.export()
+    with pytest.raises(B.FVError, match="collapses") as e:
+        m.set_geometry("vertex")
+    assert e.value.code == B.FV_EINVAL
+    xy2, g = m.nodes()
+    assert g is None
+    np.testing.assert_array_equal(xy2, xy)
+    for a, b in zip(m.export(), before):
+        np.testing.assert_array_equal(a, b)
+    # a periodic copy displaced across the seam by more than a grid step: the
+    # stored records accept it (one normal per face), the grid cannot make
+    # the two sides of its faces opposite
+    mi = W.periodic_square(8, 6, seed=2)
+    xy = mi.xy.copy()
+    j = np.nonzero(mi.canon != np.arange(len(xy)))[0][3]
+    xy[j, 1] += 1e-7
+    m = B.Mesh(xy, mi.tri, mi.canon, mi.bnd, mi.default_bc)
+    m.export()
+    with pytest.raises(B.FVError, match="opposite"):
+        m.set_geometry("vertex")
+    assert m.nodes()[1] is None
+    with pytest.raises(KeyError):
+        m.set_geometry("faces")
