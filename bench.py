@@ -67,8 +67,9 @@ def parse_args():
     p.add_argument("--blocking", type=int, default=1, choices=[1, 2],
                    help="time steps per kernel launch (2: tiles staged in shared memory, "
                         "dt evaluated once per pair)")
-    p.add_argument("--tile", type=int, default=1024, choices=[512, 768, 1024, 2048],
-                   help="cells per tile with --blocking 2")
+    p.add_argument("--tile", type=int, default=1024,
+                   help="cells per tile: with --blocking 2 (512, 768, 1024 or 2048), or with "
+                        "--variant 6 (32 .. 2048)")
     p.add_argument("--staged", action="store_true",
                    help="with --blocking 2: tile records by bulk copies (512 or 1024 cells)")
     p.add_argument("--closure", action="store_true",
@@ -303,6 +304,9 @@ def run_ours(args):
         tune = {"blocking": 2, "tile": args.tile, "staged": args.staged}
     else:
         tune = choose_variant(m, U0dev, args.variant, args.scheme)
+        if args.variant == 6:
+            m.set_blocking(1, args.tile)
+            tune["tile"] = args.tile
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     with ClockSampler(gpu_smi_id()) as clk:
         times = timed_loop(m, U, U0dev, S, args.steps, args.warmup, args.scheme, flush=flush,
