@@ -796,8 +796,9 @@ def forward_step_leg(B, t_end=4.0):
         U0 = torch.tensor(W.uniform_state(mi.n_tri, prim)[perm], dtype=torch.float32,
                           device="cuda")
         U = U0.clone()
+        tune = None
         if timed:
-            choose_variant(m, U0, None)
+            tune = choose_variant(m, U0, None)
             m.step(U, 200, 0.4)  # warm-up (graph capture)
             U.copy_(U0)
         torch.cuda.synchronize()
@@ -816,7 +817,8 @@ def forward_step_leg(B, t_end=4.0):
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         rho = U[:, 0].double()
-        res = {"cells": mi.n_tri, "t_reached": t, "steps_launched": steps, "wall_s": wall}
+        res = {"cells": mi.n_tri, "t_reached": t, "steps_launched": steps, "wall_s": wall,
+               "order": "rcm", "kernel_shape": tune}
         if failed:
             res["failed"] = failed
         else:

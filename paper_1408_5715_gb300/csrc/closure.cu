@@ -549,10 +549,11 @@ __global__ void __launch_bounds__(kGrThreads) k_closure_grad(StepArgs a, const f
       }
       const float invV = c.g1.z;
       const float f = -dt * invV;
+      const float fh = mul(0.5f, f);  // acc holds twice the flux sum
       const float V = 1.0f / invV;
       const float4 ut = Ut[i];
-      const float d[4] = {fma_(f, acc[0], c.U.x) - ut.x, fma_(f, acc[1], c.U.y) - ut.y,
-                          fma_(f, acc[2], c.U.z) - ut.z, fma_(f, acc[3], c.U.w) - ut.w};
+      const float d[4] = {fma_(fh, acc[0], c.U.x) - ut.x, fma_(fh, acc[1], c.U.y) - ut.y,
+                          fma_(fh, acc[2], c.U.z) - ut.z, fma_(fh, acc[3], c.U.w) - ut.w};
       float gU[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {

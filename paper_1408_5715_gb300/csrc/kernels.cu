@@ -69,20 +69,23 @@ __global__ void __launch_bounds__(kBlock, var_min_blocks(VAR)) k_step(StepArgs a
   const R dtR = R(dt);
   R bmin = R(INFINITY);
   bool ok = true;
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // cell ids are 32-bit (a mesh holds fewer than 2^31 / 3 cells): 32-bit
+  // index arithmetic, one wide multiply-add per address
+  const int n = (int)a.n;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (!var_persistent(VAR)) {
-    if (i < a.n) {
+    if (i < n) {
       CellIn<R> cur;
       load_cell<R, MODE, COMP>(a, U, geom, i, cur);
       update_cell<R, MODE, COMP, WAVE>(a, U, out, i, cur, dtR, far_field<R>(a), bmin, ok);
     }
   } else {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int stride = gridDim.x * blockDim.x;
     CellIn<R> cur, nxt;
-    if (i < a.n) load_cell<R, MODE, COMP>(a, U, geom, i, cur);
-    for (; i < a.n; i += stride) {
-      const int64_t j = i + stride;
-      if (j < a.n) load_cell<R, MODE, COMP>(a, U, geom, j, nxt);
+    if (i < n) load_cell<R, MODE, COMP>(a, U, geom, i, cur);
+    for (; i < n; i += stride) {
+      const int j = i + stride;
+      if (j < n) load_cell<R, MODE, COMP>(a, U, geom, j, nxt);
       update_cell<R, MODE, COMP, WAVE>(a, U, out, i, cur, dtR, far_field<R>(a), bmin, ok);
       cur = nxt;
     }

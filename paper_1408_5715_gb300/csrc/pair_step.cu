@@ -60,8 +60,9 @@ __device__ __forceinline__ float cell_fluxes(const float4& g0, const float4& g1,
 template <bool COMP>
 __device__ __forceinline__ float4 fe_update(const float4& UL, float invV, const float acc[4],
                                             float dt, uint2 lo_in, uint2& lo_out) {
+  // acc holds twice the flux sum (face_flux_acc)
   if (COMP) {
-    const float f = mul(-dt, invV);
+    const float f = mul(mul(-0.5f, dt), invV);
     const float u[4] = {UL.x, UL.y, UL.z, UL.w};
     float lo[4], s[4], e[4];
     unpack_rem(lo_in, lo);
@@ -70,7 +71,7 @@ __device__ __forceinline__ float4 fe_update(const float4& UL, float invV, const 
     lo_out = pack_rem(e);
     return make_float4(s[0], s[1], s[2], s[3]);
   }
-  const float f = mul(-dt, invV);
+  const float f = mul(mul(-0.5f, dt), invV);
   return make_float4(fma_(f, acc[0], UL.x), fma_(f, acc[1], UL.y), fma_(f, acc[2], UL.z),
                      fma_(f, acc[3], UL.w));
 }
@@ -157,7 +158,7 @@ __device__ __forceinline__ void step1_halo(const PairArgs& a, int nt, int hs, in
                                            float4* sP1, float dt) {
   for (int e = nt + threadIdx.x; e < nt + h1; e += THREADS) {
     const int j = hs + (e - nt);
-    const int64_t g = __ldg(a.halo_id + j);
+    const int g = __ldg(a.halo_id + j);
     const float4 g0 = __ldg(a.geom + 2 * g), g1 = __ldg(a.geom + 2 * g + 1);
     const uint2 ln = __ldg(a.halo_ln + j);
     const uint2 lo0 = COMP ? __ldg(a.lo_in + g) : make_uint2(0u, 0u);
@@ -189,8 +190,8 @@ __global__ void __launch_bounds__(THREADS) k_step_pair(PairArgs a) {
   float4* sP0 = smem + a.e_cap;       // [e_cap]  their primitives (u, v, p, c)
   float4* sU1 = smem + 2 * a.e_cap;   // [t1_cap] U^{n+1} of tile + first halo
   float4* sP1 = sU1 + a.t1_cap;       // [t1_cap]
-  const int64_t t0 = (int64_t)blockIdx.x * a.tile;
-  const int nt = (int)min((int64_t)a.tile, a.n - t0);
+  const int t0 = blockIdx.x * a.tile;  // cell ids are 32-bit
+  const int nt = min(a.tile, (int)a.n - t0);
   const int hs = __ldg(a.tile_info + 2 * blockIdx.x);
   const int h1 = __ldg(a.tile_info + 2 * blockIdx.x + 1);
   const int h12 = __ldg(a.tile_info + 2 * blockIdx.x + 2) - hs;  // both halos
@@ -199,7 +200,7 @@ __global__ void __launch_bounds__(THREADS) k_step_pair(PairArgs a) {
 
   // states at the start of the pair, with their primitives
   for (int e = threadIdx.x; e < nt + h12; e += THREADS) {
-    const int64_t g = e < nt ? t0 + e : (int64_t)__ldg(a.halo_id + hs + (e - nt));
+    const int g = e < nt ? t0 + e : __ldg(a.halo_id + hs + (e - nt));
     const float4 u = __ldg(a.U + g);
     sU0[e] = u;
     sP0[e] = prim4(primitive<float>(u));
@@ -215,7 +216,7 @@ __global__ void __launch_bounds__(THREADS) k_step_pair(PairArgs a) {
     const int e = threadIdx.x + k * THREADS;
     lo1[k] = make_uint2(0u, 0u);
     if (e < nt) {
-      const int64_t g = t0 + e;
+      const int g = t0 + e;
       const uint2 lo0 = COMP ? __ldg(a.lo_in + g) : make_uint2(0u, 0u);
       lo1[k] = step1_cell<COMP>(__ldg(a.geom + 2 * g), __ldg(a.geom + 2 * g + 1),
                                 __ldg(a.cell_ln + g), lo0, e, sU0, sP0, sU1, sP1, a.uinf, dt1f,
@@ -231,7 +232,7 @@ __global__ void __launch_bounds__(THREADS) k_step_pair(PairArgs a) {
   for (int k = 0; k < KMAX; ++k) {
     const int e = threadIdx.x + k * THREADS;
     if (e < nt) {
-      const int64_t g = t0 + e;
+      const int g = t0 + e;
       uint2 lo2;
       const float4 U2 = step2_cell<COMP>(__ldg(a.geom + 2 * g), __ldg(a.geom + 2 * g + 1),
                                          __ldg(a.cell_ln + g), lo1[k], e, sU1, sP1, a.uinf, dt2f,

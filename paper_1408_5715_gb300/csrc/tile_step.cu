@@ -80,8 +80,8 @@ __global__ void __launch_bounds__(THREADS, sizeof(R) == 4 ? 1280 / THREADS : 1)
   const rec_t<R>* __restrict__ U = static_cast<const rec_t<R>*>(a.U);
   const rec_t<R>* __restrict__ geom = static_cast<const rec_t<R>*>(a.geom);
   rec_t<R>* out = static_cast<rec_t<R>*>(a.out);
-  const int64_t t0 = (int64_t)blockIdx.x * a.tile;
-  const int nt = (int)min((int64_t)a.tile, a.n - t0);
+  const int t0 = blockIdx.x * a.tile;  // cell ids are 32-bit
+  const int nt = min(a.tile, (int)a.n - t0);
   const int hs = __ldg(a.tile_info + 2 * blockIdx.x);
   const int h1 = __ldg(a.tile_info + 2 * blockIdx.x + 1);
   // dt formed once per block (FP64 scalar work), read after the barrier
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(THREADS, sizeof(R) == 4 ? 1280 / THREADS : 1)
   for (int k = 0; k < KMAX; ++k) {
     const int e = threadIdx.x + k * THREADS;
     if (e < nt) {
-      const int64_t i = t0 + e;
+      const int i = t0 + e;
       CellIn<R> c;
       const uint2 ln = __ldg(a.cell_ln + i);
       if constexpr (VTX) {
