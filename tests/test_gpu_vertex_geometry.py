@@ -225,3 +225,39 @@ def test_any_tile_size_gives_the_same_bits(geometry):
         U = dev(U0[perm])
         assert m.step(U, 13, 0.4) == tr
         assert torch.equal(U, Ur), tile
+
+
+def test_snapping_then_renumbering_equals_renumbering_then_snapping():
+    # the node grid does not depend on the cell order, and renumbering a
+    # snapped mesh carries its node lists along
+    mi, prim, U0 = case("channel")
+    a = B.Mesh.from_input(mi, "f32")
+    b = B.Mesh.from_input(mi, "f32")
+    for m in (a, b):
+        m.set_freestream(*prim)
+    a.set_geometry("vertex")
+    pa = a.renumber("rcm", seed=1)
+    pb = b.renumber("rcm", seed=1)
+    b.set_geometry("vertex")
+    np.testing.assert_array_equal(pa, pb)
+    np.testing.assert_array_equal(a.nodes()[0], b.nodes()[0])
+    Ua, Ub = dev(U0[pa]), dev(U0[pb])
+    assert a.step(Ua, 15, 0.4) == b.step(Ub, 15, 0.4)
+    assert torch.equal(Ua, Ub)
+
+
+def test_vertex_form_on_tiny_and_empty_meshes():
+    two = W.two_cells()
+    v = B.Mesh.from_input(two, "f32")
+    s = B.Mesh.from_input(two, "f32")
+    v.set_geometry("vertex")
+    s.set_geometry("vertex")
+    s.set_geometry("stored")
+    U = dev(np.array([[1.0, 0.0, 0.0, 2.5], [0.125, 0.0, 0.0, 0.25]]))
+    Us = U.clone()
+    assert v.step(U, 5, -1e-3) == s.step(Us, 5, -1e-3)
+    assert torch.equal(U, Us)
+    e = B.Mesh(np.zeros((0, 2)), np.zeros((0, 3), np.int32))
+    e.set_geometry("vertex")
+    assert e.nodes()[1] is None
+    assert e.step(torch.zeros((0, 4), dtype=torch.float32, device="cuda"), 3, 0.4) == 0.0
