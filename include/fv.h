@@ -198,18 +198,19 @@ int fv_mesh_set_wave_speed(fv_mesh* mesh, int32_t mode);
  *         precomputed normals and 1/V (32 bytes per cell in FP32).
  *         FV_GEOM_VERTEX: the tile kernel stages the grid coordinates of its
  *         tile's nodes in shared memory (8 bytes per node, about half a node
- *         per cell) and forms each cell's three normals and 1/V from them,
- *         reading 4 bytes of node ids per cell instead of 32 of geometry.
+ *         per cell) and forms each cell's three normals from them, reading
+ *         4 bytes of node ids and 4 of 1/V per cell instead of 32 of
+ *         geometry.
  * The first FV_GEOM_VERTEX call snaps every node of the mesh to a grid of
  * spacing s = 2^e, the finest with the mesh's extent E within 2^31 - 16
  * steps (so a node moves by at most s, s <= E / (2^31 - 16)); a periodic node
  * copy keeps the offset of its canonical node in whole steps.  Normals and
  * areas of the mesh are then those of the snapped nodes for every shape,
  * every later call and any batch made from the mesh: normals are exact
- * integer edge vectors converted with one rounding, 2V is an exact 64-bit
- * cross product, and the FP32 1/V is 2^(1-2e) times the correctly rounded
- * reciprocal of 2V in grid units rounded to FP32, as the kernel forms them,
- * so all shapes still give bitwise the same states.  The snapping stays when
+ * integer edge vectors times 2^e, which the kernel converts to FP32 with one
+ * rounding -- bitwise the stored FP32 normals -- and 2V is an exact 64-bit
+ * cross product; so all shapes still give bitwise the same states.  The
+ * snapping stays when
  * the form goes back to FV_GEOM_STORED.  fv_mesh_nodes returns the snapped
  * coordinates.  Selecting FV_GEOM_VERTEX also selects shape 6; fv_mesh_autotune
  * then times shape 6 at each tile size only.
