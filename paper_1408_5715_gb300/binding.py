@@ -244,7 +244,7 @@ class Mesh:
 
     def set_geometry(self, form: str):
         """'stored' (precomputed normals and 1/V, default) or 'vertex'
-        (normals and 1/V formed from node coordinates on a fixed-point grid;
+        (normals formed from node coordinates on a fixed-point grid, 1/V read;
         FP32, tile shape).  The first 'vertex' snaps the nodes to the grid."""
         _check(load().fv_mesh_set_geometry(self._h, {"stored": 0, "vertex": 1}[form]))
 

@@ -2,8 +2,8 @@
 against the stored geometry of the same snapped mesh and the FP64 oracle.
 
 After fv_mesh_set_geometry(FV_GEOM_VERTEX) the nodes sit on a fixed-point
-grid; the tile kernel forms each cell's normals and 1/V from the grid
-coordinates of its nodes.  Those are bitwise the stored FP32 records of the
+grid; the tile kernel forms each cell's normals from the grid coordinates
+of its nodes and reads 1/V.  Those are bitwise the stored FP32 records of the
 snapped mesh, so every step, residual and CFL bound must be bitwise equal to
 the stored-record kernels, and within the FP32 tolerance of the oracle run on
 the snapped node coordinates."""
