@@ -792,7 +792,7 @@ def forward_step_leg(B, t_end=4.0):
         m = B.Mesh.from_input(mi, "f32")
         m.set_freestream(*prim)
         m.set_wave_speed(wave)
-        perm = m.renumber("rcm")
+        perm = m.renumber("hilbert")
         U0 = torch.tensor(W.uniform_state(mi.n_tri, prim)[perm], dtype=torch.float32,
                           device="cuda")
         U = U0.clone()
@@ -818,7 +818,7 @@ def forward_step_leg(B, t_end=4.0):
         wall = time.perf_counter() - t0
         rho = U[:, 0].double()
         res = {"cells": mi.n_tri, "t_reached": t, "steps_launched": steps, "wall_s": wall,
-               "order": "rcm", "kernel_shape": tune}
+               "order": "hilbert", "kernel_shape": tune}
         if failed:
             res["failed"] = failed
         else:
