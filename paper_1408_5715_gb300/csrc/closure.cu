@@ -58,6 +58,15 @@ __device__ __forceinline__ void mma_bf16(float d[4], unsigned a0, unsigned a1, u
 
 __device__ __forceinline__ float relu(float x) { return x > 0.0f ? x : 0.0f; }
 
+// ReLU of two values packed to bfloat16: rounding keeps the sign, so the
+// ReLU of the rounded pair is the rounding of the ReLU (the next layer sees
+// the same values), with one packed maximum for both.
+__device__ __forceinline__ unsigned pack_bf16_relu(float lo, float hi) {
+  const __nv_bfloat162 v =
+      __hmax2(__floats2bfloat162_rn(lo, hi), __floats2bfloat162_rn(0.0f, 0.0f));
+  return *reinterpret_cast<const unsigned*>(&v);
+}
+
 __device__ __forceinline__ float scale_of(float z) {
   return 0.2f + 1.3f * (1.0f / (1.0f + expf(-z)));
 }
@@ -127,8 +136,8 @@ __device__ __forceinline__ void tile_forward(const ClWarpSmem& w, int t, const C
     a1[nt][1] += b1[col + 1];
     a1[nt][2] += b1[col];
     a1[nt][3] += b1[col + 1];
-    const unsigned p0 = pack_bf16(relu(a1[nt][0]), relu(a1[nt][1]));
-    const unsigned p1 = pack_bf16(relu(a1[nt][2]), relu(a1[nt][3]));
+    const unsigned p0 = pack_bf16_relu(a1[nt][0], a1[nt][1]);
+    const unsigned p1 = pack_bf16_relu(a1[nt][2], a1[nt][3]);
     A2[nt >> 1][(nt & 1) ? 2 : 0] = p0;
     A2[nt >> 1][(nt & 1) ? 3 : 1] = p1;
   }
