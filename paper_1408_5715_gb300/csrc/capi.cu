@@ -827,7 +827,9 @@ int fv_mesh_autotune(fv_mesh* mesh, const void* U, int32_t scheme, void* stream,
       if (times[v] < times[b]) b = v;
     mesh->variant = b;
     // the tile size of the tiled shapes: the fastest for shape 6 when it wins
-    mesh->pair_tile = b == fv::kTileVariant ? best_tile : keep_tile;
+    // (two steps per launch keep their own tile size: the two-step kernel
+    // takes the standard sizes only)
+    mesh->pair_tile = b == fv::kTileVariant && mesh->blocking == 1 ? best_tile : keep_tile;
     mesh->drop_graph();
     if (best) *best = b;
     if (us_per_step)

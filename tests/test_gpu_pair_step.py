@@ -222,3 +222,19 @@ def test_pairs_on_the_16m_square_match_single_steps():
     a.step(Ua, 4, -dt)
     b.step(Ub, 4, -dt)
     assert torch.equal(Ua, Ub)
+
+
+def test_autotune_keeps_the_two_step_tile_size():
+    # the autotuner times one-step shapes (and tile sizes that fill whole
+    # waves); a mesh set to two steps per launch keeps its standard tile size
+    mi, prim, U0 = case("channel")
+    m, perm = mesh(mi, prim)
+    m.set_blocking(2, 768)
+    m.autotune(dev(U0[perm]))
+    assert m.tiling()[1] == 768
+    ref, _ = mesh(mi, prim)
+    ref.set_blocking(2, 768)
+    U, Ur = dev(U0[perm]), dev(U0[perm])
+    m.step(U, 6, -1e-4)
+    ref.step(Ur, 6, -1e-4)
+    assert torch.equal(U, Ur)
