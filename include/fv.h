@@ -221,6 +221,20 @@ int fv_mesh_set_wave_speed(fv_mesh* mesh, int32_t mode);
  * inconsistent periodic identification); the mesh is unchanged then. */
 int fv_mesh_set_geometry(fv_mesh* mesh, int32_t form);
 
+/* Host diagnostics of the vertex geometry (after FV_GEOM_VERTEX): the nodes
+ * that the tile kernel stages for tile `tile` (cells [tile*tile_cells,
+ * (tile+1)*tile_cells) of the current numbering), in the order of the
+ * tile-local node ids.  All outputs nullable, host.
+ *   grid_xy     [2*capacity] their grid coordinates (x, y): a node sits at
+ *               centre + grid_xy * 2^e (fv_mesh_nodes gives e).
+ *   n_nodes     number of nodes of the tile.
+ *   cell_local  [3 * cells of the tile] each cell's three tile-local node
+ *               ids, counter-clockwise (face k runs from node k to k+1).
+ * FV_EINVAL without vertex geometry, for a bad tile index or size, or a
+ * capacity below n_nodes. */
+int fv_mesh_tile_nodes(const fv_mesh* mesh, int32_t tile_cells, int64_t tile, int32_t* grid_xy,
+                       int64_t capacity, int64_t* n_nodes, uint16_t* cell_local);
+
 /* Node coordinates of the mesh as its geometry uses them: those given to
  * fv_mesh_create, or after FV_GEOM_VERTEX their grid points (nodes that no
  * triangle uses keep their coordinates).  All outputs nullable, host.

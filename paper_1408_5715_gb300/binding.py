@@ -74,6 +74,7 @@ def load():
             "fv_mesh_set_wave_speed": (ctypes.c_int, [_vp, _i32]),
             "fv_mesh_set_geometry": (ctypes.c_int, [_vp, _i32]),
             "fv_mesh_get_tiling": (ctypes.c_int, [_vp, _P(_i32), _P(_i32)]),
+            "fv_mesh_tile_nodes": (ctypes.c_int, [_vp, _i32, _i64, _vp, _i64, _P(_i64), _vp]),
             "fv_mesh_nodes": (ctypes.c_int, [_vp, _P(_i64), _vp, _P(_i32)]),
             "fv_mesh_tile_halo": (ctypes.c_int, [_vp, _i32, _i64, _vp, _i64, _P(_i64), _P(_i64)]),
             "fv_mesh_autotune": (ctypes.c_int, [_vp, _vp, _i32, _vp, _P(_i32), _P(_dbl)]),
@@ -268,6 +269,19 @@ class Mesh:
         bulk copies into double-buffered shared memory."""
         _check(load().fv_mesh_set_blocking(self._h, int(steps_per_launch), int(tile_cells),
                                            int(bool(staged))))
+
+    def tile_nodes(self, tile_cells: int, tile: int):
+        """(grid coordinates [n, 2] of the nodes the vertex-geometry tile
+        kernel stages for a tile, each cell's three tile-local node ids)."""
+        nn = _i64()
+        _check(load().fv_mesh_tile_nodes(self._h, int(tile_cells), int(tile), None, 0,
+                                         ctypes.byref(nn), None))
+        q = np.zeros((max(nn.value, 1), 2), np.int32)
+        cells = max(0, min(int(tile_cells), self.n - int(tile) * int(tile_cells)))
+        loc = np.zeros((max(cells, 1), 3), np.uint16)
+        _check(load().fv_mesh_tile_nodes(self._h, int(tile_cells), int(tile), _np_ptr(q),
+                                         nn.value, ctypes.byref(nn), _np_ptr(loc)))
+        return q[:nn.value].copy(), loc[:cells].copy()
 
     def tiling(self):
         """(step-kernel shape, tile size in cells of the tiled shapes)."""

@@ -691,6 +691,32 @@ int fv_mesh_tile_halo(const fv_mesh* mesh, int32_t tile_cells, int64_t tile, int
   });
 }
 
+int fv_mesh_tile_nodes(const fv_mesh* mesh, int32_t tile_cells, int64_t tile, int32_t* grid_xy,
+                       int64_t capacity, int64_t* n_nodes, uint16_t* cell_local) {
+  return guarded([&] {
+    check_mesh(mesh);
+    if (!mesh->h.snapped()) invalid("tile nodes exist only on a mesh with vertex geometry");
+    const fv::TileVertices V = fv::build_tile_vertices(mesh->h, tile_cells);
+    const int64_t n_tiles = (int64_t)V.voff.size() - 1;
+    if (tile < 0 || tile >= n_tiles) invalid("tile index out of range");
+    const int64_t v0 = V.voff[tile], nb = V.voff[tile + 1] - v0;
+    if (n_nodes) *n_nodes = nb;
+    if (grid_xy) {
+      if (capacity < nb) invalid("grid_xy capacity too small");
+      std::memcpy(grid_xy, V.vq.data() + 2 * v0, 2 * nb * sizeof(int32_t));
+    }
+    if (cell_local) {
+      const int64_t c0 = tile * (int64_t)tile_cells;
+      const int64_t c1 = std::min<int64_t>(c0 + tile_cells, mesh->h.n);
+      for (int64_t c = c0; c < c1; ++c) {
+        cell_local[3 * (c - c0)] = V.v0[c];
+        cell_local[3 * (c - c0) + 1] = (uint16_t)(V.cell_vl[c] & 0xffffu);
+        cell_local[3 * (c - c0) + 2] = (uint16_t)(V.cell_vl[c] >> 16);
+      }
+    }
+  });
+}
+
 int fv_mesh_set_geometry(fv_mesh* mesh, int32_t form) {
   return guarded([&] {
     check_mesh(mesh);

@@ -349,3 +349,42 @@ def test_vertex_grid_refusals_leave_the_mesh_unchanged():
     assert m.nodes()[1] is None
     with pytest.raises(KeyError):
         m.set_geometry("faces")
+
+
+@pytest.mark.parametrize("kind", ["periodic", "channel", "step"])
+def test_vertex_tiles_stage_each_cells_nodes(kind):
+    # the node lists the vertex-geometry tile kernel stages: every cell's
+    # three counter-clockwise nodes sit at their grid points, each node once
+    # per tile, every staged node used
+    mi = _vertex_case(kind)
+    m = B.Mesh.from_input(mi, "f32")
+    with pytest.raises(B.FVError, match="vertex geometry"):
+        m.tile_nodes(96, 0)
+    perm = m.renumber("hilbert")
+    m.set_geometry("vertex")
+    xy, e = m.nodes()
+    s = 2.0 ** e
+    tri = mi.tri[perm].astype(np.int64)
+    p0, p1, p2 = mi.xy[tri[:, 0]], mi.xy[tri[:, 1]], mi.xy[tri[:, 2]]
+    cw = ((p1[:, 0] - p0[:, 0]) * (p2[:, 1] - p0[:, 1])
+          - (p2[:, 0] - p0[:, 0]) * (p1[:, 1] - p0[:, 1])) < 0
+    tri[cw] = tri[cw][:, [0, 2, 1]]  # the library's counter-clockwise order
+    n = m.n
+    centre = None
+    for tile_cells in (32, 96, 512):
+        n_tiles = (n + tile_cells - 1) // tile_cells
+        for t in sorted({0, n_tiles // 2, n_tiles - 1}):
+            q, loc = m.tile_nodes(tile_cells, t)
+            cells = tri[t * tile_cells:min((t + 1) * tile_cells, n)]
+            assert loc.shape == cells.shape
+            assert loc.max() < len(q) and set(np.unique(loc)) == set(range(len(q)))
+            # one local id per node and one node per local id
+            pairs = set(zip(cells.ravel().tolist(), loc.ravel().tolist()))
+            assert len({a for a, _ in pairs}) == len(pairs) == len(q)
+            c = xy[cells.ravel()] - q[loc.ravel()].astype(np.float64) * s
+            if centre is None:
+                centre = c[0]
+                assert np.array_equal(centre / s, np.round(centre / s))
+            np.testing.assert_array_equal(c, np.broadcast_to(centre, c.shape))
+    with pytest.raises(B.FVError, match="out of range"):
+        m.tile_nodes(512, (n + 511) // 512)
