@@ -36,7 +36,7 @@ def nvcc() -> str:
 
 def _flags(src: str):
     common = ["-O3", "-std=c++17", "-I", os.path.join(ROOT, "include"), "-I", CSRC,
-              "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr"]
+              "-Xcompiler", "-fPIC,-O2,-ffp-contract=off", "--expt-relaxed-constexpr"]
     if src.endswith(".cu"):
         return common + ARCH + ["-lineinfo", "-Xptxas", "-v"]
     return common + ["-x", "c++"]
