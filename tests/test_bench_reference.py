@@ -45,3 +45,13 @@ def test_reference_arm_on_the_batch_samples_its_largest_mesh():
     assert d["impl"] == "reference" and d["value"] > 0
     assert d["config"]["workload"] == "batch_256"
     assert d["config"]["cells"] > 100_000
+
+
+def test_reference_arm_other_ranks_exit_without_work():
+    # under torchrun only rank 0 prints the line; the other ranks exit 0
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2")
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--workload", "vortex_square_small", "--steps", "1", "--warmup", "0"],
+                         capture_output=True, text=True, cwd=ROOT, env=env, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    assert not [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
