@@ -380,11 +380,16 @@ int fv_conserved_totals(fv_mesh* mesh, const void* U, double* out, void* stream)
  * memory on the current device. */
 int fv_closure_create(const float* theta, fv_closure** out);
 
+/* Frees the closure's device memory (waits for the device); NULL is a no-op.
+ * Step graphs that meshes captured with it are never replayed again: every
+ * closure carries a process-unique parameter stamp, so another closure, even
+ * at the same address, makes the mesh recapture. */
 int fv_closure_destroy(fv_closure* closure);
 
 /* New parameters (same order); theta is host memory, or device memory when
- * theta_on_device != 0.  Synchronises the stream.  Captured step graphs keep
- * using the closure's (updated) parameters. */
+ * theta_on_device != 0.  Synchronises the stream.  A mesh whose captured
+ * step graph used the closure recaptures it on its next fv_step (the output
+ * bias b3 is a kernel argument of the captured launches). */
 int fv_closure_set(fv_closure* closure, const float* theta, int32_t theta_on_device,
                    void* stream);
 
@@ -426,6 +431,8 @@ int fv_adam_step(float* theta, const float* grad, float* m, float* v, int64_t n,
  * FV_EINVAL for no meshes, mixed precisions or more than 2^31 cells. */
 int fv_batch_create(fv_mesh* const* meshes, int32_t n_meshes, fv_batch** out);
 
+/* Frees the batch's host and device arrays (waits for its device work); NULL
+ * is a no-op.  The meshes it was made from are not touched. */
 int fv_batch_destroy(fv_batch* batch);
 
 /* Padded total number of cells, and offsets[n_meshes + 1] (nullable): mesh k

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <iterator>
@@ -77,6 +78,10 @@ struct fv_closure {
   float* d_b = nullptr;      // b1[32] b2[32] w3[32] b3
   float* d_theta = nullptr;  // FP32 staging of theta (kClosureParams)
   float b3 = 0.0f;           // host copy: a kernel argument
+  // stamp of the parameters now uploaded, unique in the process: a step
+  // graph captured with other parameters (b3 is baked into its launches) or
+  // with another closure at the same address is recaptured
+  uint64_t version = 0;
   // training scratch: per-block gradient and loss partials, outputs
   int grad_blocks = 0;
   float* d_gpart = nullptr;
@@ -142,6 +147,7 @@ struct fv_mesh {
   int32_t g_scheme = -1;
   double g_cfl = 0.0, g_tstop = 0.0;
   const fv_closure* g_closure = nullptr;
+  uint64_t g_closure_version = 0;
   bool g_comp = false;
   int g_variant = -1;
   int g_blocking = -1, g_tile = -1, g_staged = -1;
@@ -495,6 +501,7 @@ void capture_graph(fv_mesh* m, void* U, double cfl, double t_stop, int32_t schem
   m->g_cfl = cfl;
   m->g_tstop = t_stop;
   m->g_closure = cl;
+  m->g_closure_version = cl ? cl->version : 0;
   m->g_comp = m->use_lo();
   m->g_variant = m->variant;
   m->g_blocking = m->blocking;
@@ -924,6 +931,7 @@ int fv_step(fv_mesh* mesh, void* U, int64_t nsteps, double cfl, double t_stop, i
       if (chunks > 0) {
         if (!mesh->graph || mesh->g_U != U || mesh->g_scheme != scheme || mesh->g_cfl != cfl ||
             mesh->g_tstop != t_stop || mesh->g_closure != closure ||
+            mesh->g_closure_version != (closure ? closure->version : 0) ||
             mesh->g_comp != mesh->use_lo() || mesh->g_variant != mesh->variant ||
             mesh->g_blocking != mesh->blocking || mesh->g_tile != mesh->tiles_built ||
             mesh->g_staged != mesh->pair_staged || mesh->g_chained != mesh->chained)
@@ -1556,6 +1564,8 @@ void closure_upload(fv_closure* c, const float* theta, bool on_device, cudaStrea
   // b3 is a kernel argument: read it back (a 4-byte copy; synchronises)
   FV_CUDA(cudaMemcpyAsync(&c->b3, c->d_b + 96, sizeof(float), cudaMemcpyDeviceToHost, s));
   FV_CUDA(cudaStreamSynchronize(s));
+  static std::atomic<uint64_t> uploads{0};
+  c->version = ++uploads;
 }
 
 void check_closure(const fv_closure* c) {

@@ -240,3 +240,31 @@ def test_closure_step_is_bitwise_the_same_in_any_order(vortex_case, scheme):
         outs.append((t, out))
     assert outs[0][0] == outs[1][0]
     assert np.array_equal(outs[0][1], outs[1][1])
+
+
+def test_captured_graphs_see_new_closure_parameters(vortex_case):
+    # the output bias b3 is a kernel argument of a captured step graph: after
+    # fv_closure_set the mesh recaptures, and a new closure in the old one's
+    # place does not replay the old graph either
+    mi, U0 = vortex_case
+    th1, _ = make_theta(3, scale=0.3)
+    th2, _ = make_theta(3, scale=0.3)
+    th2[-1] = -1.5  # only the output bias differs
+    g = B.Mesh.from_input(mi, "f32")
+    cl = B.Closure(th1)
+    U = torch.tensor(U0, dtype=torch.float32, device="cuda")
+    g.step(U, 100, 0.4, closure=cl)  # 96 steps through a captured graph
+    cl.set(th2)
+    U = torch.tensor(U0, dtype=torch.float32, device="cuda")
+    g.step(U, 100, 0.4, closure=cl)
+    ref = B.Mesh.from_input(mi, "f32")
+    Ur = torch.tensor(U0, dtype=torch.float32, device="cuda")
+    ref.step(Ur, 100, 0.4, closure=B.Closure(th2))
+    assert torch.equal(U, Ur)
+    cl.close()
+    cl = B.Closure(th1)
+    U = torch.tensor(U0, dtype=torch.float32, device="cuda")
+    g.step(U, 100, 0.4, closure=cl)
+    Ur = torch.tensor(U0, dtype=torch.float32, device="cuda")
+    ref.step(Ur, 100, 0.4, closure=B.Closure(th1))
+    assert torch.equal(U, Ur)
