@@ -1,18 +1,24 @@
 #!/usr/bin/env python3
 """Throughput benchmark of the fused finite-volume Euler step (cell updates/s).
 
-Default workload: the 1M-triangle channel with a 10%-thick circular-arc bump
-(graded 4x over the bump and at the lower wall, jittered interior nodes,
-far-field inflow/outflow at Mach 0.5, slip walls), Hilbert cell order (the
-faster of RCM and Hilbert on this mesh), FP32 state, forward Euler at CFL 0.4.  One benchmark step = one call of the time
-loop (10,000 time steps, each one fused kernel, replayed as captured CUDA
-graphs) followed by the FP64 conserved totals -- every row of the hot path.
+Default workload: the 16.8M-triangle periodic unit square (4096 x 2048 quads,
+seeded diagonals, nodes jittered 20 %), an isentropic vortex at Mach 0.5,
+Hilbert cell order, FP32 state (plain float update; its error against the
+FP64 path is reported), forward Euler at CFL 0.4.  Its state and geometry
+(1.4 GB) are far larger than the L2, so every step streams from HBM: this is
+the bandwidth headline.  One benchmark step = one call of the time loop (1,000
+time steps, each one fused kernel, replayed as captured CUDA graphs) followed
+by the FP64 conserved totals -- every row of the hot path.
 
 Prints ONE JSON line.  Also reported: the same workload in FP64 (throughput,
-speedup of FP32 over it, and the FP32 error against it), the 16.8M-triangle
-periodic square (the HBM-bound headline), the roofline of the step kernel,
-the FP64 CPU oracle timed on one host core, and an end-to-end figure with
-host buffers.  `--impl reference` times the CPU oracle alone.
+speedup of FP32 over it, and the FP32 error against it) and with the
+compensated FP32 update; the 1M-triangle channel with a circular-arc bump
+(FP32 compensated, 10,000 time steps, and FP64); the roofline of the step
+kernel; two steps per launch; normals from node coordinates; the 256-mesh
+batch; the learned closure; the Mach 3 forward-facing step; the FP64 CPU
+oracle timed on one host core; an end-to-end figure with host buffers.  The
+key figures are repeated in a short `summary` object at the end of the line.
+`--impl reference` times the CPU oracle alone.
 """
 from __future__ import annotations
 
@@ -57,10 +63,13 @@ def parse_args():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", default="channel_bump_1m",
+    p.add_argument("--workload", default="square_16m",
                    choices=["channel_bump_1m", "square_16m", "batch_256", "vortex_square_small"])
     p.add_argument("--precision", default="f32", choices=["f32", "f64"])
     p.add_argument("--scheme", default="fe", choices=["fe", "rk2"])
+    p.add_argument("--update", default=None, choices=["plain", "compensated"],
+                   help="FP32 state update: plain float, or with the bfloat16 remainder "
+                        "(default: the workload's)")
     p.add_argument("--order", default=None, choices=["identity", "shuffle", "rcm", "hilbert", "am1"])
     p.add_argument("--time-steps", type=int, default=None, help="time steps per benchmark step")
     p.add_argument("--no-extras", action="store_true", help="skip FP64 / 16M / CPU / e2e legs")
@@ -83,16 +92,16 @@ def parse_args():
 
 WORKLOADS = {
     "channel_bump_1m": dict(make=W.channel_bump_1m, init="uniform", mach=0.5, time_steps=10000,
-                            order="hilbert", desc="channel 3x1, 10% circular-arc bump, 1250x400 quads, "
+                            order="hilbert", update="compensated", desc="channel 3x1, 10% circular-arc bump, 1250x400 quads, "
                             "graded 4x, jitter 20%, far field M=0.5, slip walls"),
     "square_16m": dict(make=W.vortex_square_16m, init="vortex", mach=0.5, time_steps=1000,
-                       order="hilbert", desc="periodic unit square, 4096x2048 quads, jitter 20%, "
+                       order="hilbert", update="plain", desc="periodic unit square, 4096x2048 quads, jitter 20%, "
                        "isentropic vortex beta=5 M=0.5"),
     "batch_256": dict(make=W.vortex_batch, batch=True, time_steps=1000, order="hilbert",
                       desc="256 periodic jittered squares, 4,900-200,704 triangles each "
                            "(log-uniform), vortex or uniform flow, Mach U(0.3, 0.8)"),
     "vortex_square_small": dict(make=W.vortex_square_small, init="vortex", mach=0.5,
-                                time_steps=100, order="shuffle",
+                                time_steps=100, order="shuffle", update="compensated",
                                 desc="periodic unit square, 64x32 quads, vortex"),
 }
 
@@ -284,6 +293,10 @@ def run_ours(args):
     prec = args.precision
     tdt = torch.float32 if prec == "f32" else torch.float64
     m, perm = make_mesh(B, spec, mi, prec, order)
+    update = (args.update or spec.get("update", "compensated")) if prec == "f32" else None
+    if prec == "f32":
+        m.set_compensation(update == "compensated")
+    comp = update == "compensated"
     U0p = U0[perm]
     U0dev = torch.tensor(U0p, dtype=tdt, device="cuda")
     U = torch.empty_like(U0dev)
@@ -323,17 +336,17 @@ def run_ours(args):
     avg_launch = total / (args.steps * launches)  # includes the per-call small kernels
     peak, peak_kind = measured_peaks()
     if args.blocking == 2:
-        algo = kbytes = PAIR_BYTES
+        algo = kbytes = PAIR_BYTES if comp else PAIR_BYTES - COMP_BYTES
         kname = (f"{'k_step_pair_tma' if args.staged else 'k_step_pair'}"
-                 f"<tile {args.tile}, compensated>")
+                 f"<tile {args.tile}, {'compensated' if comp else 'plain'}>")
     else:
         algo = VERTEX_BYTES if args.geometry == "vertex" else ALGO_BYTES[prec]
-        kbytes = algo + (COMP_BYTES if prec == "f32" else 0)
+        kbytes = algo + (COMP_BYTES if comp else 0)
         kfun = ("k_step_closure" if args.closure else
                 {5: "k_step_tma", 6: "k_step_tile"}.get(tune["variant"], "k_step"))
         kname = (f"{kfun}<{'float' if prec == 'f32' else 'double'}, "
                  f"{'RK2' if stages == 2 else 'FE'}, "
-                 f"{'compensated' if prec == 'f32' else 'plain'}, shape {tune['variant']}"
+                 f"{'compensated' if comp else 'plain'}, shape {tune['variant']}"
                  f"{', vertex geometry' if args.geometry == 'vertex' else ''}>")
     achieved = algo * n / avg_launch / 1e9  # GB/s of one step-kernel launch
     U_final = U.double().cpu().numpy()
@@ -353,6 +366,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": args.workload, "mesh": spec["desc"], "cells": n,
                    "time_steps_per_step": S, "scheme": args.scheme, "cfl": 0.4, "order": order,
+                   "update": update,
                    "geometry": ("normals from node coordinates on a grid of 2^%d" %
                                 m.nodes()[1]) if args.geometry == "vertex" else "stored normals",
                    "dt": "CFL bound of the state at the start of each pair" if args.blocking == 2
@@ -374,13 +388,15 @@ def run_ours(args):
                      "traffic": profiled_traffic(
                          f"step_pair_{args.workload}.md" if args.blocking == 2
                          else f"step_vertex_{args.workload}.md" if args.geometry == "vertex"
-                         else f"step_{prec}_{args.workload}.md")},
+                         else f"step_{prec}{'' if comp or prec == 'f64' else '_plain'}"
+                              f"_{args.workload}.md")},
         "e2e": e2e,
         "gpu_launches": args.steps * (launches + 4),
         "clocks": clk.summary(),
     }
     if rank == 0 and not args.no_extras and world == 1:
         extras(args, B, spec, mi, U0, U0p, perm, m, S, U_final, out)
+        out["summary"] = summary(out)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:
@@ -538,51 +554,77 @@ def e2e_leg(args, m, U0p, n, S, dist=None, closure=None):
             "api": "fv_step + fv_conserved_totals on host-copied state"}
 
 
-def extras(args, B, spec, mi, U0, U0p, perm, m32, S, U32_final, out):
+def mesh_run(B, spec, mi, U0, prec, update, time_steps, steps=2, warmup=1):
+    """One single-mesh workload in one precision and update: autotuned shape,
+    timed like the main line (L2 flushed between benchmark steps).  Returns
+    the report and the final state in the mesh's input cell order."""
     import torch
+    m, perm = make_mesh(B, spec, mi, prec, spec["order"])
+    comp = prec == "f32" and update == "compensated"
+    if prec == "f32":
+        m.set_compensation(comp)
+    tdt = torch.float32 if prec == "f32" else torch.float64
+    U0d = torch.tensor(U0[perm], dtype=tdt, device="cuda")
+    U = torch.empty_like(U0d)
+    tune = choose_variant(m, U0d, None)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    tt = timed_loop(m, U, U0d, time_steps, steps, warmup, "fe", flush=flush)
+    v = mi.n_tri * time_steps / statistics.mean(tt)
+    peak, _ = measured_peaks()
+    gbs = ALGO_BYTES[prec] * v / 1e9
+    res = {"value": v, "unit": "cell-updates/s", "dtype": prec, "cells": mi.n_tri,
+           "time_steps": time_steps, "order": spec["order"], "kernel_shape": tune,
+           "achieved_gbs": gbs, "frac_of_measured_hbm": gbs / peak,
+           "frac_with_kernel_bytes": (ALGO_BYTES[prec] + (COMP_BYTES if comp else 0)) * v / 1e9
+                                     / peak}
+    if prec == "f32":
+        res["update"] = update
+    final = np.empty(U0.shape)
+    final[perm] = U.double().cpu().numpy()
+    del U, U0d, flush
+    m.close()
+    return res, final
+
+
+def rel_l2_rho(a, b):
+    return float(np.linalg.norm(a[:, 0] - b[:, 0]) / np.linalg.norm(b[:, 0]))
+
+
+def extras(args, B, spec, mi, U0, U0p, perm, m32, S, U32_final, out):
     n = mi.n_tri
-    # ---- same workload in FP64: throughput, speedup, error of FP32 against it
-    if args.precision == "f32":
-        m64, _ = make_mesh(B, spec, mi, "f64", out["config"]["order"])
-        U0d = torch.tensor(U0p, dtype=torch.float64, device="cuda")
-        U = torch.empty_like(U0d)
-        tune64 = choose_variant(m64, U0d, None, args.scheme)
-        t64 = timed_loop(m64, U, U0d, S, 1, 1, args.scheme)
-        v64 = n * S / sum(t64)
-        U64 = U.cpu().numpy()
-        err = float(np.linalg.norm(U32_final[:, 0] - U64[:, 0]) / np.linalg.norm(U64[:, 0]))
-        out["fp64"] = {"value": v64, "unit": "cell-updates/s", "time_steps": S,
-                       "kernel_shape": tune64,
-                       "speedup_fp32_over_fp64": out["value"] / v64,
-                       "fp32_rel_l2_rho_vs_fp64": err, "tolerance": 1e-5}
-        del U, U0d
-        m64.close()
-    # ---- the HBM-bound headline: 16.8M cells
-    if args.workload != "square_16m":
-        spec16 = WORKLOADS["square_16m"]
-        mi16 = spec16["make"]()
-        U16 = initial_state(spec16, mi16)
-        res = {}
-        for prec, steps16 in (("f32", 1000), ("f64", 100)):
-            m16, p16 = make_mesh(B, spec16, mi16, prec, spec16["order"])
-            tdt = torch.float32 if prec == "f32" else torch.float64
-            U0d = torch.tensor(U16[p16], dtype=tdt, device="cuda")
-            U = torch.empty_like(U0d)
-            t16 = choose_variant(m16, U0d, None)
-            tt = timed_loop(m16, U, U0d, steps16, 2, 1, "fe")
-            v = mi16.n_tri * steps16 / statistics.mean(tt)
-            gbs = ALGO_BYTES[prec] * v / 1e9
-            peak, _ = measured_peaks()
-            res[prec] = {"value": v, "unit": "cell-updates/s", "time_steps": steps16,
-                         "kernel_shape": t16,
-                         "achieved_gbs": gbs, "frac_of_measured_hbm": gbs / peak,
-                         "traffic": profiled_traffic(f"step_{prec}_square_16m.md")}
-            del U, U0d
-            m16.close()
-        res["cells"] = mi16.n_tri
-        res["order"] = spec16["order"]
-        res["speedup_fp32_over_fp64"] = res["f32"]["value"] / res["f64"]["value"]
-        out["square_16m"] = res
+    cfg = out["config"]
+    if args.precision == "f32" and args.blocking == 1 and args.geometry == "stored" \
+            and not args.closure:
+        # ---- same workload in FP64: throughput, speedup, error of FP32 against it
+        r64, U64 = mesh_run(B, spec, mi, U0, "f64", None, S, steps=1, warmup=1)
+        main32 = np.empty(U0.shape)
+        main32[perm] = U32_final
+        r64["speedup_fp32_over_fp64"] = out["value"] / r64["value"]
+        r64["fp32_rel_l2_rho_vs_fp64"] = rel_l2_rho(main32, U64)
+        r64["tolerance"] = 1e-5
+        out["fp64"] = r64
+        # ---- the other FP32 update on the same workload
+        other = "plain" if cfg["update"] == "compensated" else "compensated"
+        r, U = mesh_run(B, spec, mi, U0, "f32", other, S)
+        r["rel_l2_rho_vs_fp64"] = rel_l2_rho(U, U64)
+        out[f"fp32_{other}"] = r
+        del U64, U
+    # ---- the other single-mesh workload of the survey: the 1M channel (L2-sized,
+    # 10,000 steps, compensated update) or the 16.8M square (the HBM headline)
+    name = "channel_bump_1m" if args.workload != "channel_bump_1m" else "square_16m"
+    spec2 = WORKLOADS[name]
+    mi2 = spec2["make"]()
+    U02 = initial_state(spec2, mi2)
+    res = {"cells": mi2.n_tri, "order": spec2["order"], "mesh": spec2["desc"]}
+    res["f32"], U32 = mesh_run(B, spec2, mi2, U02, "f32", spec2["update"], spec2["time_steps"])
+    res["f32"]["traffic"] = profiled_traffic(
+        f"step_f32{'' if spec2['update'] == 'compensated' else '_plain'}_{name}.md")
+    res["f64"], U64 = mesh_run(B, spec2, mi2, U02, "f64", None, spec2["time_steps"], steps=1)
+    res["speedup_fp32_over_fp64"] = res["f32"]["value"] / res["f64"]["value"]
+    res["fp32_rel_l2_rho_vs_fp64"] = rel_l2_rho(U32, U64)
+    res["tolerance"] = 1e-5
+    out[name] = res
+    del U32, U64
     # a leg that fails reports its error; the headline line is still printed
     def leg(name, fn):
         try:
@@ -604,6 +646,40 @@ def extras(args, B, spec, mi, U0, U0p, perm, m32, S, U32_final, out):
     leg("forward_step", forward_step_leg)
     # ---- FP64 CPU oracle on one host core, bounded sample of this workload
     out["cpu_baseline"] = cpu_baseline(spec, mi, U0, budget_s=12.0)
+
+
+def summary(out):
+    """The key figures of the line in a few hundred bytes (printed last)."""
+    def g(d, *path):
+        for p in path:
+            if not isinstance(d, dict) or p not in d:
+                return None
+            d = d[p]
+        return d
+
+    def r3(x):
+        return None if x is None else float(f"{x:.4g}")
+    other = "channel_bump_1m" if out["config"]["workload"] != "channel_bump_1m" else "square_16m"
+    return {
+        "workload": out["config"]["workload"],
+        "value": r3(out["value"]), "roofline_frac": r3(out["roofline"]["frac"]),
+        "traffic_per_launch": out["roofline"]["traffic"],
+        "fp64_value": r3(g(out, "fp64", "value")),
+        "fp32_speedup_over_fp64": r3(g(out, "fp64", "speedup_fp32_over_fp64")),
+        "fp32_rel_l2_rho_vs_fp64": r3(g(out, "fp64", "fp32_rel_l2_rho_vs_fp64")),
+        "compensated_value": r3(g(out, "fp32_compensated", "value")),
+        other: {"f32": r3(g(out, other, "f32", "value")),
+                "f32_frac": r3(g(out, other, "f32", "frac_of_measured_hbm")),
+                "f64": r3(g(out, other, "f64", "value")),
+                "fp32_rel_l2_rho_vs_fp64": r3(g(out, other, "fp32_rel_l2_rho_vs_fp64"))},
+        "batched": r3(g(out, "batched", "value")),
+        "batched_frac_72B": r3(g(out, "batched", "frac_of_measured_hbm_72B")),
+        "pairs_speedup_16m": r3(g(out, "pairs", "square_16m", "speedup_over_single_step")),
+        "learned_overhead": r3(g(out, "learned", "overhead")),
+        "cpu_baseline": r3(g(out, "cpu_baseline", "value")),
+        "e2e": r3(out["e2e"]["value"]),
+        "peak_gbs": out["roofline"]["peak"],
+    }
 
 
 def unchained_leg(m, U0p, S, scheme, chained_value):
@@ -774,6 +850,7 @@ def batched_leg(B, time_steps=1000):
            "value_by_shape": {k: cells * time_steps / t for k, t in by_shape.items()},
            "fp32_rel_l2_rho_vs_fp64": errs, "tolerance": 1e-5,
            "achieved_gbs_kernel_bytes": gbs, "frac_of_measured_hbm": gbs / peak,
+           "frac_of_measured_hbm_72B": ALGO_BYTES["f32"] * v / 1e9 / peak,
            "launches_per_step": time_steps + 4}
     batch.close()
     return res
@@ -917,7 +994,9 @@ def run_reference(args):
         U0 = initial_state(spec, mi)
         uinf = W.conserved(*W.freestream(spec["mach"]))
     om = oracle.Mesh(mi.xy, mi.tri, mi.canon, mi.bnd, mi.default_bc, uinf)
-    per_step = 2  # time steps per benchmark step: a bounded sample of the workload
+    # time steps per benchmark step: a bounded sample of the workload (one
+    # step of the 16.8M-cell square takes a few seconds on one core)
+    per_step = 1 if mi.n_tri > 4_000_000 else 2
     for _ in range(args.warmup):
         om.run(U0, 1, 0.4)
     t0 = time.perf_counter()

@@ -41,6 +41,10 @@ extern "C" {
 #define FV_ECUDA 3      /* a CUDA runtime call failed (message has the CUDA error) */
 #define FV_ENONFINITE 4 /* a step produced a non-finite state, rho <= 0 or p <= 0 */
 #define FV_ETIMEOUT 5   /* a bounded device wait gave up */
+#define FV_ESTATE 6     /* a bounded device wait gave up and the kernel's own bulk copies
+                           still in flight did not complete within the drain limit either:
+                           they may still write the device memory of the mesh or batch.
+                           Destroy the handle (and do not reuse its state buffers). */
 
 /* ---- precision of a mesh's state and geometry ------------------------------ */
 #define FV_F32 0
@@ -141,11 +145,30 @@ int fv_mesh_export(const fv_mesh* mesh, int32_t* nbr, double* normals, double* a
 /* FV_F32 meshes: chooses how fv_step adds each increment to the float state.
  * enable = 1 (the default): compensated -- the part of every update that the
  * float state cannot represent is kept in a per-cell bfloat16 remainder
- * (8 bytes per cell, library-owned, zeroed at the start of every fv_step call)
- * and added back on the next step, so long runs do not stall when increments
- * fall below half a float ulp of the state.  enable = 0: plain float update.
+ * (8 bytes per cell, library-owned and zeroed at the start of every fv_step
+ * call, unless the caller supplies it with fv_mesh_set_remainder) and added
+ * back on the next step, so long runs do not stall when increments fall below
+ * half a float ulp of the state.  enable = 0: plain float update.
  * Not part of the paper; FV_EINVAL for FV_F64 meshes with enable = 1. */
 int fv_mesh_set_compensation(fv_mesh* mesh, int32_t enable);
+
+/* Caller-owned remainder of the compensated FP32 update, so that a run split
+ * over several fv_step calls, or saved to a checkpoint and resumed later,
+ * gives the same bits as one call.  Not part of the paper.
+ *   lo  device memory of n_cells records of 8 bytes: four bfloat16 values per
+ *       cell, the remainders of rho, rho*u, rho*v, E in U's order, in the
+ *       mesh's current cell numbering; or NULL (the default): the library's
+ *       own remainder, zeroed at the start of every fv_step call.
+ * With lo set, each fv_step call starts from the remainder in lo and leaves
+ * the remainder of its final state there (two device-to-device copies of
+ * 8 bytes per cell per call).  The library never clears lo: zero it whenever
+ * a new state is put into U -- a zero remainder is the state of a fresh
+ * start, and a call with a zeroed lo gives the bits of a call without one.
+ * Saving U and lo and loading both resumes a run bit for bit.  lo must stay
+ * valid while it is set; after fv_renumber permute it as U.  It is not read
+ * or written while compensation is off.  FV_EINVAL for a non-NULL lo on an
+ * FV_F64 mesh. */
+int fv_mesh_set_remainder(fv_mesh* mesh, void* lo);
 
 /* Shape of the step kernel: 0 one thread per cell; 1 (default) a persistent
  * grid of resident blocks that walks the cells and prefetches the next
@@ -176,6 +199,7 @@ int fv_mesh_autotune(fv_mesh* mesh, const void* U, int32_t scheme, void* stream,
  * copies on mbarriers).  A wait that gives up makes the kernel stop, drain its
  * own copies in flight (with the default limit) and set an error bit, and
  * fv_step / fv_mesh_status return FV_ETIMEOUT; the state is then not valid.
+ * If the drain gives up as well they return FV_ESTATE.
  * Default 2^24.  A limit of 0 forces the timeout path (for tests). */
 int fv_mesh_set_wait_limit(fv_mesh* mesh, uint32_t polls);
 
@@ -455,6 +479,13 @@ int fv_batch_get_variant(const fv_batch* batch, int32_t* variant);
 /* Compensated float update for FV_F32 batches (see fv_mesh_set_compensation). */
 int fv_batch_set_compensation(fv_batch* batch, int32_t enable);
 
+/* Caller-owned remainder of a batch's compensated update, as
+ * fv_mesh_set_remainder: lo holds n_cells_padded records of 8 bytes (device),
+ * in the batch's record order; NULL returns to the library's own remainder,
+ * zeroed at the start of every fv_batch_step call.  FV_EINVAL for a non-NULL
+ * lo on an FV_F64 batch. */
+int fv_batch_set_remainder(fv_batch* batch, void* lo);
+
 /* fv_step for every mesh of the batch: U is device memory of n_cells_padded
  * records in the batch precision; cfl, t_stop and scheme apply to every mesh,
  * dt is each mesh's own.  t_advanced (nullable, host, [n_meshes]): if given the
@@ -478,21 +509,26 @@ int fv_batch_totals(fv_batch* batch, const void* U, double* out, void* stream);
  * latency-critical loop where cudaMalloc's implicit device synchronisation
  * would stall other streams.  It calls no cudaMalloc, cudaFree or allocating
  * library routine and needs no fv_mesh.
- *   U        device, [4*n_cells] states in `precision` (FV_F32 or FV_F64).
+ *   U        device, [4*n_cells] states in `precision` (FV_F32 or FV_F64),
+ *            16-byte aligned for FV_F32 and 32-byte aligned for FV_F64.
  *   area     device, [n_cells] cell areas V_T (e.g. fv_mesh_export's area,
- *            copied to the device by the caller), same cell order as U.
- *   out      device, double[4], written by the call (caller-owned).
+ *            copied to the device by the caller), same cell order as U,
+ *            8-byte aligned.
+ *   out      device, double[4], written by the call (caller-owned), 8-byte
+ *            aligned.
  *   stream   cudaStream_t as void*; nothing is synchronised.
  * Scratch: per-tile partial sums live in a fixed array inside the library's
  * device code (4096 tiles of 4096 cells, 128 KiB per GPU, held by every GPU
  * that loads the library until the process exits).  Hence n_cells may be at
- * most 16,777,216; larger sizes return FV_EINVAL before any device work.
- * The first call on a device looks up that array's device address
- * (cudaGetSymbolAddress) with the device current; make that first call
- * before any stream capture.  All calls share the one array: calls that
- * overlap on the GPU (different streams, no ordering) race and give wrong
- * sums.  Every partial a call reads is written earlier in the same call, so
- * leftovers of a previous call do not matter.  Results agree with
+ * most 16,777,216; larger sizes, a null or misaligned pointer and an unknown
+ * precision return FV_EINVAL before any device work.
+ * Every call looks up that array's device address (cudaGetSymbolAddress) for
+ * the current device, so a device reset between calls is harmless; the first
+ * call on a device also loads the library's device code there, so make that
+ * first call before any stream capture.  All calls share the one array:
+ * calls that overlap on the GPU (different streams, no ordering) race and
+ * give wrong sums.  Every partial a call reads is written earlier in the same
+ * call, so leftovers of a previous call do not matter.  Results agree with
  * fv_conserved_totals to rounding (the summation order differs). */
 int fv_conserved_totals_noalloc(const void* U, const double* area, int64_t n_cells,
                                 int32_t precision, double* out, void* stream);

@@ -15,7 +15,7 @@ import numpy as np
 
 from . import build as _build
 
-FV_OK, FV_EINVAL, FV_ENOMEM, FV_ECUDA, FV_ENONFINITE, FV_ETIMEOUT = range(6)
+FV_OK, FV_EINVAL, FV_ENOMEM, FV_ECUDA, FV_ENONFINITE, FV_ETIMEOUT, FV_ESTATE = range(7)
 N_VARIANTS = 7  # step-kernel shapes (fv_mesh_set_variant)
 FV_F32, FV_F64 = 0, 1
 FV_BC_NONE, FV_BC_WALL, FV_BC_FARFIELD, FV_BC_EXTRAP = 0, 1, 2, 3
@@ -67,6 +67,7 @@ def load():
             "fv_partition_sizes": (ctypes.c_int, [_vp, _i32, _i32, _P(_i64), _P(_i64)]),
             "fv_partition_local": (ctypes.c_int, [_vp, _i32, _i32, _vp, _vp, _vp, _vp, _vp]),
             "fv_mesh_set_compensation": (ctypes.c_int, [_vp, _i32]),
+            "fv_mesh_set_remainder": (ctypes.c_int, [_vp, _vp]),
             "fv_mesh_set_variant": (ctypes.c_int, [_vp, _i32]),
             "fv_mesh_set_wait_limit": (ctypes.c_int, [_vp, ctypes.c_uint32]),
             "fv_mesh_set_blocking": (ctypes.c_int, [_vp, _i32, _i32, _i32]),
@@ -97,6 +98,7 @@ def load():
             "fv_batch_destroy": (ctypes.c_int, [_vp]),
             "fv_batch_info": (ctypes.c_int, [_vp, _P(_i64), _vp]),
             "fv_batch_set_compensation": (ctypes.c_int, [_vp, _i32]),
+            "fv_batch_set_remainder": (ctypes.c_int, [_vp, _vp]),
             "fv_batch_set_variant": (ctypes.c_int, [_vp, _i32]),
             "fv_batch_get_variant": (ctypes.c_int, [_vp, _P(_i32)]),
             "fv_batch_step": (ctypes.c_int, [_vp, _vp, _i64, _dbl, _dbl, _i32, _vp, _vp]),
@@ -113,6 +115,15 @@ def load():
 def _check(rc):
     if rc != FV_OK:
         raise FVError(rc, load().fv_last_error().decode(errors="replace"))
+
+
+def _remainder_ptr(lo, n):
+    """Device pointer of a remainder tensor of 8 bytes per cell, or None."""
+    if lo is None:
+        return None
+    if not lo.is_cuda or not lo.is_contiguous() or lo.numel() * lo.element_size() != 8 * n:
+        raise ValueError(f"remainder must be a contiguous CUDA tensor of {8 * n} bytes")
+    return _vp(lo.data_ptr())
 
 
 def _np_ptr(a):
@@ -200,6 +211,15 @@ class Mesh:
 
     def set_compensation(self, enable: bool):
         _check(load().fv_mesh_set_compensation(self._h, int(bool(enable))))
+
+    def set_remainder(self, lo):
+        """fv_mesh_set_remainder: ``lo`` is a caller-owned CUDA tensor of
+        8 bytes per cell (e.g. int16 (n, 4) or uint8 (n, 8)) that carries the
+        compensated update's remainder across fv_step calls; None returns to
+        the remainder the library zeroes at every call.  The tensor must stay
+        alive while it is set."""
+        self._lo = lo
+        _check(load().fv_mesh_set_remainder(self._h, _remainder_ptr(lo, self.n)))
 
     def partition(self, nparts, part):
         """Local view of one part: dict with global_ids, halo_owner, nbr,
@@ -465,6 +485,12 @@ class Batch:
 
     def set_compensation(self, enable: bool):
         _check(load().fv_batch_set_compensation(self._h, int(bool(enable))))
+
+    def set_remainder(self, lo):
+        """fv_batch_set_remainder: as Mesh.set_remainder, 8 bytes per cell of
+        the padded batch (``n_padded`` cells)."""
+        self._lo = lo
+        _check(load().fv_batch_set_remainder(self._h, _remainder_ptr(lo, self.n_padded)))
 
     def set_variant(self, variant: int):
         _check(load().fv_batch_set_variant(self._h, int(variant)))

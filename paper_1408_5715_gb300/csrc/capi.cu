@@ -116,6 +116,7 @@ struct fv_mesh {
   uint2* d_lo = nullptr;        // FP32 compensated update: remainder of the state
   uint2* d_lo_stage = nullptr;  // ... and of the RK2 stage state
   bool compensated = true;      // FP32 meshes only
+  void* user_lo = nullptr;      // caller-owned remainder (fv_mesh_set_remainder)
   int variant = 1;              // step-kernel shape (fv_mesh_autotune / fv_mesh_set_variant)
   // two steps per launch (fv_mesh_set_blocking): tiles and halos on the device
   int blocking = 1;
@@ -515,6 +516,9 @@ void read_status(fv_mesh* m, cudaStream_t s, double* t_adv, bool check) {
   FV_CUDA(cudaMemcpyAsync(&h, m->d_scal, sizeof h, cudaMemcpyDeviceToHost, s));
   FV_CUDA(cudaStreamSynchronize(s));
   if (t_adv) *t_adv = h.t[m->last_t_slot];
+  if (check && (h.err & 4))
+    throw fv::Error{FV_ESTATE, "a bounded device wait gave up and the copies in flight did not "
+                               "drain either; destroy the mesh"};
   if (check && (h.err & 2))
     throw fv::Error{FV_ETIMEOUT, "a bounded device wait gave up; the state is not valid"};
   if (check && h.err) throw fv::Error{FV_ENONFINITE, "a step produced a non-finite state or "
@@ -635,6 +639,14 @@ int fv_mesh_set_compensation(fv_mesh* mesh, int32_t enable) {
     if (mesh->f64() && enable) invalid("compensated update applies to FV_F32 meshes only");
     mesh->compensated = enable != 0;
     mesh->drop_graph();
+  });
+}
+
+int fv_mesh_set_remainder(fv_mesh* mesh, void* lo) {
+  return guarded([&] {
+    check_mesh(mesh);
+    if (lo && mesh->f64()) invalid("FV_F64 meshes have no remainder");
+    mesh->user_lo = lo;
   });
 }
 
@@ -922,8 +934,13 @@ int fv_step(fv_mesh* mesh, void* U, int64_t nsteps, double cfl, double t_stop, i
     mesh->last_t_slot = 0;
     mesh->stepped = true;
     if (n > 0 && nsteps > 0) {
-      if (mesh->use_lo())  // the caller's float state carries no remainder
-        FV_CUDA(cudaMemsetAsync(mesh->d_lo, 0, n * sizeof(uint2), s));
+      if (mesh->use_lo()) {
+        if (mesh->user_lo)  // the remainder the caller kept from the last call
+          FV_CUDA(cudaMemcpyAsync(mesh->d_lo, mesh->user_lo, n * sizeof(uint2),
+                                  cudaMemcpyDeviceToDevice, s));
+        else  // the caller's float state carries no remainder
+          FV_CUDA(cudaMemsetAsync(mesh->d_lo, 0, n * sizeof(uint2), s));
+      }
       if (cfl > 0.0)
         FV_CUDA(fv::launch_bound(mesh->f64(), U, mesh->d_geom, n, &mesh->d_scal->bmin[0],
                                  &mesh->d_scal->err, s));
@@ -952,6 +969,13 @@ int fv_step(fv_mesh* mesh, void* U, int64_t nsteps, double cfl, double t_stop, i
       if (scheme == FV_SCHEME_FE && (launches % 2) == 1)
         FV_CUDA(cudaMemcpyAsync(U, mesh->d_work, n * mesh->rec_bytes(), cudaMemcpyDeviceToDevice,
                                 s));
+      if (mesh->use_lo() && mesh->user_lo) {
+        // single steps update the remainder in place; after an odd number of
+        // two-step launches it is in the second buffer
+        const uint2* last = (mesh->blocking == 2 && tail % 2 == 1) ? mesh->d_lo_stage : mesh->d_lo;
+        FV_CUDA(cudaMemcpyAsync(mesh->user_lo, last, n * sizeof(uint2), cudaMemcpyDeviceToDevice,
+                                s));
+      }
       mesh->last_t_slot = (int)(launches % 2);
     }
     if (t_advanced) read_status(mesh, s, t_advanced, true);
@@ -1075,6 +1099,7 @@ struct fv_batch {
   void* d_work = nullptr;
   uint2* d_lo = nullptr;
   uint2* d_lo_stage = nullptr;
+  void* user_lo = nullptr;  // caller-owned remainder (fv_batch_set_remainder)
   int* d_block_mesh = nullptr;
   int64_t* d_mesh_end = nullptr;
   int* d_first_block = nullptr;
@@ -1459,6 +1484,14 @@ int fv_batch_set_compensation(fv_batch* batch, int32_t enable) {
   });
 }
 
+int fv_batch_set_remainder(fv_batch* batch, void* lo) {
+  return guarded([&] {
+    check_batch(batch);
+    if (lo && batch->f64()) invalid("FV_F64 batches have no remainder");
+    batch->user_lo = lo;
+  });
+}
+
 int fv_batch_step(fv_batch* batch, void* U, int64_t nsteps, double cfl, double t_stop,
                   int32_t scheme, void* stream, double* t_advanced) {
   return guarded([&] {
@@ -1475,8 +1508,13 @@ int fv_batch_step(fv_batch* batch, void* U, int64_t nsteps, double cfl, double t
     batch->last_t_slot = 0;
     batch->stepped = true;
     if (nsteps > 0) {
-      if (batch->use_lo())
-        FV_CUDA(cudaMemsetAsync(batch->d_lo, 0, batch->n * sizeof(uint2), s));
+      if (batch->use_lo()) {
+        if (batch->user_lo)
+          FV_CUDA(cudaMemcpyAsync(batch->d_lo, batch->user_lo, batch->n * sizeof(uint2),
+                                  cudaMemcpyDeviceToDevice, s));
+        else
+          FV_CUDA(cudaMemsetAsync(batch->d_lo, 0, batch->n * sizeof(uint2), s));
+      }
       if (cfl > 0.0)
         FV_CUDA(fv::launch_batch_bound(batch->f64(), U, batch->d_geom, batch->d_block_mesh,
                                        batch->d_mesh_end, M, batch->n_blocks(), batch->d_bmin,
@@ -1514,6 +1552,9 @@ int fv_batch_step(fv_batch* batch, void* U, int64_t nsteps, double cfl, double t
       if (scheme == FV_SCHEME_FE && (nsteps % 2) == 1)
         FV_CUDA(cudaMemcpyAsync(U, batch->d_work, batch->n * batch->rec_bytes(),
                                 cudaMemcpyDeviceToDevice, s));
+      if (batch->use_lo() && batch->user_lo)  // updated in place by every step
+        FV_CUDA(cudaMemcpyAsync(batch->user_lo, batch->d_lo, batch->n * sizeof(uint2),
+                                cudaMemcpyDeviceToDevice, s));
       batch->last_t_slot = (int)(nsteps % 2);
     }
     if (t_advanced) {
@@ -1524,6 +1565,11 @@ int fv_batch_step(fv_batch* batch, void* U, int64_t nsteps, double cfl, double t
       FV_CUDA(cudaMemcpyAsync(&err, batch->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
       FV_CUDA(cudaStreamSynchronize(s));
       for (int k = 0; k < M; ++k) t_advanced[k] = t[batch->last_t_slot * M + k];
+      if (err & 4)
+        throw fv::Error{FV_ESTATE, "a bounded device wait gave up and the copies in flight did "
+                                   "not drain either; destroy the batch"};
+      if (err & 2)
+        throw fv::Error{FV_ETIMEOUT, "a bounded device wait gave up; the state is not valid"};
       if (err) throw fv::Error{FV_ENONFINITE, "a step produced a non-finite state or "
                                               "non-positive density or pressure"};
     }

@@ -30,7 +30,8 @@
 //                    gathered with plain loads.  Waits on the copies are
 //                    bounded (a.wait_limit polls); one that gives up sets
 //                    error bit 2, the block drains its own copies (bounded)
-//                    and returns.
+//                    and returns; if that drain gives up too it sets bit 4
+//                    (copies may still land in shared memory).
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -366,7 +367,8 @@ __global__ void __launch_bounds__(THREADS) k_step_pair_tma(PairArgs a) {
     if (tid == 0) {
       atomicOr(a.err, 2);
       for (int s = 0; s < 2; ++s)
-        if ((pending >> s) & 1u) mbar_wait(&bars[s], (phase >> s) & 1u, a.drain_limit);
+        if (((pending >> s) & 1u) && !mbar_wait(&bars[s], (phase >> s) & 1u, a.drain_limit))
+          atomicOr(a.err, 4);  // copies may still land: the device state is suspect
     }
     __syncthreads();
     return;

@@ -13,7 +13,8 @@
 // Every wait on an mbarrier is bounded by a_.wait_limit polls.  When a wait
 // gives up, the kernel sets bit 2 of the error word (the host reports
 // FV_ETIMEOUT), stops computing, waits (bounded again) for its own copies
-// still in flight and returns.
+// still in flight and returns.  If that second wait gives up too it also sets
+// bit 4 (the host reports FV_ESTATE: copies may still be landing).
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -216,7 +217,8 @@ __global__ void __launch_bounds__(kBlock) k_step_tma(BatchArgs b) {
     if (tid == 0) {
       atomicOr(a.err, 2);
       for (int s = 0; s < 2; ++s)
-        if (issued_not_waited[s]) mbar_wait(&bars[s], phase[s], a.drain_limit);
+        if (issued_not_waited[s] && !mbar_wait(&bars[s], phase[s], a.drain_limit))
+          atomicOr(a.err, 4);  // copies may still land: the device state is suspect
     }
     __syncthreads();
     return;

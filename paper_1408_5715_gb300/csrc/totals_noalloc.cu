@@ -12,7 +12,6 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
-#include <mutex>
 #include <string>
 
 #include "fv.h"
@@ -28,7 +27,6 @@ constexpr int kTileThreads = 256;
 constexpr int kTileCellsPerThread = 16;
 constexpr int64_t kTileCells = (int64_t)kTileThreads * kTileCellsPerThread;  // 4096
 constexpr int kNoAllocTiles = 4096;
-constexpr int kMaxDevices = 64;
 
 // One partial (mass, x-momentum, y-momentum, energy) per tile of 4096 cells.
 static __device__ __align__(256) double g_noalloc_partials[kNoAllocTiles * 4];
@@ -105,21 +103,18 @@ __global__ void __launch_bounds__(kTileThreads) k_tile_totals_final(const double
   }
 }
 
-// Device address of g_noalloc_partials, looked up once per device.  In host
-// code the array's name is only a host-side stand-in, so kernels must be
-// given the address that cudaGetSymbolAddress returns for the current device.
-std::mutex g_addr_mutex;
-double* g_addr[kMaxDevices] = {};
-
-cudaError_t scratch_address(int dev, double** out) {
-  std::lock_guard<std::mutex> lock(g_addr_mutex);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
-    if (e != cudaSuccess) return e;
-    g_addr[dev] = static_cast<double*>(p);
-  }
-  *out = g_addr[dev];
+// Device address of g_noalloc_partials for the current device.  In host code
+// the array's name is only a host-side stand-in, so kernels must be given the
+// address that cudaGetSymbolAddress returns with the device current.  The
+// lookup is repeated on every call instead of cached: after cudaDeviceReset
+// (or a release and re-creation of the primary context) the module is loaded
+// again and an address kept from before would point at freed memory.  The
+// first lookup on a device also loads the library's device code there.
+cudaError_t scratch_address(double** out) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+  if (e != cudaSuccess) return e;
+  *out = static_cast<double*>(p);
   return cudaSuccess;
 }
 
@@ -137,12 +132,16 @@ extern "C" int fv_conserved_totals_noalloc(const void* U, const double* area, in
                                " exceeds the no-allocation scratch capacity of " +
                                std::to_string((int64_t)kNoAllocTiles * kTileCells) + " cells");
   if (!out || (n_cells > 0 && (!U || !area))) return fail(FV_EINVAL, "null pointer");
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return fail(FV_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices) return fail(FV_EINVAL, "device id out of range");
+  // the kernels read U as 16-byte (FP32) or 32-byte (FP64) records and the
+  // areas and totals as doubles: a misaligned pointer would fault the device
+  const uintptr_t u_align = precision == FV_F64 ? 32 : 16;
+  if (n_cells > 0 && (reinterpret_cast<uintptr_t>(U) % u_align != 0 ||
+                      reinterpret_cast<uintptr_t>(area) % 8 != 0))
+    return fail(FV_EINVAL, "U must be " + std::to_string(u_align) +
+                               "-byte aligned and area 8-byte aligned");
+  if (reinterpret_cast<uintptr_t>(out) % 8 != 0) return fail(FV_EINVAL, "out must be 8-byte aligned");
   double* partials = nullptr;
-  e = scratch_address(dev, &partials);
+  cudaError_t e = scratch_address(&partials);
   if (e != cudaSuccess)
     return fail(FV_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

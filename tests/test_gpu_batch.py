@@ -102,6 +102,22 @@ def test_batch_t_stop_and_bad_state():
     assert e.value.code == B.FV_ENONFINITE
 
 
+@pytest.mark.parametrize("variant", [5, 0, 6])
+def test_batch_split_calls_with_remainder_equal_one_call(variant):
+    items = make_set(3, n_meshes=4)
+    _, batch, flat, _ = solo_and_batch(items, "f32", 0, "fe", variant=variant)
+    start = flat.clone()
+    batch.step(flat, 151, 0.4)
+    lo = torch.zeros((batch.n_padded, 4), dtype=torch.int16, device="cuda")
+    batch.set_remainder(lo)
+    split = start.clone()
+    for k in (96, 1, 54):
+        batch.step(split, k, 0.4)
+    for k in range(len(items)):
+        o0, o1 = batch.offsets[k], batch.offsets[k] + items[k][0].n_tri
+        assert torch.equal(flat[o0:o1], split[o0:o1]), k
+
+
 def test_batch_rejects_mixed_precision():
     a = B.Mesh.from_input(W.periodic_square(4, 4, seed=1), "f32")
     b = B.Mesh.from_input(W.periodic_square(4, 4, seed=1), "f64")

@@ -122,6 +122,28 @@ def test_channel_walls_farfield_fp64_parity(orc):
     assert rel_l2(U32.double().cpu().numpy()[:, 0], Uo[:, 0]) <= 1e-5
 
 
+def test_am1_ordered_channel_fp64_parity_on_every_shape(orc):
+    # Amoeba1 (Sec. 4.2) renumbers the cells of a channel with walls and far
+    # field; every kernel shape steps it and matches the oracle run on the
+    # unpermuted mesh
+    mi = shuffled(W.channel_bump(60, 25, seed=8), seed=5)
+    uinf_prim = W.freestream(0.5)
+    om, g64, _ = pair(orc, mi, uinf_prim)
+    U0 = W.random_smooth_state(mi.centroids(), seed=3)
+    Uo, to, _, bad = om.run(U0, 80, 0.4)
+    assert not bad
+    perm = g64.renumber("am1")
+    assert sorted(perm) == list(range(mi.n_tri))
+    bw, _ = g64.diagnostics()
+    assert bw < mi.n_tri // 4  # a banded order, unlike the shuffled input
+    for variant in range(7):
+        g64.set_variant(variant)
+        U = dev(U0[perm], torch.float64)
+        t = g64.step(U, 80, 0.4)
+        assert t == pytest.approx(to, rel=1e-13), variant
+        assert rel_err_max(U.cpu().numpy(), Uo[perm]) <= 1e-12, variant
+
+
 @pytest.mark.parametrize("scheme", ["fe", "rk2"])
 def test_sod_strip_extrapolation_and_t_stop(orc, scheme):
     mi = shuffled(W.shock_tube_strip(120, 6, seed=7), seed=4)
@@ -147,22 +169,76 @@ def test_rk2_fp64_matches_oracle(c1):
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_split_calls_equal_one_call(c1, prec):
     # 197 steps in one call (two captured graphs + a remainder, odd count)
-    # equal 96 + 1 + 100 steps in three calls, bit for bit
+    # equal 96 + 1 + 100 steps in three calls, bit for bit; the compensated
+    # FP32 update carries its remainder across the calls in a caller buffer
     mi, U0, om, g64, g32 = c1
     g = g64 if prec == "f64" else B.Mesh.from_input(mi, "f32")
-    if prec == "f32":
-        g.set_compensation(False)  # the float remainder is not carried across calls
     dt_ = torch.float64 if prec == "f64" else torch.float32
     A = dev(U0, dt_)
     Bt = dev(U0, dt_)
     ta = g.step(A, 197, 0.4)
+    if prec == "f32":
+        lo = torch.zeros((mi.n_tri, 4), dtype=torch.int16, device="cuda")
+        g.set_remainder(lo)
     tb = g.step(Bt, 96, 0.4) + g.step(Bt, 1, 0.4) + g.step(Bt, 100, 0.4)
+    assert torch.equal(A, Bt)
+    assert ta == pytest.approx(tb, rel=1e-12)
+    if prec == "f32":
+        assert lo.abs().sum() > 0  # the remainder is carried, not zero
+        # without the caller's remainder every call starts from zero again
+        g.set_remainder(None)
+        C = dev(U0, dt_)
+        for k in (96, 1, 100):
+            g.step(C, k, 0.4)
+        assert not torch.equal(A, C)
+
+
+def _resumed_mesh(mi, blocking):
+    g = B.Mesh.from_input(mi, "f32")
+    perm = g.renumber("hilbert")
+    if blocking == 2:
+        g.set_blocking(2, 512)
+    return g, perm
+
+
+@pytest.mark.parametrize("blocking,scheme", [(1, "fe"), (1, "rk2"), (2, "fe")])
+def test_checkpoint_and_resume_is_bitwise(c1, tmp_path, blocking, scheme):
+    # one call of 206 steps against three calls (103, 50, 53 steps), the
+    # state and the compensated update's remainder saved to files after the
+    # first and loaded into a new mesh and new buffers.  With two steps per
+    # launch 103 and 50 end on an odd number of pair launches (the remainder
+    # then sits in the second buffer) and 103 and 53 end with a single step.
+    mi, U0, *_ = c1
+    g, perm = _resumed_mesh(mi, blocking)
+    A = dev(U0[perm], torch.float32)
+    ta = g.step(A, 206, 0.4, scheme=scheme)
+    g1, _ = _resumed_mesh(mi, blocking)
+    Bt = dev(U0[perm], torch.float32)
+    lo = torch.zeros((mi.n_tri, 4), dtype=torch.int16, device="cuda")
+    g1.set_remainder(lo)
+    tb = g1.step(Bt, 103, 0.4, scheme=scheme)
+    np.save(tmp_path / "U.npy", Bt.cpu().numpy())
+    np.save(tmp_path / "lo.npy", lo.cpu().numpy())
+    del g1, Bt, lo
+    g2, _ = _resumed_mesh(mi, blocking)
+    Bt = torch.tensor(np.load(tmp_path / "U.npy"), device="cuda")
+    lo = torch.tensor(np.load(tmp_path / "lo.npy"), device="cuda")
+    g2.set_remainder(lo)
+    tb += g2.step(Bt, 50, 0.4, scheme=scheme) + g2.step(Bt, 53, 0.4, scheme=scheme)
     assert torch.equal(A, Bt)
     assert ta == pytest.approx(tb, rel=1e-12)
 
 
+def test_remainder_refused_for_fp64(c1):
+    mi, *_ = c1
+    g = B.Mesh.from_input(mi, "f64")
+    with pytest.raises(B.FVError):
+        g.set_remainder(torch.zeros((mi.n_tri, 4), dtype=torch.int16, device="cuda"))
+    g.set_remainder(None)
+
+
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-@pytest.mark.parametrize("order", ["rcm", "hilbert", "shuffle"])
+@pytest.mark.parametrize("order", ["rcm", "hilbert", "shuffle", "am1"])
 def test_renumbering_leaves_results_unchanged(c1, prec, order):
     mi, U0, om, g64, g32 = c1
     dt_ = torch.float64 if prec == "f64" else torch.float32
