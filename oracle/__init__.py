@@ -89,6 +89,13 @@ def _load():
             lib.orc_closure_loss_grad.restype = ctypes.c_double
             lib.orc_closure_loss_grad.argtypes = [ctypes.c_int64, _i32, _d, _d, _d, _d, _d,
                                                   ctypes.c_double, _d, _d, ctypes.c_int32, _d]
+            lib.orc_closure_feature_errors.restype = None
+            lib.orc_closure_feature_errors.argtypes = [_d, _d, _d, _d]
+            lib.orc_closure_scale_interval.restype = ctypes.c_int
+            lib.orc_closure_scale_interval.argtypes = [_d, _d, _d, _d, _d]
+            lib.orc_closure_face_intervals.restype = None
+            lib.orc_closure_face_intervals.argtypes = [ctypes.c_int64, _i32, _d, _d, _d, _d,
+                                                       _d, _d, _i32]
             lib.orc_bandwidth.restype = ctypes.c_int64
             lib.orc_bandwidth.argtypes = [ctypes.c_int64, _i32]
             lib.orc_serial_bandwidth.restype = ctypes.c_int64
@@ -206,6 +213,20 @@ class Mesh:
                                              _pd(th), int(bf16_acts), _pd(g))
         return (loss, g) if grad else loss
 
+    def closure_scale_intervals(self, U, theta):
+        """Interval [lo, hi] of every face's scale over the admissible
+        bfloat16 roundings of its features and first-layer activations
+        (orc_closure_face_intervals), and whether every rounding of the face
+        is determined.  Returns (lo, hi, determined), each (n, 3)."""
+        U = _f64(U, (self.n, 4))
+        th = _f64(theta)
+        lo = np.empty((self.n, 3))
+        hi = np.empty((self.n, 3))
+        det = np.empty((self.n, 3), np.int32)
+        _load().orc_closure_face_intervals(self.n, _pi(self.nbr), _pd(self.nrm), _pd(self.uinf),
+                                           _pd(U), _pd(th), _pd(lo), _pd(hi), _pi(det))
+        return lo, hi, det.astype(bool)
+
     def bandwidth(self):
         return _load().orc_bandwidth(self.n, _pi(self.nbr))
 
@@ -255,3 +276,23 @@ def closure_mlp(theta, feat, bf16_acts=False):
 def cell_dt_bound(U, nrm_cell, vol):
     U, nc = _f64(U), _f64(nrm_cell)
     return _load().orc_cell_dt_bound(_pd(U), _pd(nc), float(vol))
+
+
+def closure_feature_errors(UL, UR, n):
+    """Bounds on the FP32 evaluation error of the eight features of a face."""
+    UL, UR, n = _f64(UL), _f64(UR), _f64(n)
+    e = np.empty(8, np.float64)
+    _load().orc_closure_feature_errors(_pd(UL), _pd(UR), _pd(n), _pd(e))
+    return e
+
+
+def closure_scale_interval(theta, feat, feat_err=None):
+    """Interval of the MLP's scale for one feature vector over the admissible
+    bfloat16 roundings (orc_closure_scale_interval); feat_err None takes the
+    features as exact.  Returns (lo, hi, determined)."""
+    th, f = _f64(theta), _f64(feat)
+    e = None if feat_err is None else _f64(feat_err)
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    det = _load().orc_closure_scale_interval(_pd(th), _pd(f), _pd(e), ctypes.byref(lo),
+                                             ctypes.byref(hi))
+    return lo.value, hi.value, bool(det)

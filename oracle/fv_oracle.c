@@ -416,6 +416,157 @@ double orc_closure_scale(const double* theta, int32_t bf16_acts, const double* U
 }
 
 /* ------------------------------------------------------------------------ */
+/* Rounding ambiguity of the learned scale (test support).                  */
+/*                                                                          */
+/* A device evaluates the features in FP32 and the first hidden layer with  */
+/* FP32 accumulation, then rounds both to bfloat16 as tensor-core operands.  */
+/* Where such a value lies within its FP32 evaluation error of a bfloat16    */
+/* rounding boundary, either neighbouring bfloat16 value is a correct       */
+/* result of that evaluation, and the scale differs accordingly (a relative */
+/* change of up to 2^-8 in one operand).  The functions below bound the     */
+/* FP32 evaluation error of every rounded value and enumerate the scales of */
+/* all admissible roundings, so that a device result can be checked        */
+/* against the set instead of against one value.                           */
+/* ------------------------------------------------------------------------ */
+
+static void orc_neighbour_state(int64_t c, int k, const int32_t* nbr, const double* nrm,
+                                const double* uinf, const double* U, double* UR);
+
+/* Relative error bound of one FP32 operation, taken as 2^-22 so that it    */
+/* also covers approximate reciprocals and square roots (about 2^-23).      */
+#define ORC_U32 (1.0 / 8388608.0)
+/* Safety factor on the first-order error bounds below. */
+#define ORC_ERR_SAFETY 1.0
+
+/* First-order bounds on |f32 - f| for the eight features of
+ * orc_closure_features evaluated in FP32 from the same (FP32-exact) states:
+ * each operation is charged ORC_U32 of its result and the errors of its
+ * inputs are propagated by their partial derivatives.  err[8] out. */
+void orc_closure_feature_errors(const double* UL, const double* UR, const double* n,
+                                double* err) {
+  const double u = ORC_U32;
+  double len = sqrt(n[0] * n[0] + n[1] * n[1]);
+  double nx = n[0] / len, ny = n[1] / len;
+  orc_face_state S[2];
+  double e_p[2], e_c[2], e_un[2], spd[2];
+  int k;
+  orc_to_face_frame(UL, nx, ny, &S[0]);
+  orc_to_face_frame(UR, nx, ny, &S[1]);
+  for (k = 0; k < 2; ++k) {
+    const orc_face_state* X = &S[k];
+    double m2 = X->rho * (X->un * X->un + X->ut * X->ut); /* rho |v|^2 */
+    spd[k] = fabs(X->un) + fabs(X->ut);
+    /* p = (gamma-1)(E - m2/2): the kinetic part carries 4u, the subtraction u */
+    e_p[k] = 2.0 * u * (X->E + m2) + u * X->p;
+    /* c = sqrt(gamma p / rho): half the relative error of p/rho, plus rounding */
+    e_c[k] = X->c * (0.5 * e_p[k] / X->p + 2.5 * u);
+    /* u_n = u hx + v hy: velocities (2u), unit normal (4u), products and sum */
+    e_un[k] = 8.0 * u * spd[k];
+  }
+  double cbar = 0.5 * (S[0].c + S[1].c);
+  double pbar = 0.5 * (S[0].p + S[1].p);
+  double e_cbar = 0.5 * (e_c[0] + e_c[1]) + u * cbar;
+  double r_icb = e_cbar / cbar + u; /* relative error of 1 / c-bar */
+  double f[ORC_NF];
+  orc_closure_features(UL, UR, n, f);
+  err[0] = 4.0 * u * f[0]; /* jump exact or one rounding, mean, reciprocal, product */
+  err[1] = (e_un[0] + e_un[1] + u * fabs(S[1].un - S[0].un)) / cbar + f[1] * (r_icb + u);
+  err[2] = (e_un[0] + e_un[1] + u * fabs(S[1].ut - S[0].ut)) / cbar + f[2] * (r_icb + u);
+  err[3] = (e_p[0] + e_p[1] + u * fabs(S[1].p - S[0].p)) / pbar +
+           f[3] * (0.5 * (e_p[0] + e_p[1]) / pbar + 3.0 * u);
+  err[4] = 0.5 * (e_un[0] + e_un[1] + u * fabs(S[0].un + S[1].un)) / cbar + f[4] * (r_icb + u);
+  err[5] = 0.0;
+  for (k = 0; k < 2; ++k) {
+    double t = fabs(S[k].un) / S[k].c;
+    err[5] += e_un[k] / S[k].c + t * (e_c[k] / S[k].c + 2.0 * u);
+  }
+  err[5] += u * (fabs(S[0].un) / S[0].c + fabs(S[1].un) / S[1].c);
+  err[6] = (S[0].c < S[1].c ? e_c[0] : e_c[1]) / cbar + f[6] * (r_icb + u);
+  err[7] = (S[0].c < S[1].c ? e_c[1] : e_c[0]) / cbar + f[7] * (r_icb + u);
+  for (k = 0; k < ORC_NF; ++k) err[k] *= ORC_ERR_SAFETY;
+}
+
+/* Interval of the scale over every admissible rounding (test support).
+ * Each bfloat16 operand is replaced by the interval of bfloat16 values that
+ * its admissible FP32 results round to (rounding is monotone, so the ends
+ * are the roundings of the ends of the error window); the intervals are
+ * carried through the layers in FP64 in centre-radius form (exact weights
+ * times an interval), the ReLUs and the sigmoid are monotone and map ends to
+ * ends.  The FP32 accumulation of layer 1 is charged 16 * 2^-23 of the sum
+ * of the magnitudes of its terms (products of bfloat16 values are exact in
+ * FP32; the sum may be rounded or truncated at every addition).
+ *   feat_err  nullable: error bounds of the features
+ *             (orc_closure_feature_errors); NULL takes the features as exact.
+ * Writes [*s_lo, *s_hi] and returns 1 when every rounding is determined (each
+ * operand interval is a single bfloat16 value), else 0.  Rounding errors of
+ * an FP32 evaluation of layers 2 and 3 are not included. */
+int orc_closure_scale_interval(const double* theta, const double* feat, const double* feat_err,
+                               double* s_lo, double* s_hi) {
+  const double* th = theta;
+  double xlo[ORC_NF], xhi[ORC_NF], hlo[ORC_NH], hhi[ORC_NH], glo[ORC_NH], ghi[ORC_NH];
+  int i, j, determined = 1;
+  for (j = 0; j < ORC_NF; ++j) {
+    double w = feat_err ? feat_err[j] : 0.0;
+    double lo = feat[j] - w;
+    xlo[j] = orc_round_bf16(lo > 0.0 ? lo : 0.0);
+    xhi[j] = orc_round_bf16(feat[j] + w);
+    if (xlo[j] != xhi[j]) determined = 0;
+  }
+  for (i = 0; i < ORC_NH; ++i) {
+    double c = th[ORC_OFF_B1 + i], r = 0.0, mag = fabs(th[ORC_OFF_B1 + i]);
+    for (j = 0; j < ORC_NF; ++j) {
+      double wij = th[ORC_OFF_W1 + i * ORC_NF + j];
+      c += wij * 0.5 * (xlo[j] + xhi[j]);
+      r += fabs(wij) * 0.5 * (xhi[j] - xlo[j]);
+      mag += fabs(wij) * xhi[j];
+    }
+    double w = 10.0 / 8388608.0 * mag;
+    double lo = c - r - w, hi = c + r + w;
+    hlo[i] = orc_round_bf16(lo > 0.0 ? lo : 0.0);
+    hhi[i] = orc_round_bf16(hi > 0.0 ? hi : 0.0);
+    if (hlo[i] != hhi[i]) determined = 0;
+  }
+  for (i = 0; i < ORC_NH; ++i) {
+    double c = th[ORC_OFF_B2 + i], r = 0.0;
+    for (j = 0; j < ORC_NH; ++j) {
+      double wij = th[ORC_OFF_W2 + i * ORC_NH + j];
+      c += wij * 0.5 * (hlo[j] + hhi[j]);
+      r += fabs(wij) * 0.5 * (hhi[j] - hlo[j]);
+    }
+    glo[i] = c - r > 0.0 ? c - r : 0.0;
+    ghi[i] = c + r > 0.0 ? c + r : 0.0;
+  }
+  double zc = th[ORC_OFF_B3], zr = 0.0;
+  for (i = 0; i < ORC_NH; ++i) {
+    zc += th[ORC_OFF_W3 + i] * 0.5 * (glo[i] + ghi[i]);
+    zr += fabs(th[ORC_OFF_W3 + i]) * 0.5 * (ghi[i] - glo[i]);
+  }
+  /* the same expression as orc_mlp_forward: a determined face gives its bits */
+  *s_lo = 0.2 + 1.3 * (1.0 / (1.0 + exp(-(zc - zr))));
+  *s_hi = 0.2 + 1.3 * (1.0 / (1.0 + exp(-(zc + zr))));
+  return determined;
+}
+
+/* orc_closure_scale_interval for every face of a mesh with state U (ghost
+ * states as in the residual): s_lo[3n], s_hi[3n], determined[3n]. */
+void orc_closure_face_intervals(int64_t n, const int32_t* nbr, const double* nrm,
+                                const double* uinf, const double* U, const double* theta,
+                                double* s_lo, double* s_hi, int32_t* determined) {
+  int64_t c;
+  int k;
+  for (c = 0; c < n; ++c)
+    for (k = 0; k < 3; ++k) {
+      double UR[4], f[ORC_NF], e[ORC_NF];
+      const double* nk = nrm + 6 * c + 2 * k;
+      orc_neighbour_state(c, k, nbr, nrm, uinf, U, UR);
+      orc_closure_features(U + 4 * c, UR, nk, f);
+      orc_closure_feature_errors(U + 4 * c, UR, nk, e);
+      determined[3 * c + k] =
+          orc_closure_scale_interval(theta, f, e, s_lo + 3 * c + k, s_hi + 3 * c + k);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Semi-discrete residual dU/dt = -(1/V_T) sum_f F_f . n_f   (Eq. 4)        */
 /* ------------------------------------------------------------------------ */
 

@@ -2,11 +2,17 @@
 flux) against the FP64 oracle's MLP with the same bfloat16 weights and the
 same bfloat16 rounding of layer inputs.
 
-Tolerances: the GPU computes features in FP32 and accumulates in FP32, the
-oracle in FP64, so a feature or hidden activation that lies within FP32
-rounding of a bfloat16 rounding boundary can round to the neighbouring
-bfloat16 value (a relative change of 2^-8 in one input).  Scales therefore
-agree to 1e-5 for almost all rows and to a few 1e-3 for the rest.
+The GPU evaluates the features in FP32 and accumulates layer 1 in FP32 before
+rounding both to bfloat16, so a value within its FP32 evaluation error of a
+bfloat16 rounding boundary may round either way.  The oracle bounds that error
+for every rounded value and gives, per face, the interval of scales over all
+admissible roundings and whether every rounding is determined
+(orc_closure_scale_interval).  Every face is checked on its own: a face whose
+roundings are determined must agree with the oracle's scale to 1e-5; every
+other face must lie within its interval widened by 1e-5 (the FP32 rounding of
+layers 2 and 3).  Gradients are compared on inputs where every face whose
+roundings are not determined is inert (equal states on both sides), so that
+its scale enters neither the flux nor the gradient.
 """
 import math
 
@@ -49,6 +55,20 @@ def make_theta(seed, scale=0.5):
     return th, th64
 
 
+TOL_S = 1e-5  # FP32 rounding of layers 2 and 3 and of the sigmoid
+
+
+def check_scales(s_gpu, s_orc, lo, hi, det):
+    """Every entry: inside its admissible interval (widened by TOL_S); entries
+    whose roundings are determined: within TOL_S of the oracle."""
+    s_gpu, s_orc, lo, hi, det = (np.asarray(a).ravel() for a in (s_gpu, s_orc, lo, hi, det))
+    out = (s_gpu < lo - TOL_S) | (s_gpu > hi + TOL_S)
+    assert not out.any(), (np.nonzero(out)[0][:10], s_gpu[out][:5], lo[out][:5], hi[out][:5])
+    d = np.abs(s_gpu - s_orc)[det]
+    assert d.max() <= TOL_S, d.max()
+    return det.mean()
+
+
 def test_mlp_alone_matches_oracle(orc):
     th, th64 = make_theta(1)
     cl = B.Closure(th)
@@ -58,10 +78,10 @@ def test_mlp_alone_matches_oracle(orc):
     f = bf16(f).astype(np.float64)  # bfloat16-exact inputs: no rounding ambiguity at layer 1
     s_gpu = cl.eval(torch.tensor(f, dtype=torch.float32, device="cuda")).cpu().numpy()
     s_orc = np.array([orc.closure_mlp(th64, f[i], bf16_acts=True) for i in range(rows)])
-    d = np.abs(s_gpu - s_orc)
+    lo, hi, det = map(np.array, zip(*[orc.closure_scale_interval(th64, f[i]) for i in range(rows)]))
     assert (s_gpu >= 0.2).all() and (s_gpu <= 1.5).all()
-    assert np.quantile(d, 0.99) <= 1e-5, np.quantile(d, [0.5, 0.99, 1.0])
-    assert d.max() <= 5e-3
+    frac = check_scales(s_gpu, s_orc, lo, hi, det)
+    assert frac > 0.5, frac
     # the scales really vary with the features
     assert s_gpu.std() > 0.05
 
@@ -83,9 +103,9 @@ def test_face_scales_match_oracle_and_are_swap_invariant(orc, vortex_case):
     s = cl.scales(g, U).cpu().numpy()
     om = orc.Mesh(mi.xy, mi.tri, mi.canon, None, 0)
     _, so = om.residual(U0, theta=th64, bf16_acts=True, return_scales=True)
-    d = np.abs(s - so)
-    assert np.quantile(d, 0.99) <= 1e-4, np.quantile(d, [0.5, 0.99, 1.0])
-    assert d.max() <= 2e-2
+    lo, hi, det = om.closure_scale_intervals(U0, th64)
+    check_scales(s, so, lo, hi, det)
+    assert det.any() and (hi - lo).max() < 0.1
     # both cells of every face use the same scale, bit for bit
     nbr, nrm, _ = g.export()
     for c in range(mi.n_tri):
@@ -147,15 +167,74 @@ def test_closure_residual_and_errors(vortex_case):
         g64.step(torch.tensor(U0, device="cuda"), 1, 0.4, closure=cl)
 
 
+def settle_undetermined_faces(orc, om, U, theta, max_iter=100):
+    """Input generation for the gradient comparison: makes every face whose
+    bfloat16 roundings are not all determined inert -- its two states equal,
+    so its scale enters neither the flux nor the gradient.  Cells are merged
+    into clusters of one state (union-find); a cluster at an undetermined wall
+    face loses its momentum (the mirrored ghost then equals the cell), one at
+    an undetermined far-field face takes the free stream (at rest here, so
+    both hold at once).  Merging never separates two cells, so it settles."""
+    U = U.copy()
+    n = om.n
+    parent = np.arange(n)
+    pin = np.zeros(n, int)  # 0 free, 1 no momentum (wall), 2 free stream
+
+    def find(a):
+        while parent[a] != a:
+            parent[a] = parent[parent[a]]
+            a = parent[a]
+        return a
+
+    for _ in range(max_iter):
+        _, _, det = om.closure_scale_intervals(U, theta)
+        changed = False
+        for c, k in zip(*np.nonzero(~det)):
+            m, rc = om.nbr[c, k], find(c)
+            if m >= 0:
+                rm = find(m)
+                if rc == rm:
+                    continue
+                parent[rm] = rc
+                pin[rc] = max(pin[rc], pin[rm])
+            elif m == orc.WALL and pin[rc] < 1:
+                pin[rc] = 1
+            elif m == orc.FARFIELD and pin[rc] < 2:
+                pin[rc] = 2
+            else:
+                continue
+            changed = True
+        if not changed:
+            return U
+        roots = np.array([find(a) for a in range(n)])
+        for r in np.unique(roots):
+            st = om.uinf.copy() if pin[r] == 2 else U[r].copy()
+            if pin[r] == 1:
+                st[1:3] = 0.0
+            U[roots == r] = st
+    raise RuntimeError("undetermined faces did not settle")
+
+
 def test_closure_gradient_matches_oracle(orc):
     # channel with walls and far field: ghost faces take part too
     mi = W.channel_bump(36, 14, seed=12)
-    prim = W.freestream(0.5)
+    prim = (1.0, 0.0, 0.0, 1.0)  # free stream at rest (see settle_undetermined_faces)
     uinf = W.conserved(*prim)
-    U0 = W.random_smooth_state(mi.centroids(), seed=6).astype(np.float32).astype(np.float64)
     rng = np.random.default_rng(7)
-    Ut = (U0 + 0.02 * rng.normal(size=U0.shape)).astype(np.float32).astype(np.float64)
+    # cell states drawn independently: the features are O(1), not cancelling jumps
+    n = mi.n_tri
+    U0 = W.conserved(rng.uniform(0.5, 2.0, n), rng.uniform(-0.5, 0.5, n),
+                     rng.uniform(-0.5, 0.5, n), rng.uniform(0.5, 2.0, n))
+    U0 = U0.astype(np.float32).astype(np.float64)
     th, th64 = make_theta(8, scale=0.4)
+    om = orc.Mesh(mi.xy, mi.tri, None, mi.bnd, 0, uinf)
+    U0 = settle_undetermined_faces(orc, om, U0, th64)
+    Ut = (U0 + 0.02 * rng.normal(size=U0.shape)).astype(np.float32).astype(np.float64)
+    _, _, det = om.closure_scale_intervals(U0, th64)
+    inner = om.nbr >= 0
+    active = det.copy()  # faces whose scale matters: determined, or not inert
+    active[inner] &= ~(U0[om.nbr[inner]] == U0[np.nonzero(inner)[0]]).all(-1)
+    assert active.mean() > 0.5, active.mean()
     dt, w = 2e-3, np.array([1.0, 0.5, 0.5, 2.0])
     g = B.Mesh.from_input(mi, "f32")
     g.set_freestream(*prim)
@@ -164,16 +243,17 @@ def test_closure_gradient_matches_oracle(orc):
     Utd = torch.tensor(Ut, dtype=torch.float32, device="cuda")
     loss, grad = cl.loss_grad(g, Ud, Utd, dt, w)
     grad = grad.cpu().numpy().astype(np.float64)
-    om = orc.Mesh(mi.xy, mi.tri, None, mi.bnd, 0, uinf)
     lo, go = om.closure_loss_grad(U0, Ut, dt, w, th64, bf16_acts=True)
-    assert loss == pytest.approx(lo, rel=1e-4)
-    err = np.linalg.norm(grad - go) / np.linalg.norm(go)
-    assert err <= 3e-3, err
-    # layer by layer, each block of parameters on its own
+    assert loss == pytest.approx(lo, rel=1e-5)
+    # each block of parameters on its own (W1, b1, W2, b2, w3, b3), and each
+    # entry against its block's scale
     for sl in (slice(0, 256), slice(256, 288), slice(288, 1312), slice(1312, 1344),
                slice(1344, 1376), slice(1376, 1377)):
-        e = np.linalg.norm(grad[sl] - go[sl]) / (np.linalg.norm(go[sl]) + 1e-30)
-        assert e <= 1e-2, (sl, e)
+        ref = go[sl]
+        assert np.linalg.norm(ref) > 0, sl
+        e = np.linalg.norm(grad[sl] - ref) / np.linalg.norm(ref)
+        assert e <= 1e-3, (sl, e)
+        assert (np.abs(grad[sl] - ref) <= 1e-3 * np.abs(ref).max()).all(), sl
     # deterministic
     loss2, grad2 = cl.loss_grad(g, Ud, Utd, dt, w)
     assert loss2 == loss and np.array_equal(grad2.cpu().numpy().astype(np.float64), grad)

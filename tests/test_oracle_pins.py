@@ -570,3 +570,151 @@ def test_bandwidth_brute_force(orc, c1):
     j = nb.reshape(-1)
     ok = j >= 0
     assert pm.bandwidth() == np.abs(i[ok] - j[ok]).max()
+
+
+# ---------------------------------------------------------------------------
+# rounding ambiguity of the learned scale: error bounds and scale intervals
+# ---------------------------------------------------------------------------
+def _bf16(x):
+    """bfloat16 round-to-nearest-even of float32 values, returned as float64."""
+    f = np.asarray(x, np.float32).copy()
+    b = f.view(np.uint32)
+    b += np.uint32(0x7FFF) + ((b >> 16) & np.uint32(1))
+    b &= np.uint32(0xFFFF0000)
+    return f.astype(np.float64)
+
+
+def _features_fp32(UL, UR, n):
+    """The eight closure features evaluated in numpy float32 (every operation
+    rounded to nearest), in an order of its own: velocities from the
+    conserved state, face-normal components through the unit normal."""
+    f32 = np.float32
+
+    def prim(U):
+        r, mx, my, E = (f32(x) for x in U)
+        u, v = mx / r, my / r
+        p = f32(0.4) * (E - f32(0.5) * (mx * u + my * v))
+        return r, u, v, p, np.sqrt(f32(1.4) * p / r)
+
+    nx, ny = f32(n[0]), f32(n[1])
+    ln = np.sqrt(nx * nx + ny * ny)
+    hx, hy = nx / ln, ny / ln
+    rL, uL, vL, pL, cL = prim(UL)
+    rR, uR, vR, pR, cR = prim(UR)
+    unL, unR = uL * hx + vL * hy, uR * hx + vR * hy
+    utL, utR = vL * hx - uL * hy, vR * hx - uR * hy
+    cb = f32(0.5) * (cL + cR)
+    return np.array([abs(rR - rL) / (f32(0.5) * (rL + rR)), abs(unR - unL) / cb,
+                     abs(utR - utL) / cb, abs(pR - pL) / (f32(0.5) * (pL + pR)),
+                     abs(f32(0.5) * (unL + unR)) / cb, abs(unR / cR - unL / cL),
+                     min(cL, cR) / cb, max(cL, cR) / cb], np.float64)
+
+
+def _mlp_fp32(th, x):
+    """The MLP in float32 on bfloat16 inputs x: layer 1 accumulated term by
+    term in float32 and rounded to bfloat16, layers 2 and 3 in float32."""
+    f32 = np.float32
+    W1 = th[:256].reshape(32, 8).astype(f32)
+    b1, W2 = th[256:288].astype(f32), th[288:1312].reshape(32, 32).astype(f32)
+    b2, w3, b3 = th[1312:1344].astype(f32), th[1344:1376].astype(f32), f32(th[1376])
+    acc = np.zeros(32, f32)
+    for j in range(8):
+        acc = acc + W1[:, j] * f32(x[j])
+    h1 = _bf16(np.maximum(acc + b1, f32(0))).astype(f32)
+    acc = np.zeros(32, f32)
+    for j in range(32):
+        acc = acc + W2[:, j] * h1[j]
+    h2 = np.maximum(acc + b2, f32(0))
+    z = f32(0)
+    for j in range(32):
+        z = z + w3[j] * h2[j]
+    z = z + b3
+    return float(f32(0.2) + f32(1.3) / (f32(1) + np.exp(-z)))
+
+
+def _bf16_theta(rng, scale=0.4):
+    th = rng.normal(scale=scale, size=orc_nparam()).astype(np.float32).astype(np.float64)
+    th[:256] = _bf16(th[:256])
+    th[288:1312] = _bf16(th[288:1312])
+    return th
+
+
+def _face_pairs(rng, count):
+    """Random faces: independent states, nearly equal states (small jumps,
+    where the features cancel), and wall ghosts."""
+    import oracle
+    out = []
+    for t in range(count):
+        UL = random_state(rng).astype(np.float32).astype(np.float64)
+        n = rng.normal(size=2) * 10.0 ** rng.uniform(-3, 0)
+        kind = t % 3
+        if kind == 0:
+            UR = random_state(rng)
+        elif kind == 1:
+            UR = UL * (1.0 + 10.0 ** rng.uniform(-6, -2) * rng.normal(size=4))
+        else:
+            UR = oracle.ghost(oracle.WALL, UL, n, np.zeros(4))
+        out.append((UL, UR.astype(np.float32).astype(np.float64), n))
+    return out
+
+
+def test_closure_feature_error_bounds_hold_for_an_fp32_evaluation(orc):
+    # the bounds are first-order error propagation; an independent float32
+    # evaluation must stay inside them (they are several times larger)
+    rng = np.random.default_rng(21)
+    worst = 0.0
+    for UL, UR, n in _face_pairs(rng, 3000):
+        f = orc.closure_features(UL, UR, n)
+        e = orc.closure_feature_errors(UL, UR, n)
+        g = _features_fp32(UL, UR, n)
+        assert (e >= 0).all()
+        assert (np.abs(g - f) <= e).all(), (UL, UR, n, g - f, e)
+        worst = max(worst, float((np.abs(g - f) / np.maximum(e, 1e-300)).max()))
+    assert worst > 1e-3  # the test really measures FP32 errors
+
+
+def test_closure_scale_interval_contains_fp32_evaluations(orc):
+    # a float32 evaluation of features and MLP lands inside the interval
+    # (up to its own layer-2/3 rounding); a face whose roundings are all
+    # determined has the oracle's bfloat16 scale as both ends
+    rng = np.random.default_rng(22)
+    th = _bf16_theta(rng)
+    n_undet = 0
+    pairs = _face_pairs(rng, 1500)
+    for UL, UR, n in pairs:
+        f = orc.closure_features(UL, UR, n)
+        e = orc.closure_feature_errors(UL, UR, n)
+        lo, hi, det = orc.closure_scale_interval(th, f, e)
+        s32 = _mlp_fp32(th, _bf16(_features_fp32(UL, UR, n)))
+        assert lo - 2e-6 <= s32 <= hi + 2e-6, (lo, hi, s32)
+        s = orc.closure_scale(th, UL, UR, n, bf16_acts=True)
+        assert lo <= s <= hi
+        if det:
+            assert lo == hi == s
+        else:
+            n_undet += 1
+    assert 0 < n_undet < len(pairs)
+
+
+def test_closure_scale_interval_covers_sampled_roundings(orc):
+    # brute force: features and first-layer sums moved anywhere inside their
+    # windows, then rounded, give scales inside the interval
+    rng = np.random.default_rng(23)
+    th = _bf16_theta(rng)
+    W1, b1 = th[:256].reshape(32, 8), th[256:288]
+    hit = 0
+    for UL, UR, n in _face_pairs(rng, 300):
+        f = orc.closure_features(UL, UR, n)
+        e = orc.closure_feature_errors(UL, UR, n)
+        lo, hi, det = orc.closure_scale_interval(th, f, e)
+        for _ in range(20):
+            x = _bf16(np.maximum(f + e * rng.uniform(-1, 1, 8), 0.0))
+            a = b1 + W1 @ x
+            mag = np.abs(b1) + np.abs(W1) @ x
+            h1 = _bf16(np.maximum(a + 10.0 / 2 ** 23 * mag * rng.uniform(-1, 1, 32), 0.0))
+            a2 = th[1312:1344] + th[288:1312].reshape(32, 32) @ h1
+            z = th[1376] + th[1344:1376] @ np.maximum(a2, 0.0)
+            s = 0.2 + 1.3 / (1.0 + math.exp(-z))
+            assert lo - 1e-12 <= s <= hi + 1e-12
+            hit += (not det) and s != lo
+    assert hit > 0  # some samples really took another rounding

@@ -54,8 +54,11 @@ def test_noalloc_totals_match_allocating_entry_point_twice(prec):
         torch.cuda.synchronize()
         got = out.cpu().numpy()
         assert (np.abs(got - want) <= 1e-14 * scale).all(), (call, got, want)
-        host = numpy_totals(U.cpu().numpy(), area)
-        assert (np.abs(got - host) <= 1e-14 * scale).all(), (call, got, host)
+        Uh = U.cpu().numpy()
+        host = numpy_totals(Uh, area)
+        # any summation order is within n * 2^-53 of the sum of magnitudes
+        bound = Uh.shape[0] * 2.0 ** -53 * np.abs(area[:, None] * Uh).sum(axis=0)
+        assert (np.abs(got - host) <= bound).all(), (call, got, host)
 
 
 def test_noalloc_totals_at_full_capacity():
