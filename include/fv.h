@@ -45,6 +45,9 @@ extern "C" {
                            still in flight did not complete within the drain limit either:
                            they may still write the device memory of the mesh or batch.
                            Destroy the handle (and do not reuse its state buffers). */
+#define FV_EINDEX 7     /* bounds-checked builds only (see fv_index_checks): a kernel met a
+                           neighbour, halo or node index outside the array it indexes, skipped
+                           that access and flagged it; the state is not valid. */
 
 /* ---- precision of a mesh's state and geometry ------------------------------ */
 #define FV_F32 0
@@ -86,6 +89,16 @@ const char* fv_last_error(void);
 
 /* ABI version of this header: 1. */
 int32_t fv_abi_version(void);
+
+/* 1 if this library is the bounds-checked build (compiled with FV_DEBUG),
+ * else 0.  In that build every kernel tests each index it reads through a
+ * table -- global neighbour ids against the cell count, 16-bit tile-local ids
+ * against the entries its tile staged in shared memory, halo ids, node ids --
+ * and on an index outside its array skips the access and sets an error bit
+ * that fv_step and fv_mesh_status report as FV_EINDEX (fv_batch_step for
+ * batches).  It stands in for a memory checker on machines where none can
+ * run; results are bitwise those of the normal build. */
+int32_t fv_index_checks(void);
 
 /* ===========================================================================
  * Mesh (Sec. 6.2.1 geometry; Sec. 7: each cell has three neighbours, ghost
@@ -346,6 +359,17 @@ int fv_partition_local(const fv_mesh* mesh, int32_t nparts, int32_t part, int64_
 /* Creates or refreshes the device arrays now, on `stream` (otherwise the
  * first device call does it).  Allocates device memory. */
 int fv_mesh_upload(fv_mesh* mesh, void* stream);
+
+/* Test support of the bounds-checked build (FV_EINVAL in the normal build):
+ * overwrites one entry of the mesh's device neighbour tables so that a test
+ * can check that the kernels catch an index outside its array.
+ *   table 0: the global neighbour id of face `slot` (0..2) of `cell`;
+ *   table 1: its 16-bit tile-local id (tiles must have been built by a step
+ *            of a tiled shape; value 0..0xFFFF).
+ * Synchronises the stream.  The host mesh is unchanged; fv_renumber or a new
+ * tile size rebuilds the device tables from it. */
+int fv_mesh_debug_set_index(fv_mesh* mesh, int32_t table, int64_t cell, int32_t slot,
+                            int32_t value, void* stream);
 
 /* ===========================================================================
  * Time stepping (Eq. 4 semi-discrete form, Eq. 5 flux, Eq. 6 forward Euler).

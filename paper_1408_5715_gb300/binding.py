@@ -15,7 +15,7 @@ import numpy as np
 
 from . import build as _build
 
-FV_OK, FV_EINVAL, FV_ENOMEM, FV_ECUDA, FV_ENONFINITE, FV_ETIMEOUT, FV_ESTATE = range(7)
+FV_OK, FV_EINVAL, FV_ENOMEM, FV_ECUDA, FV_ENONFINITE, FV_ETIMEOUT, FV_ESTATE, FV_EINDEX = range(8)
 N_VARIANTS = 7  # step-kernel shapes (fv_mesh_set_variant)
 FV_F32, FV_F64 = 0, 1
 FV_BC_NONE, FV_BC_WALL, FV_BC_FARFIELD, FV_BC_EXTRAP = 0, 1, 2, 3
@@ -39,7 +39,9 @@ class FVError(RuntimeError):
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The library this process loads: the bounds-checked build when the
+    environment sets FV_LIBRARY=debug, else the normal one."""
+    return _build.LIB_DEBUG if os.environ.get("FV_LIBRARY") == "debug" else _build.LIB
 
 
 def load():
@@ -48,13 +50,15 @@ def load():
     with _lock:
         if _lib is not None:
             return _lib
-        path = _build.LIB
+        path = library_path()
         if not os.path.exists(path):
             raise RuntimeError(f"CUDA library not built ({path}); run __graft_entry__.build()")
         lib = ctypes.CDLL(path)
         sig = {
             "fv_last_error": (ctypes.c_char_p, []),
             "fv_abi_version": (_i32, []),
+            "fv_index_checks": (_i32, []),
+            "fv_mesh_debug_set_index": (ctypes.c_int, [_vp, _i32, _i64, _i32, _i32, _vp]),
             "fv_mesh_create": (ctypes.c_int, [_vp, _i64, _vp, _i64, _vp, _vp, _i64, _i32, _i32,
                                               _P(_vp)]),
             "fv_mesh_destroy": (ctypes.c_int, [_vp]),

@@ -18,6 +18,9 @@ CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libfvgb300.so")
 BUILD_DIR = os.path.join(PKG, "_build")
+# the bounds-checked build (-DFV_DEBUG): every table-indexed gather is tested
+LIB_DEBUG = os.path.join(OUT_DIR, "libfvgb300_debug.so")
+BUILD_DIR_DEBUG = os.path.join(PKG, "_build_debug")
 
 SOURCES = ["host_mesh.cpp", "renumber.cpp", "partition.cpp", "tiles.cpp", "vertex_geom.cpp",
            "kernels.cu", "tma_step.cu",
@@ -34,9 +37,11 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
-def _flags(src: str):
+def _flags(src: str, debug: bool = False):
     common = ["-O3", "-std=c++17", "-I", os.path.join(ROOT, "include"), "-I", CSRC,
               "-Xcompiler", "-fPIC,-O2,-ffp-contract=off", "--expt-relaxed-constexpr"]
+    if debug:
+        common.append("-DFV_DEBUG")
     if src.endswith(".cu"):
         return common + ARCH + ["-lineinfo", "-Xptxas", "-v"]
     return common + ["-x", "c++"]
@@ -49,19 +54,22 @@ def _deps_mtime() -> float:
     return max(os.path.getmtime(f) for f in files)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compiles and links the library if any source is newer; returns its path."""
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime():
-        return LIB
-    os.makedirs(BUILD_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    """Compiles and links the library if any source is newer; returns its path.
+    debug=True builds the bounds-checked library (LIB_DEBUG) instead."""
+    lib = LIB_DEBUG if debug else LIB
+    build_dir = BUILD_DIR_DEBUG if debug else BUILD_DIR
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _deps_mtime():
+        return lib
+    os.makedirs(build_dir, exist_ok=True)
     os.makedirs(OUT_DIR, exist_ok=True)
     exe = nvcc()
 
     def compile_one(src):
-        obj = os.path.join(BUILD_DIR, os.path.splitext(src)[0] + ".o")
-        cmd = [exe, "-c", os.path.join(CSRC, src), "-o", obj] + _flags(src)
+        obj = os.path.join(build_dir, os.path.splitext(src)[0] + ".o")
+        cmd = [exe, "-c", os.path.join(CSRC, src), "-o", obj] + _flags(src, debug)
         res = subprocess.run(cmd, capture_output=True, text=True)
-        log = os.path.join(BUILD_DIR, src + ".log")
+        log = os.path.join(build_dir, src + ".log")
         with open(log, "w") as f:
             f.write(" ".join(cmd) + "\n" + res.stdout + res.stderr)
         if res.returncode != 0:
@@ -70,18 +78,19 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib + f".{os.getpid()}.tmp"
     cmd = [exe, "-shared", "-o", tmp] + objs + ARCH + ["-Xcompiler", "-fPIC"]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stderr[-4000:]}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     if verbose:
         for src in SOURCES:
-            with open(os.path.join(BUILD_DIR, src + ".log")) as f:
+            with open(os.path.join(build_dir, src + ".log")) as f:
                 sys.stdout.write(f.read())
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
+                debug="--debug" in sys.argv))

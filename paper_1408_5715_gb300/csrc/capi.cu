@@ -516,6 +516,9 @@ void read_status(fv_mesh* m, cudaStream_t s, double* t_adv, bool check) {
   FV_CUDA(cudaMemcpyAsync(&h, m->d_scal, sizeof h, cudaMemcpyDeviceToHost, s));
   FV_CUDA(cudaStreamSynchronize(s));
   if (t_adv) *t_adv = h.t[m->last_t_slot];
+  if (check && (h.err & 8))
+    throw fv::Error{FV_EINDEX, "a neighbour, halo or node index was outside its array "
+                               "(bounds-checked build); the state is not valid"};
   if (check && (h.err & 4))
     throw fv::Error{FV_ESTATE, "a bounded device wait gave up and the copies in flight did not "
                                "drain either; destroy the mesh"};
@@ -536,6 +539,14 @@ extern "C" {
 const char* fv_last_error(void) { return g_last_error.c_str(); }
 
 int32_t fv_abi_version(void) { return 1; }
+
+int32_t fv_index_checks(void) {
+#ifdef FV_DEBUG
+  return 1;
+#else
+  return 0;
+#endif
+}
 
 int fv_mesh_create(const double* xy, int64_t n_nodes, const int32_t* tri, int64_t n_tri,
                    const int32_t* node_canon, const int32_t* bnd_edges, int64_t n_bnd,
@@ -910,6 +921,43 @@ int fv_mesh_upload(fv_mesh* mesh, void* stream) {
   return guarded([&] {
     check_mesh(mesh);
     ensure_device(mesh, as_stream(stream));
+  });
+}
+
+int fv_mesh_debug_set_index(fv_mesh* mesh, int32_t table, int64_t cell, int32_t slot,
+                            int32_t value, void* stream) {
+  return guarded([&] {
+    check_mesh(mesh);
+    if (!fv_index_checks()) invalid("only bounds-checked builds (FV_DEBUG) take this call");
+    if (cell < 0 || cell >= mesh->h.n || slot < 0 || slot > 2) invalid("cell or slot out of range");
+    cudaStream_t s = as_stream(stream);
+    ensure_device(mesh, s);
+    if (table == 0) {
+      // global neighbour ids: FP32 keeps face 0's in the geometry record
+      if (mesh->f64()) {
+        int* p = static_cast<int*>(mesh->d_nbr) + 4 * cell + slot;
+        FV_CUDA(cudaMemcpyAsync(p, &value, sizeof value, cudaMemcpyHostToDevice, s));
+      } else if (slot == 0) {
+        float* p = static_cast<float*>(mesh->d_geom) + 8 * cell + 7;
+        FV_CUDA(cudaMemcpyAsync(p, &value, sizeof value, cudaMemcpyHostToDevice, s));
+      } else {
+        int* p = static_cast<int*>(mesh->d_nbr) + 2 * cell + (slot - 1);
+        FV_CUDA(cudaMemcpyAsync(p, &value, sizeof value, cudaMemcpyHostToDevice, s));
+      }
+    } else if (table == 1) {
+      if (!mesh->tiles_built) invalid("no tiles built: step a tiled shape first");
+      if (value < 0 || value > 0xFFFF) invalid("tile-local ids are 16-bit");
+      uint2 ln{};
+      FV_CUDA(cudaMemcpyAsync(&ln, mesh->d_cell_ln + cell, sizeof ln, cudaMemcpyDeviceToHost, s));
+      FV_CUDA(cudaStreamSynchronize(s));
+      unsigned* w = slot < 2 ? &ln.x : &ln.y;
+      const int sh = slot == 1 ? 16 : 0;
+      *w = (*w & ~(0xFFFFu << sh)) | ((unsigned)value << sh);
+      FV_CUDA(cudaMemcpyAsync(mesh->d_cell_ln + cell, &ln, sizeof ln, cudaMemcpyHostToDevice, s));
+    } else {
+      invalid("table must be 0 (neighbour ids) or 1 (tile-local ids)");
+    }
+    FV_CUDA(cudaStreamSynchronize(s));
   });
 }
 
@@ -1565,6 +1613,9 @@ int fv_batch_step(fv_batch* batch, void* U, int64_t nsteps, double cfl, double t
       FV_CUDA(cudaMemcpyAsync(&err, batch->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
       FV_CUDA(cudaStreamSynchronize(s));
       for (int k = 0; k < M; ++k) t_advanced[k] = t[batch->last_t_slot * M + k];
+      if (err & 8)
+        throw fv::Error{FV_EINDEX, "a neighbour or halo index was outside its array "
+                                   "(bounds-checked build); the state is not valid"};
       if (err & 4)
         throw fv::Error{FV_ESTATE, "a bounded device wait gave up and the copies in flight did "
                                    "not drain either; destroy the batch"};

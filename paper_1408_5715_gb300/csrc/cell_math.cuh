@@ -156,12 +156,34 @@ __device__ __forceinline__ rec_t<R> ghost(int code, const rec_t<R>& U, R nx, R n
   return U;
 }
 
-// Adds the Lax-Friedrichs flux of one face (times its length) to acc.
+// Index checks of the bounds-checked build (compiled with -DFV_DEBUG): every
+// gather through a neighbour table (global cell ids, tile-local 16-bit ids,
+// halo ids, node ids) tests its index against the array it reads; an index
+// outside sets bit 8 of the error word (the host reports FV_EINDEX) and the
+// access is skipped (the cell's own state stands in).  In the normal build
+// the test is compiled out.
+#ifdef FV_DEBUG
+constexpr bool kIndexChecks = true;
+#else
+constexpr bool kIndexChecks = false;
+#endif
+constexpr int kErrIndex = 8;
+
+__device__ __forceinline__ bool index_ok(int64_t i, int64_t n, int* err) {
+  if (!kIndexChecks) return true;
+  if (i >= 0 && i < n) return true;
+  atomicOr(err, kErrIndex);
+  return false;
+}
+
+// The state across face nb of a cell: the neighbour's (global id nb of n
+// cells) or a ghost state.
 template <typename R>
 __device__ __forceinline__ rec_t<R> neighbour_state(const rec_t<R>& UL, int nb, R nx, R ny,
                                                     const rec_t<R>* __restrict__ Ucur,
-                                                    const R* uinf) {
-  return nb >= 0 ? Rec<R>::ld(Ucur + nb) : ghost<R>(nb, UL, nx, ny, uinf);
+                                                    const R* uinf, int64_t n, int* err) {
+  if (nb >= 0) return index_ok(nb, n, err) ? Rec<R>::ld(Ucur + nb) : UL;
+  return ghost<R>(nb, UL, nx, ny, uinf);
 }
 
 // Adds TWICE the flux of one face (times its length) to acc, given both
@@ -199,8 +221,8 @@ __device__ __forceinline__ void face_flux_acc(const rec_t<R>& UL, const Prim<R>&
 template <typename R, int WAVE = kWaveAverage>
 __device__ __forceinline__ R add_face_flux(const rec_t<R>& UL, const Prim<R>& L, int nb, R nx,
                                            R ny, const rec_t<R>* __restrict__ Ucur,
-                                           const R* uinf, R acc[4]) {
-  const rec_t<R> UR = neighbour_state<R>(UL, nb, nx, ny, Ucur, uinf);
+                                           const R* uinf, R acc[4], int64_t n, int* err) {
+  const rec_t<R> UR = neighbour_state<R>(UL, nb, nx, ny, Ucur, uinf, n, err);
   const Prim<R> W = primitive<R>(UR);
   const R len = face_len<R>(nx, ny);
   face_flux_acc<R, false, WAVE>(UL, L, UR, W, nx, ny, len, R(1), acc);

@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(kClThreads) k_step_closure(StepArgs a, Closure
       nb[0] = c.n0, nb[1] = c.n1, nb[2] = c.n2;
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        UR[k] = neighbour_state<float>(c.U, nb[k], nx[k], ny[k], U, a.uinf_f);
+        UR[k] = neighbour_state<float>(c.U, nb[k], nx[k], ny[k], U, a.uinf_f, a.n, a.err);
         W[k] = primitive<float>(UR[k]);
         len[k] = face_len<float>(nx[k], ny[k]);
         if (!(nb[k] >= base && nb[k] < i)) own |= 1u << k;
@@ -380,7 +380,7 @@ __global__ void __launch_bounds__(kClThreads) k_closure_scales(StepArgs a, Closu
       const int nb[3] = {c.n0, c.n1, c.n2};
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        const float4 UR = neighbour_state<float>(c.U, nb[k], nx[k], ny[k], U, a.uinf_f);
+        const float4 UR = neighbour_state<float>(c.U, nb[k], nx[k], ny[k], U, a.uinf_f, a.n, a.err);
         const Prim<float> W = primitive<float>(UR);
         float f[8];
         face_features(c.U, L, UR, W, nx[k], ny[k], face_len<float>(nx[k], ny[k]), f);
@@ -505,7 +505,7 @@ __global__ void __launch_bounds__(kGrThreads) k_closure_grad(StepArgs a, const f
       const int nb[3] = {c.n0, c.n1, c.n2};
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        UR[k] = neighbour_state<float>(c.U, nb[k], nx[k], ny[k], U, a.uinf_f);
+        UR[k] = neighbour_state<float>(c.U, nb[k], nx[k], ny[k], U, a.uinf_f, a.n, a.err);
         W[k] = primitive<float>(UR[k]);
         len[k] = face_len<float>(nx[k], ny[k]);
         float f[8];

@@ -39,9 +39,9 @@ __device__ __forceinline__ void update_cell(const StepArgs& a, const rec_t<R>* _
   const rec_t<R>& UL = c.U;
   const Prim<R> L = primitive<R>(UL);
   R acc[4] = {R(0), R(0), R(0), R(0)};
-  R perim = add_face_flux<R, WAVE>(UL, L, c.n0, c.g0.x, c.g0.y, U, uinf, acc);
-  perim = add(perim, add_face_flux<R, WAVE>(UL, L, c.n1, c.g0.z, c.g0.w, U, uinf, acc));
-  perim = add(perim, add_face_flux<R, WAVE>(UL, L, c.n2, c.g1.x, c.g1.y, U, uinf, acc));
+  R perim = add_face_flux<R, WAVE>(UL, L, c.n0, c.g0.x, c.g0.y, U, uinf, acc, a.n, a.err);
+  perim = add(perim, add_face_flux<R, WAVE>(UL, L, c.n1, c.g0.z, c.g0.w, U, uinf, acc, a.n, a.err));
+  perim = add(perim, add_face_flux<R, WAVE>(UL, L, c.n2, c.g1.x, c.g1.y, U, uinf, acc, a.n, a.err));
   finish_cell<R, MODE, COMP>(a, out, i, c, acc, perim, dt, bmin, ok);
 }
 

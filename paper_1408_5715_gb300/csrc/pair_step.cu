@@ -48,12 +48,20 @@ namespace {
 
 __device__ __forceinline__ float4 prim4(const Prim<float>& w) { return prim_rec<float>(w); }
 
-// Residual sum of one cell from shared-memory neighbours (tile_math.cuh).
+// Residual sum of one cell from shared-memory neighbours (tile_math.cuh):
+// entries [0, cap) of sU and sP.
 __device__ __forceinline__ float cell_fluxes(const float4& g0, const float4& g1, uint2 ln,
                                              const float4& UL, const Prim<float>& L,
                                              const float4* sU, const float4* sP,
-                                             const float* uinf, float acc[4]) {
-  return cell_fluxes<float>(g0, g1, ln, UL, L, sU, sP, uinf, acc);
+                                             const float* uinf, float acc[4], int cap, int* err) {
+  return cell_fluxes<float>(g0, g1, ln, UL, L, sU, sP, uinf, acc, cap, err);
+}
+
+// Global id of halo entry j (checked in the bounds-checked build; a bad id
+// reads cell 0 instead).
+__device__ __forceinline__ int halo_cell(const PairArgs& a, int j) {
+  const int g = __ldg(a.halo_id + j);
+  return index_ok(g, a.n, a.err) ? g : 0;
 }
 
 // Forward-Euler update of one cell, plain or compensated (the arithmetic of
@@ -113,12 +121,13 @@ template <bool COMP>
 __device__ __forceinline__ uint2 step1_cell(const float4& g0, const float4& g1, uint2 ln,
                                             uint2 lo0, int e, const float4* sU0,
                                             const float4* sP0, float4* sU1, float4* sP1,
-                                            const float* uinf, float dt, bool check, bool& ok) {
+                                            const float* uinf, float dt, bool check, bool& ok,
+                                            int cap, int* err) {
   const float4 UL = sU0[e];
   const float4 p = sP0[e];
   const Prim<float> L{p.x, p.y, p.z, p.w};
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
-  const float perim = cell_fluxes(g0, g1, ln, UL, L, sU0, sP0, uinf, acc);
+  const float perim = cell_fluxes(g0, g1, ln, UL, L, sU0, sP0, uinf, acc, cap, err);
   uint2 lo1 = make_uint2(0u, 0u);
   const float4 U1 = fe_update<COMP>(UL, g1.z, acc, dt, lo0, lo1);
   const Prim<float> w = primitive<float>(U1);
@@ -138,12 +147,13 @@ template <bool COMP>
 __device__ __forceinline__ float4 step2_cell(const float4& g0, const float4& g1, uint2 ln,
                                              uint2 lo1, int e, const float4* sU1,
                                              const float4* sP1, const float* uinf, float dt,
-                                             uint2& lo2, float& bmin, bool& ok) {
+                                             uint2& lo2, float& bmin, bool& ok, int cap,
+                                             int* err) {
   const float4 UL = sU1[e];
   const float4 p = sP1[e];
   const Prim<float> L{p.x, p.y, p.z, p.w};
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
-  const float perim = cell_fluxes(g0, g1, ln, UL, L, sU1, sP1, uinf, acc);
+  const float perim = cell_fluxes(g0, g1, ln, UL, L, sU1, sP1, uinf, acc, cap, err);
   const float4 U2 = fe_update<COMP>(UL, g1.z, acc, dt, lo1, lo2);
   bool c_ok;
   bmin = fmin(bmin, cell_bound<float>(U2, inradius<float>(g1, perim), c_ok));
@@ -153,18 +163,20 @@ __device__ __forceinline__ float4 step2_cell(const float4& g0, const float4& g1,
 
 // Step 1 of the first-halo cells of a tile (global gathers); their states are
 // checked by the tiles that own them.
+// ne: the entries staged in sU0 and sP0 (tile and both halos).
 template <int THREADS, bool COMP>
-__device__ __forceinline__ void step1_halo(const PairArgs& a, int nt, int hs, int h1,
+__device__ __forceinline__ void step1_halo(const PairArgs& a, int nt, int hs, int h1, int ne,
                                            const float4* sU0, const float4* sP0, float4* sU1,
                                            float4* sP1, float dt) {
   for (int e = nt + threadIdx.x; e < nt + h1; e += THREADS) {
     const int j = hs + (e - nt);
-    const int g = __ldg(a.halo_id + j);
+    const int g = halo_cell(a, j);
     const float4 g0 = __ldg(a.geom + 2 * g), g1 = __ldg(a.geom + 2 * g + 1);
     const uint2 ln = __ldg(a.halo_ln + j);
     const uint2 lo0 = COMP ? __ldg(a.lo_in + g) : make_uint2(0u, 0u);
     bool unused = true;
-    step1_cell<COMP>(g0, g1, ln, lo0, e, sU0, sP0, sU1, sP1, a.uinf, dt, false, unused);
+    step1_cell<COMP>(g0, g1, ln, lo0, e, sU0, sP0, sU1, sP1, a.uinf, dt, false, unused, ne,
+                     a.err);
   }
 }
 
@@ -201,7 +213,7 @@ __global__ void __launch_bounds__(THREADS) k_step_pair(PairArgs a) {
 
   // states at the start of the pair, with their primitives
   for (int e = threadIdx.x; e < nt + h12; e += THREADS) {
-    const int g = e < nt ? t0 + e : __ldg(a.halo_id + hs + (e - nt));
+    const int g = e < nt ? t0 + e : halo_cell(a, hs + (e - nt));
     const float4 u = __ldg(a.U + g);
     sU0[e] = u;
     sP0[e] = prim4(primitive<float>(u));
@@ -221,10 +233,10 @@ __global__ void __launch_bounds__(THREADS) k_step_pair(PairArgs a) {
       const uint2 lo0 = COMP ? __ldg(a.lo_in + g) : make_uint2(0u, 0u);
       lo1[k] = step1_cell<COMP>(__ldg(a.geom + 2 * g), __ldg(a.geom + 2 * g + 1),
                                 __ldg(a.cell_ln + g), lo0, e, sU0, sP0, sU1, sP1, a.uinf, dt1f,
-                                true, ok);
+                                true, ok, nt + h12, a.err);
     }
   }
-  step1_halo<THREADS, COMP>(a, nt, hs, h1, sU0, sP0, sU1, sP1, dt1f);
+  step1_halo<THREADS, COMP>(a, nt, hs, h1, nt + h12, sU0, sP0, sU1, sP1, dt1f);
   __syncthreads();
 
   // step 2: the tile, from U^{n+1}
@@ -237,7 +249,7 @@ __global__ void __launch_bounds__(THREADS) k_step_pair(PairArgs a) {
       uint2 lo2;
       const float4 U2 = step2_cell<COMP>(__ldg(a.geom + 2 * g), __ldg(a.geom + 2 * g + 1),
                                          __ldg(a.cell_ln + g), lo1[k], e, sU1, sP1, a.uinf, dt2f,
-                                         lo2, bmin, ok);
+                                         lo2, bmin, ok, nt + h1, a.err);
       a.out[g] = U2;
       if (COMP) a.lo_out[g] = lo2;
     }
@@ -324,7 +336,7 @@ __global__ void __launch_bounds__(THREADS) k_step_pair_tma(PairArgs a) {
     const int h1 = __ldg(a.tile_info + 2 * b + 1);
     const int h12 = __ldg(a.tile_info + 2 * b + 2) - hs;
     for (int e = tid; e < nt + h12; e += THREADS) {
-      const float4 u = e < nt ? st.U[e] : __ldg(a.U + __ldg(a.halo_id + hs + (e - nt)));
+      const float4 u = e < nt ? st.U[e] : __ldg(a.U + halo_cell(a, hs + (e - nt)));
       sU0[e] = u;
       sP0[e] = prim4(primitive<float>(u));
     }
@@ -337,9 +349,9 @@ __global__ void __launch_bounds__(THREADS) k_step_pair_tma(PairArgs a) {
       if (e < nt)
         lo1[q] = step1_cell<COMP>(st.geom[2 * e], st.geom[2 * e + 1], st.ln[e],
                                   COMP ? st.lo[e] : make_uint2(0u, 0u), e, sU0, sP0, sU1, sP1,
-                                  a.uinf, dt1f, true, ok);
+                                  a.uinf, dt1f, true, ok, nt + h12, a.err);
     }
-    step1_halo<THREADS, COMP>(a, nt, hs, h1, sU0, sP0, sU1, sP1, dt1f);
+    step1_halo<THREADS, COMP>(a, nt, hs, h1, nt + h12, sU0, sP0, sU1, sP1, dt1f);
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < KMAX; ++q) {
@@ -347,7 +359,8 @@ __global__ void __launch_bounds__(THREADS) k_step_pair_tma(PairArgs a) {
       if (e < nt) {
         uint2 lo2;
         const float4 U2 = step2_cell<COMP>(st.geom[2 * e], st.geom[2 * e + 1], st.ln[e], lo1[q],
-                                           e, sU1, sP1, a.uinf, dt2f, lo2, bmin, ok);
+                                           e, sU1, sP1, a.uinf, dt2f, lo2, bmin, ok, nt + h1,
+                                           a.err);
         a.out[t0 + e] = U2;
         if (COMP) a.lo_out[t0 + e] = lo2;
       }

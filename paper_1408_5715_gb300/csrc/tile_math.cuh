@@ -24,16 +24,22 @@ __device__ __forceinline__ Prim<R> rec_prim(const rec_t<R>& p) {
   return Prim<R>{p.x, p.y, p.z, p.w};
 }
 
-// One face of a cell whose neighbour state and primitives are in shared memory.
+// One face of a cell whose neighbour state and primitives are in shared
+// memory (entries [0, cap) of sU and sP).
 template <typename R, int WAVE = kWaveAverage>
 __device__ __forceinline__ R smem_face(const rec_t<R>& UL, const Prim<R>& L, unsigned v, R nx, R ny,
                                        const rec_t<R>* sU, const rec_t<R>* sP, const R* uinf,
-                                       R acc[4]) {
+                                       R acc[4], int cap, int* err) {
   rec_t<R> UR;
   Prim<R> W;
   if (v < kGhostCodes) {
-    UR = sU[v];
-    W = rec_prim<R>(sP[v]);
+    if (index_ok(v, cap, err)) {
+      UR = sU[v];
+      W = rec_prim<R>(sP[v]);
+    } else {
+      UR = UL;
+      W = L;
+    }
   } else {
     UR = ghost<R>((int)v - 0x10000, UL, nx, ny, uinf);
     W = primitive<R>(UR);
@@ -43,15 +49,20 @@ __device__ __forceinline__ R smem_face(const rec_t<R>& UL, const Prim<R>& L, uns
   return len;
 }
 
-// Residual sum of one cell (faces in the order 0, 1, 2) and its perimeter.
+// Residual sum of one cell (faces in the order 0, 1, 2) and its perimeter;
+// the tile-local ids of ln index entries [0, cap) of sU and sP.
 template <typename R, int WAVE = kWaveAverage>
 __device__ __forceinline__ R cell_fluxes(const rec_t<R>& g0, const rec_t<R>& g1, uint2 ln,
                                          const rec_t<R>& UL, const Prim<R>& L, const rec_t<R>* sU,
-                                         const rec_t<R>* sP, const R* uinf, R acc[4]) {
-  R perim = smem_face<R, WAVE>(UL, L, ln.x & 0xffffu, g0.x, g0.y, sU, sP, uinf, acc);
-  perim = add(perim, smem_face<R, WAVE>(UL, L, ln.x >> 16, g0.z, g0.w, sU, sP, uinf, acc));
+                                         const rec_t<R>* sP, const R* uinf, R acc[4], int cap,
+                                         int* err) {
+  R perim =
+      smem_face<R, WAVE>(UL, L, ln.x & 0xffffu, g0.x, g0.y, sU, sP, uinf, acc, cap, err);
+  perim = add(perim,
+              smem_face<R, WAVE>(UL, L, ln.x >> 16, g0.z, g0.w, sU, sP, uinf, acc, cap, err));
   // the high half of ln.y holds a node id in the vertex-geometry layout
-  perim = add(perim, smem_face<R, WAVE>(UL, L, ln.y & 0xffffu, g1.x, g1.y, sU, sP, uinf, acc));
+  perim = add(perim, smem_face<R, WAVE>(UL, L, ln.y & 0xffffu, g1.x, g1.y, sU, sP, uinf, acc,
+                                        cap, err));
   return perim;
 }
 

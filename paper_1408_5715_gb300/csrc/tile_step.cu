@@ -28,10 +28,20 @@ namespace {
 // variables.  With PA > 0 each thread issues the loads of its first PA
 // entries before it uses any, so it waits for about one memory round trip
 // (two for halo cells, whose ids come first) rather than one per entry.
+// The halo ids are global cell ids of the n cells (checked in the
+// bounds-checked build; a bad id stages the tile's first cell).
+template <typename R>
+__device__ __forceinline__ int64_t staged_id(int64_t t0, int nt, int e, const int* halo,
+                                             int64_t n, int* err) {
+  if (e < nt) return t0 + e;
+  const int64_t g = __ldg(halo + (e - nt));
+  return index_ok(g, n, err) ? g : t0;
+}
+
 template <typename R, int THREADS, int PA>
 __device__ __forceinline__ void stage_states(const rec_t<R>* __restrict__ U, int64_t t0, int nt,
                                              int h1, const int* __restrict__ halo, rec_t<R>* sU,
-                                             rec_t<R>* sP) {
+                                             rec_t<R>* sP, int64_t n, int* err) {
   const int ne = nt + h1;
   int e0 = threadIdx.x;
   if constexpr (PA > 0) {
@@ -39,7 +49,7 @@ __device__ __forceinline__ void stage_states(const rec_t<R>* __restrict__ U, int
 #pragma unroll
     for (int k = 0; k < PA; ++k) {
       const int e = threadIdx.x + k * THREADS;
-      if (e < ne) u[k] = Rec<R>::ld(U + (e < nt ? t0 + e : (int64_t)__ldg(halo + (e - nt))));
+      if (e < ne) u[k] = Rec<R>::ld(U + staged_id<R>(t0, nt, e, halo, n, err));
     }
 #pragma unroll
     for (int k = 0; k < PA; ++k) {
@@ -52,7 +62,7 @@ __device__ __forceinline__ void stage_states(const rec_t<R>* __restrict__ U, int
     e0 += PA * THREADS;
   }
   for (int e = e0; e < ne; e += THREADS) {
-    const rec_t<R> u = Rec<R>::ld(U + (e < nt ? t0 + e : (int64_t)__ldg(halo + (e - nt))));
+    const rec_t<R> u = Rec<R>::ld(U + staged_id<R>(t0, nt, e, halo, n, err));
     sU[e] = u;
     sP[e] = prim_rec<R>(primitive<R>(u));
   }
@@ -100,7 +110,8 @@ __global__ void __launch_bounds__(THREADS, sizeof(R) == 4 ? 1280 / THREADS : 1)
       if (e < nv) qv[k] = __ldg(a.tile_vq + vb + e);
     }
   }
-  stage_states<R, THREADS, kStageBatch<R, KMAX>>(U, t0, nt, h1, a.halo_id + hs, sU, sP);
+  stage_states<R, THREADS, kStageBatch<R, KMAX>>(U, t0, nt, h1, a.halo_id + hs, sU, sP, a.n,
+                                                 a.err);
   if constexpr (VTX) {
 #pragma unroll
     for (int k = 0; k < VA; ++k) {
@@ -123,7 +134,9 @@ __global__ void __launch_bounds__(THREADS, sizeof(R) == 4 ? 1280 / THREADS : 1)
       const uint2 ln = __ldg(a.cell_ln + i);
       if constexpr (VTX) {
         const unsigned vl = __ldg(a.cell_vl + i);
-        vertex_geometry(sQ[ln.y >> 16], sQ[vl & 0xffffu], sQ[vl >> 16], a.vscale,
+        // node ids index the nv staged nodes (checked in the bounds-checked build)
+        auto node = [&](unsigned q) { return index_ok(q, nv, a.err) ? sQ[q] : make_int2(0, 0); };
+        vertex_geometry(node(ln.y >> 16), node(vl & 0xffffu), node(vl >> 16), a.vscale,
                         __ldg(a.inv_vol + i), c.g0, c.g1);
       } else {
         c.g0 = Rec<R>::ld(geom + 2 * i);
@@ -135,7 +148,7 @@ __global__ void __launch_bounds__(THREADS, sizeof(R) == 4 ? 1280 / THREADS : 1)
       if (COMP && MODE == kModeRK2b) c.lo_stage = a.lo_stage[i];
       R acc[4] = {R(0), R(0), R(0), R(0)};
       const R perim = cell_fluxes<R, WAVE>(c.g0, c.g1, ln, c.U, rec_prim<R>(sP[e]), sU, sP,
-                                           far_field<R>(a), acc);
+                                           far_field<R>(a), acc, nt + h1, a.err);
       finish_cell<R, MODE, COMP>(a, out, i, c, acc, perim, dtR, bmin, ok);
     }
   }
@@ -184,7 +197,8 @@ __global__ void __launch_bounds__(THREADS) k_step_tile_batch(BatchArgs b) {
     s_t = t;
     s_dt = dt;
   }
-  stage_states<R, THREADS, kStageBatch<R, KMAX>>(U, t0, nt, h1, a.halo_id + hs, sU, sP);
+  stage_states<R, THREADS, kStageBatch<R, KMAX>>(U, t0, nt, h1, a.halo_id + hs, sU, sP, a.n,
+                                                 a.err);
   __syncthreads();
   const double t = MODE != kModeResidual ? s_t : 0.0, dt = MODE != kModeResidual ? s_dt : 0.0;
   const R dtR = R(dt);
@@ -205,7 +219,8 @@ __global__ void __launch_bounds__(THREADS) k_step_tile_batch(BatchArgs b) {
       if (COMP && MODE == kModeRK2b) c.lo_stage = a.lo_stage[i];
       const uint2 ln = __ldg(a.cell_ln + i);
       R acc[4] = {R(0), R(0), R(0), R(0)};
-      const R perim = cell_fluxes<R>(c.g0, c.g1, ln, c.U, rec_prim<R>(sP[e]), sU, sP, uinf, acc);
+      const R perim =
+          cell_fluxes<R>(c.g0, c.g1, ln, c.U, rec_prim<R>(sP[e]), sU, sP, uinf, acc, nt + h1, a.err);
       finish_cell<R, MODE, COMP>(a, out, i, c, acc, perim, dtR, bmin, ok);
     }
   }

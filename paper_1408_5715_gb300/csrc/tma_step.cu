@@ -179,7 +179,8 @@ __global__ void __launch_bounds__(kBlock) k_step_tma(BatchArgs b) {
         if (nb[q] >= 0) {
           const int64_t local = (int64_t)nb[q] - t0;
           UR = (local >= 0 && local < kTile && (int64_t)nb[q] < end) ? st.U[local]
-                                                                      : Rec<R>::ld(U + nb[q]);
+               : index_ok(nb[q], a.n, a.err)                         ? Rec<R>::ld(U + nb[q])
+                                                                      : c.U;
         } else {
           UR = ghost<R>(nb[q], c.U, nx[q], ny[q], uinf);
         }

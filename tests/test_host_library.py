@@ -34,6 +34,16 @@ def test_library_exports_every_declared_symbol():
     assert lib.fv_abi_version() == 1
 
 
+def test_normal_build_refuses_the_debug_index_entry():
+    # the test hook of the bounds-checked build answers FV_EINVAL in the
+    # normal build, before any device work
+    lib = B.load()
+    assert lib.fv_index_checks() == 0
+    m = B.Mesh.from_input(W.periodic_square(6, 4, seed=1), "f32")
+    rc = lib.fv_mesh_debug_set_index(m._h, 0, 0, 0, 12345, None)
+    assert rc == B.FV_EINVAL and "bounds-checked" in lib.fv_last_error().decode()
+
+
 def test_oracle_is_not_linked_into_the_library():
     # the product library must not depend on the test oracle
     import subprocess
