@@ -64,7 +64,8 @@ def parse_args():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="square_16m",
-                   choices=["channel_bump_1m", "square_16m", "batch_256", "vortex_square_small"])
+                   choices=["channel_bump_1m", "square_16m", "square_4m", "batch_256",
+                            "vortex_square_small"])
     p.add_argument("--precision", default="f32", choices=["f32", "f64"])
     p.add_argument("--scheme", default="fe", choices=["fe", "rk2"])
     p.add_argument("--update", default=None, choices=["plain", "compensated"],
@@ -97,6 +98,10 @@ WORKLOADS = {
     "square_16m": dict(make=W.vortex_square_16m, init="vortex", mach=0.5, time_steps=1000,
                        order="hilbert", update="plain", desc="periodic unit square, 4096x2048 quads, jitter 20%, "
                        "isentropic vortex beta=5 M=0.5"),
+    "square_4m": dict(make=lambda: W.periodic_square(2048, 1024, 4), init="vortex", mach=0.5,
+                      time_steps=1000, order="hilbert", update="plain",
+                      desc="periodic unit square, 2048x1024 quads, jitter 20%, isentropic "
+                           "vortex beta=5 M=0.5 (a quarter of the 16.8M square, for profiles)"),
     "batch_256": dict(make=W.vortex_batch, batch=True, time_steps=1000, order="hilbert",
                       update="plain",
                       desc="256 periodic jittered squares, 4,900-200,704 triangles each "
@@ -813,7 +818,11 @@ def batched_leg(B, time_steps=1000):
     U = torch.empty_like(flat0)
     cells = int(sum(batch.sizes))
     peak, _ = measured_peaks()
-    sample = (int(np.argmin(batch.sizes)), int(np.argmax(batch.sizes)))
+    # error samples: the smallest and the largest mesh that start from a
+    # vortex (a uniform stream stays uniform and tests nothing)
+    vortex = [k for k, (_, _, U0) in enumerate(items) if np.ptp(U0[:, 0]) > 0]
+    sizes = np.asarray(batch.sizes)
+    sample = (min(vortex, key=lambda k: sizes[k]), max(vortex, key=lambda k: sizes[k]))
     ref64 = {}
     for k in sample:
         mi, prim, U0 = items[k]

@@ -461,6 +461,23 @@ int fv_closure_loss_grad(fv_mesh* mesh, const void* U0, const void* Ut, double d
                          const double* weights, fv_closure* closure, double* loss, float* grad,
                          void* stream);
 
+/* Restriction of a fine state to a coarse mesh (training data of the
+ * closure): coarse cell c gets the area-weighted mean of its `children` fine
+ * cells, sum_j V_j U_j / sum_j V_j over j = fine_of[c*children + 0 ..
+ * children-1], accumulated in FP64 in that order.
+ *   U_fine    device, fine states in fine_precision (FV_F32 / FV_F64).
+ *   area_fine device double [fine cells]: the fine cells' areas.
+ *   fine_of   device int32 [n_coarse * children]: fine cell ids (in the
+ *             numbering of U_fine) of each coarse cell (in the numbering of
+ *             U_coarse), e.g. the 16 children of two midpoint refinements.
+ *   U_coarse  device, [4*n_coarse] in coarse_precision, written.
+ * Ids are not checked on the device: every id must index U_fine and
+ * area_fine.  FV_EINVAL for an unknown precision, children < 1 or a null
+ * pointer.  Nothing is synchronised. */
+int fv_restrict_mean(const void* U_fine, int32_t fine_precision, const double* area_fine,
+                     const int32_t* fine_of, int64_t n_coarse, int32_t children, void* U_coarse,
+                     int32_t coarse_precision, void* stream);
+
 /* One Adam update (Kingma and Ba) of n device FP32 parameters with moments m,
  * v (device, caller-owned, start at zero); step counts from 1. */
 int fv_adam_step(float* theta, const float* grad, float* m, float* v, int64_t n, double lr,

@@ -96,6 +96,8 @@ def load():
             "fv_closure_scales": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
             "fv_closure_loss_grad": (ctypes.c_int, [_vp, _vp, _vp, _dbl, _vp, _vp, _P(_dbl),
                                                     _vp, _vp]),
+            "fv_restrict_mean": (ctypes.c_int, [_vp, _i32, _vp, _vp, _i64, _i32, _vp, _i32,
+                                                _vp]),
             "fv_adam_step": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, _dbl, _dbl, _dbl, _dbl,
                                             _i64, _vp]),
             "fv_batch_create": (ctypes.c_int, [_vp, _i32, _P(_vp)]),
@@ -519,6 +521,30 @@ class Batch:
         _check(load().fv_batch_totals(self._h, _dev_ptr(U, self.torch_dtype, self.n_padded, "U"),
                                       _np_ptr(out), _stream_ptr(stream)))
         return out
+
+
+def restrict_mean(U_fine, area_fine, fine_of, U_coarse, stream=None):
+    """fv_restrict_mean: coarse cell c of the CUDA tensor U_coarse ((n_c, 4),
+    float32/float64) gets the area-weighted mean of the fine states
+    U_fine[fine_of[c, :]] (CUDA int32 (n_c, children); areas: CUDA float64)."""
+    import torch
+    for t, what in ((U_fine, "U_fine"), (U_coarse, "U_coarse")):
+        if t.dtype not in (torch.float32, torch.float64) or not t.is_cuda \
+                or not t.is_contiguous() or t.dim() != 2 or t.shape[1] != 4:
+            raise TypeError(f"{what} must be a contiguous CUDA (n, 4) float32/float64 tensor")
+    if fine_of.dtype != torch.int32 or not fine_of.is_cuda or not fine_of.is_contiguous() \
+            or fine_of.dim() != 2 or fine_of.shape[0] != U_coarse.shape[0]:
+        raise TypeError("fine_of must be a contiguous CUDA int32 (n_coarse, children) tensor")
+    if area_fine.dtype != torch.float64 or not area_fine.is_cuda \
+            or area_fine.numel() != U_fine.shape[0]:
+        raise TypeError("area_fine must be a CUDA float64 tensor of one area per fine cell")
+    prec = {torch.float32: FV_F32, torch.float64: FV_F64}
+    _check(load().fv_restrict_mean(_vp(U_fine.data_ptr()), prec[U_fine.dtype],
+                                   _vp(area_fine.data_ptr()), _vp(fine_of.data_ptr()),
+                                   int(U_coarse.shape[0]), int(fine_of.shape[1]),
+                                   _vp(U_coarse.data_ptr()), prec[U_coarse.dtype],
+                                   _stream_ptr(stream)))
+    return U_coarse
 
 
 def conserved_totals_noalloc(U, area, out, stream=None):

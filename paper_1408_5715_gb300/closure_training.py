@@ -78,24 +78,23 @@ class Problem:
                          device="cuda")
         self.fine_shape, _ = self.mf.autotune(U)
         del U
-        _, _, area_c = self.mc.export()
+        _, _, self.area_c = self.mc.export()  # coarse areas, coarse numbering
         _, _, area_f = self.mf.export()
-        dev = "cuda"
-        self.perm_f_t = torch.as_tensor(self.perm_f, dtype=torch.long, device=dev)
-        self.perm_c_t = torch.as_tensor(self.perm_c, dtype=torch.long, device=dev)
-        vf = np.empty_like(area_f)
-        vf[self.perm_f] = area_f  # areas in the refinement (original) order
-        self.vf = torch.tensor(vf, dtype=torch.float64, device=dev).view(-1, self.kids, 1)
-        self.vc = self.vf.sum(dim=1)  # coarse areas, original order
         self.n_c, self.n_f = self.mc.n, self.mf.n
+        # the children of coarse cell i (coarse numbering) are fine cells
+        # perm_c[i] * kids + j of the refinement order; in the fine numbering
+        inv_f = np.empty(self.n_f, np.int64)
+        inv_f[self.perm_f] = np.arange(self.n_f)
+        kids_of = inv_f[self.perm_c[:, None] * self.kids + np.arange(self.kids)[None, :]]
+        self.fine_of = torch.tensor(kids_of.astype(np.int32), device="cuda")
+        self.area_f = torch.tensor(area_f, dtype=torch.float64, device="cuda")
 
     def restrict(self, Uf):
-        """Fine FP64 state (fine numbering) -> coarse FP32 state (coarse numbering)."""
+        """Fine FP64 state (fine numbering) -> coarse FP32 state (coarse
+        numbering): area-weighted means of the children (fv_restrict_mean)."""
         import torch
-        orig = torch.empty_like(Uf)
-        orig[self.perm_f_t] = Uf
-        Uc = (orig.view(-1, self.kids, 4) * self.vf).sum(dim=1) / self.vc
-        return Uc[self.perm_c_t].to(torch.float32).contiguous()
+        Uc = torch.empty((self.n_c, 4), dtype=torch.float32, device="cuda")
+        return B.restrict_mean(Uf, self.area_f, self.fine_of, Uc)
 
     def set_mach(self, mach):
         prim = W.freestream(mach)
@@ -148,11 +147,11 @@ def fine_pairs(prob: Problem, mach, dt_c, horizon, n_pairs):
 
 
 def rel_l2_rho(prob: Problem, Uc, ref):
-    import torch
-    v = prob.vc[prob.perm_c_t].view(-1).to(torch.float64)
-    a = Uc[:, 0].double()
-    b = ref[:, 0].double()
-    return float(torch.sqrt((v * (a - b) ** 2).sum() / (v * b * b).sum()))
+    """Area-weighted relative L2 error of the density, on the host."""
+    v = prob.area_c
+    a = Uc[:, 0].double().cpu().numpy()
+    b = ref[:, 0].double().cpu().numpy()
+    return float(np.sqrt((v * (a - b) ** 2).sum() / (v * b * b).sum()))
 
 
 def coarse_run(prob: Problem, mach, dt_c, horizon, closure=None):

@@ -138,6 +138,11 @@ struct fv_mesh {
   int2* d_tile_vq = nullptr;
   float* d_inv_vol = nullptr;  // FP32 1/V per cell
   int p_v_cap = 0;
+  // learned closure: each face once (owner cell and face, cell across and
+  // its face, or a ghost code) and the scale of every cell face
+  int2* d_faces = nullptr;
+  int64_t n_faces = 0;
+  float* d_scale = nullptr;
   unsigned wait_limit = fv::kDefaultWaitLimit;  // bounded device waits (variant 5)
   fv::LoopScalars* d_scal = nullptr;
   double* d_partials = nullptr;
@@ -190,9 +195,16 @@ struct fv_mesh {
 
   bool vertex_tiles() const { return geometry == FV_GEOM_VERTEX; }
 
+  void free_faces() {
+    dev_free(d_faces);
+    dev_free(d_scale);
+    n_faces = 0;
+  }
+
   void free_device() {
     drop_graph();
     free_tiles();
+    free_faces();
     dev_free(d_nbr);
     dev_free(d_geom);
     dev_free(d_vol);
@@ -316,6 +328,7 @@ void ensure_device(fv_mesh* m, cudaStream_t s) {
     return;
   }
   m->free_tiles();
+  m->free_faces();
   const int64_t n = m->h.n;
   if (m->dev_n != n) {
     m->free_device();
@@ -352,6 +365,46 @@ void ensure_device(fv_mesh* m, cudaStream_t s) {
   ensure_tiles(m, s);
 }
 
+// The faces of the mesh, each once, for the learned closure's scale pass:
+// (4 a + ka, 4 b + kb) for the face ka of cell a whose other side is face kb
+// of cell b (a <= b; a cell may border itself across a periodic seam), and
+// (4 a + ka, ghost code) for a boundary face.  The two sides of a face are
+// matched by neighbour id and exactly opposite normals.
+std::vector<int2> closure_faces(const fv::HostMesh& h) {
+  std::vector<int2> f;
+  f.reserve((size_t)(2 * h.n));
+  for (int64_t c = 0; c < h.n; ++c)
+    for (int k = 0; k < 3; ++k) {
+      const int32_t m = h.nbr[3 * c + k];
+      if (m < 0) {
+        f.push_back(make_int2((int)(4 * c + k), m));
+        continue;
+      }
+      if (m < c) continue;
+      int km = -1;
+      for (int q = 0; q < 3; ++q)
+        if (h.nbr[3 * (int64_t)m + q] == (int32_t)c && !(m == c && q == k) &&
+            h.nrm[6 * (int64_t)m + 2 * q] == -h.nrm[6 * c + 2 * k] &&
+            h.nrm[6 * (int64_t)m + 2 * q + 1] == -h.nrm[6 * c + 2 * k + 1])
+          km = q;
+      if (km < 0) invalid("closure faces: the two sides of a face do not match");
+      if (m == c && km < k) continue;  // a self-face is listed from its lower index
+      f.push_back(make_int2((int)(4 * c + k), (int)(4 * (int64_t)m + km)));
+    }
+  return f;
+}
+
+void ensure_faces(fv_mesh* m, cudaStream_t s) {
+  if (m->d_faces) return;
+  if (4 * m->h.n > INT32_MAX) invalid("the learned closure takes meshes below 2^29 cells");
+  const std::vector<int2> f = closure_faces(m->h);
+  FV_CUDA(cudaMalloc((void**)&m->d_faces, std::max<size_t>(f.size(), 1) * sizeof(int2)));
+  FV_CUDA(cudaMalloc((void**)&m->d_scale, std::max<int64_t>(3 * m->h.n, 1) * sizeof(float)));
+  FV_CUDA(cudaMemcpyAsync(m->d_faces, f.data(), f.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+  FV_CUDA(cudaStreamSynchronize(s));  // f is a local staging buffer
+  m->n_faces = (int64_t)f.size();
+}
+
 fv::StepArgs base_args(const fv_mesh* m) {
   fv::StepArgs a{};
   a.nbr = m->d_nbr;
@@ -384,7 +437,12 @@ fv::StepArgs base_args(const fv_mesh* m) {
 
 cudaError_t launch_mode(const fv_mesh* m, int mode, const fv::StepArgs& a, const fv_closure* cl,
                         cudaStream_t s) {
-  if (cl) return fv::launch_step_closure(mode, a, cl->params(), s);
+  if (cl) {
+    // the scales of the state the stage evaluates, then the scaled step
+    cudaError_t e = fv::launch_face_scales(a, m->d_faces, m->n_faces, cl->params(), m->d_scale, s);
+    if (e != cudaSuccess) return e;
+    return fv::launch_step_scaled(mode, a, m->d_scale, s);
+  }
   return fv::launch_step(m->f64(), mode, m->variant, a, s);
 }
 
@@ -977,6 +1035,7 @@ int fv_step(fv_mesh* mesh, void* U, int64_t nsteps, double cfl, double t_stop, i
     if (!U && nsteps > 0 && mesh->h.n > 0) invalid("null state");
     cudaStream_t s = as_stream(stream);
     ensure_device(mesh, s);
+    if (closure) ensure_faces(mesh, s);
     const int64_t n = mesh->h.n;
     FV_CUDA(fv::launch_init_scalars(mesh->d_scal, s));
     mesh->last_t_slot = 0;
@@ -1058,9 +1117,12 @@ int fv_residual(fv_mesh* mesh, const void* U, void* R, const fv_closure* closure
     // one thread per cell; the tile shape with vertex geometry (same bits)
     const int shape = mesh->vertex_tiles() ? fv::kTileVariant : 0;
     if (shape == fv::kTileVariant) check_tile_smem(mesh, tile_smem(mesh));
-    if (closure)
-      FV_CUDA(fv::launch_step_closure(fv::kModeResidual, a, closure->params(), s));
-    else
+    if (closure) {
+      ensure_faces(mesh, s);
+      FV_CUDA(fv::launch_face_scales(a, mesh->d_faces, mesh->n_faces, closure->params(),
+                                     mesh->d_scale, s));
+      FV_CUDA(fv::launch_step_scaled(fv::kModeResidual, a, mesh->d_scale, s));
+    } else
       FV_CUDA(fv::launch_step(mesh->f64(), fv::kModeResidual, shape, a, s));
   });
 }
@@ -1752,9 +1814,10 @@ int fv_closure_scales(fv_mesh* mesh, const void* U, const fv_closure* closure, f
     if (!U || !scales) invalid("null state or scales");
     cudaStream_t s = as_stream(stream);
     ensure_device(mesh, s);
+    ensure_faces(mesh, s);
     fv::StepArgs a = base_args(mesh);
     a.U = U;
-    FV_CUDA(fv::launch_closure_scales(a, closure->params(), scales, s));
+    FV_CUDA(fv::launch_face_scales(a, mesh->d_faces, mesh->n_faces, closure->params(), scales, s));
   });
 }
 
@@ -1784,6 +1847,23 @@ int fv_closure_loss_grad(fv_mesh* mesh, const void* U0, const void* Ut, double d
       FV_CUDA(cudaMemcpyAsync(loss, closure->d_loss, sizeof(double), cudaMemcpyDeviceToHost, s));
       FV_CUDA(cudaStreamSynchronize(s));
     }
+  });
+}
+
+int fv_restrict_mean(const void* U_fine, int32_t fine_precision, const double* area_fine,
+                     const int32_t* fine_of, int64_t n_coarse, int32_t children, void* U_coarse,
+                     int32_t coarse_precision, void* stream) {
+  return guarded([&] {
+    if ((fine_precision != FV_F32 && fine_precision != FV_F64) ||
+        (coarse_precision != FV_F32 && coarse_precision != FV_F64))
+      invalid("precision must be FV_F32 or FV_F64");
+    if (n_coarse < 0 || children < 1 || n_coarse > INT32_MAX / children)
+      invalid("bad n_coarse or children");
+    if (n_coarse == 0) return;
+    if (!U_fine || !area_fine || !fine_of || !U_coarse) invalid("null pointer");
+    FV_CUDA(fv::launch_restrict_mean(fine_precision == FV_F64, coarse_precision == FV_F64,
+                                     U_fine, area_fine, fine_of, n_coarse, children, U_coarse,
+                                     as_stream(stream)));
   });
 }
 

@@ -27,6 +27,7 @@
 
 #include "cell_math.cuh"
 #include "kernels.h"
+#include "launch_util.cuh"
 
 namespace fv {
 
@@ -400,6 +401,119 @@ __global__ void __launch_bounds__(kClThreads) k_closure_scales(StepArgs a, Closu
   }
 }
 
+// ---------------------------------------------------------------------------
+// The scales as a pass of their own, then the step reading them.
+//
+// k_face_scales walks a list of the mesh's faces, each once (faces.cpp order:
+// owner cell a, its face ka, the cell b across with its face kb, or a ghost
+// code): a warp takes 32 faces, forms their features, evaluates the MLP on
+// two 16-row tiles and writes each scale to both cells' slots s[3a + ka] and
+// s[3b + kb].  The features are the same bits from either side of a face, so
+// the scales are those of the fused kernel above.  k_step_scaled is the
+// persistent one-thread-per-cell step with the flux's dissipation scaled by
+// s[3i + k]: the per-cell state it keeps is that of the plain step, so it
+// runs at the plain step's occupancy instead of carrying the cell across the
+// MLP.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kClThreads) k_face_scales(StepArgs a, const int2* faces,
+                                                            int64_t nf, ClosureParams cp,
+                                                            float* s_cf) {
+  chain_entry();
+  __shared__ ClShared sh;
+  load_small_params(cp, sh);
+  ClFrag fr;
+  load_frags(cp, fr);
+  const float4* __restrict__ U = static_cast<const float4*>(a.U);
+  const float4* __restrict__ geom = static_cast<const float4*>(a.geom);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  ClWarpSmem& w = sh.warp[warp];
+  const int64_t wstride = (int64_t)gridDim.x * kClWarps * 32;
+  for (int64_t base = ((int64_t)blockIdx.x * kClWarps + warp) * 32; base < nf; base += wstride) {
+    const int64_t row = base + lane;
+    const bool valid = row < nf;
+    float f[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    int2 fc = make_int2(0, -1);
+    if (valid) {
+      fc = __ldg(faces + row);
+      const int ca = fc.x >> 2, ka = fc.x & 3;
+      const float4 UL = __ldg(U + ca);
+      float nx, ny;
+      if (ka < 2) {
+        const float4 g0 = __ldg(geom + 2 * ca);
+        nx = ka ? g0.z : g0.x;
+        ny = ka ? g0.w : g0.y;
+      } else {
+        const float4 g1 = __ldg(geom + 2 * ca + 1);
+        nx = g1.x;
+        ny = g1.y;
+      }
+      const int nb = fc.y >= 0 ? (fc.y >> 2) : fc.y;
+      const float4 UR = neighbour_state<float>(UL, nb, nx, ny, U, a.uinf_f, a.n, a.err);
+      const Prim<float> L = primitive<float>(UL), W = primitive<float>(UR);
+      face_features(UL, L, UR, W, nx, ny, face_len<float>(nx, ny), f);
+    }
+    w.feat[lane] = pack_features(f);
+    __syncwarp();
+    warp_mlp(w, fr, sh.b1, sh.b2, sh.w3, cp.b3, 2);
+    __syncwarp();
+    if (valid) {
+      const float sv = w.s[lane];
+      s_cf[3 * (int64_t)(fc.x >> 2) + (fc.x & 3)] = sv;
+      if (fc.y >= 0 && index_ok(fc.y >> 2, a.n, a.err))
+        s_cf[3 * (int64_t)(fc.y >> 2) + (fc.y & 3)] = sv;
+    }
+    __syncwarp();
+  }
+}
+
+template <int MODE, bool COMP>
+__global__ void __launch_bounds__(kBlock) k_step_scaled(StepArgs a, const float* s_cf) {
+  chain_entry();
+  const float4* __restrict__ U = static_cast<const float4*>(a.U);
+  const float4* __restrict__ geom = static_cast<const float4*>(a.geom);
+  float4* out = static_cast<float4*>(a.out);
+  double t = 0.0, dt = 0.0;
+  if (MODE != kModeResidual) dt = step_dt(a, t);
+  float bmin = INFINITY;
+  bool ok = true;
+  const int n = (int)a.n;
+  const int stride = gridDim.x * blockDim.x;
+  CellIn<float> cur, nxt;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) load_cell<float, MODE, COMP>(a, U, geom, i, cur);
+  for (; i < n; i += stride) {
+    const int j = i + stride;
+    if (j < n) load_cell<float, MODE, COMP>(a, U, geom, j, nxt);
+    const Prim<float> L = primitive<float>(cur.U);
+    const int nb[3] = {cur.n0, cur.n1, cur.n2};
+    const float nx[3] = {cur.g0.x, cur.g0.z, cur.g1.x}, ny[3] = {cur.g0.y, cur.g0.w, cur.g1.y};
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    float perim = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float4 UR = neighbour_state<float>(cur.U, nb[k], nx[k], ny[k], U, a.uinf_f, a.n, a.err);
+      const Prim<float> W = primitive<float>(UR);
+      const float len = face_len<float>(nx[k], ny[k]);
+      face_flux_acc<float, true>(cur.U, L, UR, W, nx[k], ny[k], len, __ldg(s_cf + 3 * i + k),
+                                 acc);
+      perim = k == 0 ? len : add(perim, len);
+    }
+    finish_cell<float, MODE, COMP>(a, out, i, cur, acc, perim, (float)dt, bmin, ok);
+    cur = nxt;
+  }
+  if (MODE == kModeFE || MODE == kModeRK2b) {
+    if (!ok) atomicOr(a.err, 1);
+    const double m = (double)block_min<float>(bmin);
+    if (threadIdx.x == 0) {
+      atomicMin(a.bmin_write, (unsigned long long)__double_as_longlong(m));
+      if (blockIdx.x == 0) {
+        *a.t_write = t + dt;
+        *a.bmin_reset = kInfBits;
+      }
+    }
+  }
+}
+
 template <typename K>
 unsigned cl_resident_blocks(K kernel) {
   static int cached = 0;
@@ -765,6 +879,50 @@ cudaError_t launch_closure_scales(const StepArgs& a, const ClosureParams& cp, fl
   if (a.n <= 0) return cudaSuccess;
   k_closure_scales<<<cl_grid(k_closure_scales, 32, a.n), kClThreads, 0, s>>>(a, cp, s_out);
   return cudaGetLastError();
+}
+
+cudaError_t launch_face_scales(const StepArgs& a, const int2* faces, int64_t nf,
+                               const ClosureParams& cp, float* s_cf, cudaStream_t s) {
+  if (nf <= 0) return cudaSuccess;
+  return launch_chained(k_face_scales, cl_grid(k_face_scales, 32, nf), kClThreads, 0, s,
+                        a.chained, a, faces, nf, cp, s_cf);
+}
+
+namespace {
+template <int MODE, bool COMP>
+cudaError_t launch_scaled_t(const StepArgs& a, const float* s_cf, cudaStream_t s) {
+  auto k = k_step_scaled<MODE, COMP>;
+  static int per_sm = 0, sms = 0;
+  if (per_sm == 0) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kBlock, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  }
+  const int64_t want = (a.n + kBlock - 1) / kBlock, cap = (int64_t)sms * per_sm;
+  return launch_chained(k, (unsigned)std::max<int64_t>(1, std::min(want, cap)), kBlock, 0, s,
+                        a.chained, a, s_cf);
+}
+}  // namespace
+
+cudaError_t launch_step_scaled(int mode, const StepArgs& a, const float* s_cf, cudaStream_t s) {
+  if (a.n <= 0 && mode == kModeResidual) return cudaSuccess;
+  const bool comp = a.lo != nullptr;
+  switch (mode) {
+    case kModeFE:
+      return comp ? launch_scaled_t<kModeFE, true>(a, s_cf, s)
+                  : launch_scaled_t<kModeFE, false>(a, s_cf, s);
+    case kModeRK2a:
+      return comp ? launch_scaled_t<kModeRK2a, true>(a, s_cf, s)
+                  : launch_scaled_t<kModeRK2a, false>(a, s_cf, s);
+    case kModeRK2b:
+      return comp ? launch_scaled_t<kModeRK2b, true>(a, s_cf, s)
+                  : launch_scaled_t<kModeRK2b, false>(a, s_cf, s);
+    case kModeResidual: return launch_scaled_t<kModeResidual, false>(a, s_cf, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace fv

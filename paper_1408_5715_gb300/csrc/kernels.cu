@@ -475,6 +475,51 @@ cudaError_t launch_totals(bool f64, const void* U, const double* vol, int64_t n,
   return cudaGetLastError();
 }
 
+// Restriction of a fine state to coarse cells: for coarse cell c, the
+// area-weighted mean of its `kids` fine cells fine_of[c*kids + j], summed in
+// FP64 in the order j = 0, 1, ... and written in the coarse precision.
+template <typename RF, typename RC>
+__global__ void __launch_bounds__(kBlock) k_restrict_mean(const rec_t<RF>* __restrict__ Uf,
+                                                          const double* __restrict__ area,
+                                                          const int* __restrict__ fine_of,
+                                                          int64_t n_coarse, int kids,
+                                                          rec_t<RC>* Uc) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_coarse) return;
+  double s[4] = {0.0, 0.0, 0.0, 0.0}, v = 0.0;
+  for (int j = 0; j < kids; ++j) {
+    const int f = __ldg(fine_of + c * kids + j);
+    const rec_t<RF> u = Rec<RF>::ld(Uf + f);
+    const double a = __ldg(area + f);
+    s[0] += a * (double)u.x;
+    s[1] += a * (double)u.y;
+    s[2] += a * (double)u.z;
+    s[3] += a * (double)u.w;
+    v += a;
+  }
+  Uc[c] = Rec<RC>::make((RC)(s[0] / v), (RC)(s[1] / v), (RC)(s[2] / v), (RC)(s[3] / v));
+}
+
+cudaError_t launch_restrict_mean(bool fine_f64, bool coarse_f64, const void* Uf, const double* area,
+                                 const int* fine_of, int64_t n_coarse, int kids, void* Uc,
+                                 cudaStream_t s) {
+  if (n_coarse <= 0) return cudaSuccess;
+  const unsigned g = grid_for(n_coarse);
+  if (fine_f64 && coarse_f64)
+    k_restrict_mean<double, double><<<g, kBlock, 0, s>>>(
+        static_cast<const dq4*>(Uf), area, fine_of, n_coarse, kids, static_cast<dq4*>(Uc));
+  else if (fine_f64)
+    k_restrict_mean<double, float><<<g, kBlock, 0, s>>>(
+        static_cast<const dq4*>(Uf), area, fine_of, n_coarse, kids, static_cast<float4*>(Uc));
+  else if (coarse_f64)
+    k_restrict_mean<float, double><<<g, kBlock, 0, s>>>(
+        static_cast<const float4*>(Uf), area, fine_of, n_coarse, kids, static_cast<dq4*>(Uc));
+  else
+    k_restrict_mean<float, float><<<g, kBlock, 0, s>>>(
+        static_cast<const float4*>(Uf), area, fine_of, n_coarse, kids, static_cast<float4*>(Uc));
+  return cudaGetLastError();
+}
+
 cudaError_t launch_reset_min(unsigned long long* bmin, int* flag, cudaStream_t s) {
   k_set_u64<<<1, 1, 0, s>>>(bmin, kInfBits, flag);
   return cudaGetLastError();

@@ -140,6 +140,12 @@ cudaError_t launch_step_closure(int mode, const StepArgs& a, const ClosureParams
                                 cudaStream_t s);
 cudaError_t launch_closure_eval(const float* feats, float* s_out, int64_t rows,
                                 const ClosureParams& cp, cudaStream_t s);
+// The scales of a face list (each face once, both cells' slots s_cf[3c + k]
+// written) and the step that reads them (FP32; persistent one thread per cell).
+// faces[f] = (4 a + ka, 4 b + kb), or (4 a + ka, ghost code < 0).
+cudaError_t launch_face_scales(const StepArgs& a, const int2* faces, int64_t nf,
+                               const ClosureParams& cp, float* s_cf, cudaStream_t s);
+cudaError_t launch_step_scaled(int mode, const StepArgs& a, const float* s_cf, cudaStream_t s);
 cudaError_t launch_closure_scales(const StepArgs& a, const ClosureParams& cp, float* s_out,
                                   cudaStream_t s);
 // Blocks the gradient kernel launches at most on this device.
@@ -166,6 +172,9 @@ constexpr int kTileVariant = 6;
 inline size_t tile_smem_bytes(bool f64, int t1_cap, int v_cap = 0) {
   return (size_t)t1_cap * 2 * (f64 ? 32 : 16) + (size_t)v_cap * 8;
 }
+cudaError_t launch_restrict_mean(bool fine_f64, bool coarse_f64, const void* Uf, const double* area,
+                                 const int* fine_of, int64_t n_coarse, int kids, void* Uc,
+                                 cudaStream_t s);
 cudaError_t launch_step_tile(bool f64, int mode, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_batch_step_tile(bool f64, int mode, const BatchArgs& b, cudaStream_t s);
 // Library-owned per-cell arrays are allocated in whole tiles of this many
