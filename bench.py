@@ -757,8 +757,9 @@ def vertex_leg(B, time_steps=1000):
 
 def pair_leg(B, time_steps=1000):
     """Two forward-Euler steps per launch on shared-memory tiles (Hilbert order),
-    against one launch per step on the same mesh; FP32 compensated, CFL 0.4
-    (one dt per pair for the two-step launch)."""
+    against one launch per step on the same mesh; FP32 with the workload's
+    update (plain on the square, compensated on the channel), CFL 0.4 (one dt
+    per pair for the two-step launch)."""
     import torch
     peak, _ = measured_peaks()
     res = {}
@@ -767,6 +768,9 @@ def pair_leg(B, time_steps=1000):
         mi = spec["make"]()
         U0 = initial_state(spec, mi)
         m, perm = make_mesh(B, spec, mi, "f32", "hilbert")
+        comp = spec["update"] == "compensated"
+        m.set_compensation(comp)
+        pair_bytes = PAIR_BYTES if comp else PAIR_BYTES - COMP_BYTES
         U0d = torch.tensor(U0[perm], dtype=torch.float32, device="cuda")
         U = torch.empty_like(U0d)
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -783,16 +787,18 @@ def pair_leg(B, time_steps=1000):
         best = max(by_tile, key=by_tile.get)
         v2 = by_tile[best]
         launch = 2 * mi.n_tri / v2  # seconds per two-step launch (per-call kernels included)
-        gbs = PAIR_BYTES * mi.n_tri / launch / 1e9
+        gbs = pair_bytes * mi.n_tri / launch / 1e9
         res[name] = {"cells": mi.n_tri, "order": "hilbert", "time_steps": time_steps,
                      "single_step": {"value": v1, "kernel_shape": single},
                      "value": v2, "unit": "cell-updates/s", "tile": best,
                      "value_by_tile": by_tile, "speedup_over_single_step": v2 / v1,
                      "achieved_gbs": gbs, "frac_of_measured_hbm": gbs / peak,
-                     "single_step_equivalent_gbs": (ALGO_BYTES["f32"] + COMP_BYTES) * v2 / 1e9,
-                     "kernel": (f"k_step_pair_tma<tile {best.split('-')[0]}, compensated>"
+                     "update": spec["update"],
+                     "single_step_equivalent_gbs":
+                         (ALGO_BYTES["f32"] + (COMP_BYTES if comp else 0)) * v2 / 1e9,
+                     "kernel": (f"k_step_pair_tma<tile {best.split('-')[0]}, {spec['update']}>"
                                 if best.endswith("staged")
-                                else f"k_step_pair<tile {best}, compensated>")}
+                                else f"k_step_pair<tile {best}, {spec['update']}>")}
         del U, U0d, flush
         m.close()
     return res

@@ -520,7 +520,7 @@ int orc_closure_scale_interval(const double* theta, const double* feat, const do
       r += fabs(wij) * 0.5 * (xhi[j] - xlo[j]);
       mag += fabs(wij) * xhi[j];
     }
-    double w = 10.0 / 8388608.0 * mag;
+    double w = 16.0 / 8388608.0 * mag;
     double lo = c - r - w, hi = c + r + w;
     hlo[i] = orc_round_bf16(lo > 0.0 ? lo : 0.0);
     hhi[i] = orc_round_bf16(hi > 0.0 ? hi : 0.0);

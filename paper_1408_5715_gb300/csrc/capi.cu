@@ -140,7 +140,7 @@ struct fv_mesh {
   int p_v_cap = 0;
   // learned closure: each face once (owner cell and face, cell across and
   // its face, or a ghost code) and the scale of every cell face
-  int2* d_faces = nullptr;
+  fv::FaceRec* d_faces = nullptr;
   int64_t n_faces = 0;
   float* d_scale = nullptr;
   unsigned wait_limit = fv::kDefaultWaitLimit;  // bounded device waits (variant 5)
@@ -368,16 +368,21 @@ void ensure_device(fv_mesh* m, cudaStream_t s) {
 // The faces of the mesh, each once, for the learned closure's scale pass:
 // (4 a + ka, 4 b + kb) for the face ka of cell a whose other side is face kb
 // of cell b (a <= b; a cell may border itself across a periodic seam), and
-// (4 a + ka, ghost code) for a boundary face.  The two sides of a face are
-// matched by neighbour id and exactly opposite normals.
-std::vector<int2> closure_faces(const fv::HostMesh& h) {
-  std::vector<int2> f;
+// (4 a + ka, ghost code) for a boundary face, with face ka's normal as the
+// FP32 geometry record rounds it.  The two sides of a face are matched by
+// neighbour id and exactly opposite normals.
+std::vector<fv::FaceRec> closure_faces(const fv::HostMesh& h) {
+  std::vector<fv::FaceRec> f;
   f.reserve((size_t)(2 * h.n));
+  auto rec = [&](int64_t c, int k, int b) {
+    return fv::FaceRec{(int)(4 * c + k), b, (float)h.nrm[6 * c + 2 * k],
+                       (float)h.nrm[6 * c + 2 * k + 1]};
+  };
   for (int64_t c = 0; c < h.n; ++c)
     for (int k = 0; k < 3; ++k) {
       const int32_t m = h.nbr[3 * c + k];
       if (m < 0) {
-        f.push_back(make_int2((int)(4 * c + k), m));
+        f.push_back(rec(c, k, m));
         continue;
       }
       if (m < c) continue;
@@ -389,7 +394,7 @@ std::vector<int2> closure_faces(const fv::HostMesh& h) {
           km = q;
       if (km < 0) invalid("closure faces: the two sides of a face do not match");
       if (m == c && km < k) continue;  // a self-face is listed from its lower index
-      f.push_back(make_int2((int)(4 * c + k), (int)(4 * (int64_t)m + km)));
+      f.push_back(rec(c, k, (int)(4 * (int64_t)m + km)));
     }
   return f;
 }
@@ -397,10 +402,11 @@ std::vector<int2> closure_faces(const fv::HostMesh& h) {
 void ensure_faces(fv_mesh* m, cudaStream_t s) {
   if (m->d_faces) return;
   if (4 * m->h.n > INT32_MAX) invalid("the learned closure takes meshes below 2^29 cells");
-  const std::vector<int2> f = closure_faces(m->h);
-  FV_CUDA(cudaMalloc((void**)&m->d_faces, std::max<size_t>(f.size(), 1) * sizeof(int2)));
+  const std::vector<fv::FaceRec> f = closure_faces(m->h);
+  FV_CUDA(cudaMalloc((void**)&m->d_faces, std::max<size_t>(f.size(), 1) * sizeof(fv::FaceRec)));
   FV_CUDA(cudaMalloc((void**)&m->d_scale, std::max<int64_t>(3 * m->h.n, 1) * sizeof(float)));
-  FV_CUDA(cudaMemcpyAsync(m->d_faces, f.data(), f.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+  FV_CUDA(cudaMemcpyAsync(m->d_faces, f.data(), f.size() * sizeof(fv::FaceRec),
+                          cudaMemcpyHostToDevice, s));
   FV_CUDA(cudaStreamSynchronize(s));  // f is a local staging buffer
   m->n_faces = (int64_t)f.size();
 }

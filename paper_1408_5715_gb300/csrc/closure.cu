@@ -68,9 +68,13 @@ __device__ __forceinline__ unsigned pack_bf16_relu(float lo, float hi) {
   return *reinterpret_cast<const unsigned*>(&v);
 }
 
-__device__ __forceinline__ float scale_of(float z) {
-  return 0.2f + 1.3f * (1.0f / (1.0f + expf(-z)));
+// sigmoid(z) with the special-function unit's exponential and reciprocal
+// (relative error a few 2^-22: far below the 1e-5 to which scales are held)
+__device__ __forceinline__ float sigmoid(float z) {
+  return recip<float>(add(1.0f, __expf(-z)));
 }
+
+__device__ __forceinline__ float scale_of(float z) { return fma_(1.3f, sigmoid(z), 0.2f); }
 
 // The eight swap-invariant features of a face.
 __device__ __forceinline__ void face_features(const float4& UL, const Prim<float>& L,
@@ -99,31 +103,53 @@ __device__ __forceinline__ uint4 pack_features(const float f[8]) {
                     pack_bf16(f[6], f[7]));
 }
 
-// Weights as this thread's mma B fragments (loaded once per kernel).
+// Weights as this thread's mma B fragments (loaded once per kernel).  The
+// hidden-layer biases ride in the MMAs: each FP32 bias b is split into three
+// bfloat16 parts hi + mid + lo (together its 24-bit significand) placed in
+// three K rows of B, against A columns that hold 1.0 -- for layer 1 in the
+// padding rows 8..10 of its K = 16 slice, for layer 2 in an extra K slice --
+// so the tensor core adds them instead of 32 FP32 additions per row.
 struct ClFrag {
-  unsigned w1[4];   // layer 1, per n-tile: W1[n][2c..2c+1] (K rows 8..15 are zero)
+  unsigned w1[4];   // layer 1, per n-tile: W1[n][2c..2c+1]
+  unsigned w1b[4];  // layer 1, per n-tile: bias parts in K rows 8..10 (lanes c = 0, 1)
   unsigned w2[16];  // layer 2, per (n-tile, k-slice): two registers
+  unsigned w2b[4];  // layer 2, per n-tile: bias parts in K rows 0..2 of the extra slice
+  unsigned one;     // A columns of the bias rows: (1, 1) for c = 0, (1, 0) for c = 1
 };
+
+// The bias parts of unit n for lane quad position c: (hi, mid) for c = 0,
+// (lo, 0) for c = 1, nothing for c = 2, 3.
+__device__ __forceinline__ unsigned bias_parts(float b, int c) {
+  const __nv_bfloat16 hi = __float2bfloat16_rn(b);
+  const float r1 = sub(b, __bfloat162float(hi));
+  const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+  const float r2 = sub(r1, __bfloat162float(mid));
+  if (c == 0) return pack_bf16(__bfloat162float(hi), __bfloat162float(mid));
+  if (c == 1) return pack_bf16(r2, 0.0f);
+  return 0u;
+}
 
 __device__ __forceinline__ void load_frags(const ClosureParams& cp, ClFrag& fr) {
   const int lane = threadIdx.x & 31, r = lane >> 2, c = lane & 3;
 #pragma unroll
   for (int nt = 0; nt < 4; ++nt) {
     fr.w1[nt] = __ldg(cp.w1 + (nt * 8 + r) * 4 + c);
+    fr.w1b[nt] = bias_parts(__ldg(cp.b1 + nt * 8 + r), c);
+    fr.w2b[nt] = bias_parts(__ldg(cp.b2 + nt * 8 + r), c);
 #pragma unroll
     for (int kk = 0; kk < 2; ++kk) {
       fr.w2[(nt * 2 + kk) * 2] = __ldg(cp.w2 + (nt * 8 + r) * 16 + kk * 8 + c);
       fr.w2[(nt * 2 + kk) * 2 + 1] = __ldg(cp.w2 + (nt * 8 + r) * 16 + kk * 8 + 4 + c);
     }
   }
+  fr.one = c == 0 ? 0x3F803F80u : c == 1 ? 0x00003F80u : 0u;  // bfloat16 1.0 = 0x3F80
 }
 
 // Layer-1 and layer-2 pre-activations of one 16-row tile, in accumulator
 // fragment layout: g[nt][0..1] row r, g[nt][2..3] row r+8, columns
 // nt*8 + 2c, +1.  h1 (bfloat16, as layer-2 A fragments) is returned too.
 __device__ __forceinline__ void tile_forward(const ClWarpSmem& w, int t, const ClFrag& fr,
-                                             const float* b1, const float* b2, float a1[4][4],
-                                             unsigned A2[2][4], float g[4][4]) {
+                                             float a1[4][4], unsigned A2[2][4], float g[4][4]) {
   const int lane = threadIdx.x & 31, r = lane >> 2, c = lane & 3;
   const unsigned* row0 = reinterpret_cast<const unsigned*>(&w.feat[16 * t + r]);
   const unsigned* row1 = reinterpret_cast<const unsigned*>(&w.feat[16 * t + r + 8]);
@@ -131,12 +157,8 @@ __device__ __forceinline__ void tile_forward(const ClWarpSmem& w, int t, const C
 #pragma unroll
   for (int nt = 0; nt < 4; ++nt) {
     a1[nt][0] = a1[nt][1] = a1[nt][2] = a1[nt][3] = 0.0f;
-    mma_bf16(a1[nt], x0, x1, 0u, 0u, fr.w1[nt], 0u);
-    const int col = nt * 8 + 2 * c;
-    a1[nt][0] += b1[col];
-    a1[nt][1] += b1[col + 1];
-    a1[nt][2] += b1[col];
-    a1[nt][3] += b1[col + 1];
+    // K columns 0..7 the features, 8..10 the bias rows against 1.0
+    mma_bf16(a1[nt], x0, x1, fr.one, fr.one, fr.w1[nt], fr.w1b[nt]);
     const unsigned p0 = pack_bf16_relu(a1[nt][0], a1[nt][1]);
     const unsigned p1 = pack_bf16_relu(a1[nt][2], a1[nt][3]);
     A2[nt >> 1][(nt & 1) ? 2 : 0] = p0;
@@ -149,11 +171,7 @@ __device__ __forceinline__ void tile_forward(const ClWarpSmem& w, int t, const C
     for (int kk = 0; kk < 2; ++kk)
       mma_bf16(g[nt], A2[kk][0], A2[kk][1], A2[kk][2], A2[kk][3], fr.w2[(nt * 2 + kk) * 2],
                fr.w2[(nt * 2 + kk) * 2 + 1]);
-    const int col = nt * 8 + 2 * c;
-    g[nt][0] += b2[col];
-    g[nt][1] += b2[col + 1];
-    g[nt][2] += b2[col];
-    g[nt][3] += b2[col + 1];
+    mma_bf16(g[nt], fr.one, fr.one, 0u, 0u, fr.w2b[nt], 0u);  // + b2
   }
 }
 
@@ -179,14 +197,13 @@ __device__ __forceinline__ void tile_output(const float g[4][4], const float* w3
 
 // Scales of the warp's first 16 * ntile rows, from the features in w.feat
 // into w.s.
-__device__ __forceinline__ void warp_mlp(ClWarpSmem& w, const ClFrag& fr, const float* b1,
-                                         const float* b2, const float* w3, float b3,
+__device__ __forceinline__ void warp_mlp(ClWarpSmem& w, const ClFrag& fr, const float* w3, float b3,
                                          int ntile = kRows / 16) {
   const int lane = threadIdx.x & 31, r = lane >> 2, c = lane & 3;
   for (int t = 0; t < ntile; ++t) {
     float a1[4][4], g[4][4];
     unsigned A2[2][4];
-    tile_forward(w, t, fr, b1, b2, a1, A2, g);
+    tile_forward(w, t, fr, a1, A2, g);
     float z0, z1;
     tile_output(g, w3, b3, z0, z1);
     if (c == 0) {
@@ -284,7 +301,7 @@ __global__ void __launch_bounds__(kClThreads) k_step_closure(StepArgs a, Closure
     const int ntile = (total + 15) >> 4;
     for (int j = total + lane; j < 16 * ntile; j += 32) w.feat[j] = make_uint4(0u, 0u, 0u, 0u);
     __syncwarp();
-    warp_mlp(w, fr, sh.b1, sh.b2, sh.w3, cp.b3, ntile);
+    warp_mlp(w, fr, sh.w3, cp.b3, ntile);
     __syncwarp();
     // each face's row: its own, or the one the neighbouring lane evaluated for
     // the same face (the neighbour's face pointing back with the negated normal)
@@ -350,7 +367,7 @@ __global__ void __launch_bounds__(kClThreads) k_closure_eval(const float* feats,
       w.feat[j] = pack_features(f);
     }
     __syncwarp();
-    warp_mlp(w, fr, sh.b1, sh.b2, sh.w3, cp.b3);
+    warp_mlp(w, fr, sh.w3, cp.b3);
     __syncwarp();
     for (int j = lane; j < kRows; j += 32)
       if (base + j < rows) s_out[base + j] = w.s[j];
@@ -392,7 +409,7 @@ __global__ void __launch_bounds__(kClThreads) k_closure_scales(StepArgs a, Closu
       for (int k = 0; k < 3; ++k) w.feat[k * 32 + lane] = make_uint4(0u, 0u, 0u, 0u);
     }
     __syncwarp();
-    warp_mlp(w, fr, sh.b1, sh.b2, sh.w3, cp.b3);
+    warp_mlp(w, fr, sh.w3, cp.b3);
     __syncwarp();
     if (i < a.n)
 #pragma unroll
@@ -415,7 +432,23 @@ __global__ void __launch_bounds__(kClThreads) k_closure_scales(StepArgs a, Closu
 // runs at the plain step's occupancy instead of carrying the cell across the
 // MLP.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kClThreads) k_face_scales(StepArgs a, const int2* faces,
+// What a face's row reads: its record and the two states (the state across
+// is a ghost state at a boundary face).
+struct FaceIn {
+  FaceRec f;
+  float4 UL, UR;
+};
+
+__device__ __forceinline__ void load_face(const StepArgs& a, const FaceRec* faces, int64_t row,
+                                          FaceIn& x) {
+  const float4* __restrict__ U = static_cast<const float4*>(a.U);
+  x.f = faces[row];
+  x.UL = __ldg(U + (x.f.a >> 2));
+  const int nb = x.f.b >= 0 ? (x.f.b >> 2) : x.f.b;
+  x.UR = neighbour_state<float>(x.UL, nb, x.f.nx, x.f.ny, U, a.uinf_f, a.n, a.err);
+}
+
+__global__ void __launch_bounds__(kClThreads) k_face_scales(StepArgs a, const FaceRec* faces,
                                                             int64_t nf, ClosureParams cp,
                                                             float* s_cf) {
   chain_entry();
@@ -423,44 +456,30 @@ __global__ void __launch_bounds__(kClThreads) k_face_scales(StepArgs a, const in
   load_small_params(cp, sh);
   ClFrag fr;
   load_frags(cp, fr);
-  const float4* __restrict__ U = static_cast<const float4*>(a.U);
-  const float4* __restrict__ geom = static_cast<const float4*>(a.geom);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   ClWarpSmem& w = sh.warp[warp];
   const int64_t wstride = (int64_t)gridDim.x * kClWarps * 32;
-  for (int64_t base = ((int64_t)blockIdx.x * kClWarps + warp) * 32; base < nf; base += wstride) {
-    const int64_t row = base + lane;
+  int64_t row = ((int64_t)blockIdx.x * kClWarps + warp) * 32 + lane;
+  // this round's face and, issued before this round computes, the next's
+  FaceIn cur, nxt;
+  for (int64_t base = row - lane; base < nf; base += wstride, row += wstride) {
     const bool valid = row < nf;
+    if (valid) load_face(a, faces, row, cur);
     float f[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    int2 fc = make_int2(0, -1);
     if (valid) {
-      fc = __ldg(faces + row);
-      const int ca = fc.x >> 2, ka = fc.x & 3;
-      const float4 UL = __ldg(U + ca);
-      float nx, ny;
-      if (ka < 2) {
-        const float4 g0 = __ldg(geom + 2 * ca);
-        nx = ka ? g0.z : g0.x;
-        ny = ka ? g0.w : g0.y;
-      } else {
-        const float4 g1 = __ldg(geom + 2 * ca + 1);
-        nx = g1.x;
-        ny = g1.y;
-      }
-      const int nb = fc.y >= 0 ? (fc.y >> 2) : fc.y;
-      const float4 UR = neighbour_state<float>(UL, nb, nx, ny, U, a.uinf_f, a.n, a.err);
-      const Prim<float> L = primitive<float>(UL), W = primitive<float>(UR);
-      face_features(UL, L, UR, W, nx, ny, face_len<float>(nx, ny), f);
+      const Prim<float> L = primitive<float>(cur.UL), W = primitive<float>(cur.UR);
+      face_features(cur.UL, L, cur.UR, W, cur.f.nx, cur.f.ny, face_len<float>(cur.f.nx, cur.f.ny),
+                    f);
     }
     w.feat[lane] = pack_features(f);
     __syncwarp();
-    warp_mlp(w, fr, sh.b1, sh.b2, sh.w3, cp.b3, 2);
+    warp_mlp(w, fr, sh.w3, cp.b3, 2);
     __syncwarp();
     if (valid) {
       const float sv = w.s[lane];
-      s_cf[3 * (int64_t)(fc.x >> 2) + (fc.x & 3)] = sv;
-      if (fc.y >= 0 && index_ok(fc.y >> 2, a.n, a.err))
-        s_cf[3 * (int64_t)(fc.y >> 2) + (fc.y & 3)] = sv;
+      s_cf[3 * (int64_t)(cur.f.a >> 2) + (cur.f.a & 3)] = sv;
+      if (cur.f.b >= 0 && index_ok(cur.f.b >> 2, a.n, a.err))
+        s_cf[3 * (int64_t)(cur.f.b >> 2) + (cur.f.b & 3)] = sv;
     }
     __syncwarp();
   }
@@ -479,11 +498,20 @@ __global__ void __launch_bounds__(kBlock) k_step_scaled(StepArgs a, const float*
   const int n = (int)a.n;
   const int stride = gridDim.x * blockDim.x;
   CellIn<float> cur, nxt;
+  float sc[3], sn[3];  // the scales of the cell, and of the next (loaded with its records)
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) load_cell<float, MODE, COMP>(a, U, geom, i, cur);
+  if (i < n) {
+    load_cell<float, MODE, COMP>(a, U, geom, i, cur);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) sc[k] = __ldg(s_cf + 3 * i + k);
+  }
   for (; i < n; i += stride) {
     const int j = i + stride;
-    if (j < n) load_cell<float, MODE, COMP>(a, U, geom, j, nxt);
+    if (j < n) {
+      load_cell<float, MODE, COMP>(a, U, geom, j, nxt);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) sn[k] = __ldg(s_cf + 3 * j + k);
+    }
     const Prim<float> L = primitive<float>(cur.U);
     const int nb[3] = {cur.n0, cur.n1, cur.n2};
     const float nx[3] = {cur.g0.x, cur.g0.z, cur.g1.x}, ny[3] = {cur.g0.y, cur.g0.w, cur.g1.y};
@@ -494,12 +522,13 @@ __global__ void __launch_bounds__(kBlock) k_step_scaled(StepArgs a, const float*
       const float4 UR = neighbour_state<float>(cur.U, nb[k], nx[k], ny[k], U, a.uinf_f, a.n, a.err);
       const Prim<float> W = primitive<float>(UR);
       const float len = face_len<float>(nx[k], ny[k]);
-      face_flux_acc<float, true>(cur.U, L, UR, W, nx[k], ny[k], len, __ldg(s_cf + 3 * i + k),
-                                 acc);
+      face_flux_acc<float, true>(cur.U, L, UR, W, nx[k], ny[k], len, sc[k], acc);
       perim = k == 0 ? len : add(perim, len);
     }
     finish_cell<float, MODE, COMP>(a, out, i, cur, acc, perim, (float)dt, bmin, ok);
     cur = nxt;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) sc[k] = sn[k];
   }
   if (MODE == kModeFE || MODE == kModeRK2b) {
     if (!ok) atomicOr(a.err, 1);
@@ -635,7 +664,7 @@ __global__ void __launch_bounds__(kGrThreads) k_closure_grad(StepArgs a, const f
     for (int t = 0; t < kRows / 16; ++t) {
       float a1[4][4], g[4][4];
       unsigned A2[2][4];
-      tile_forward(w.f, t, fr, sh.b1, sh.b2, a1, A2, g);
+      tile_forward(w.f, t, fr, a1, A2, g);
 #pragma unroll
       for (int nt = 0; nt < 4; ++nt) {
         w.h1[(16 * t + r) * 16 + nt * 4 + cq] = A2[nt >> 1][(nt & 1) ? 2 : 0];
@@ -649,8 +678,8 @@ __global__ void __launch_bounds__(kGrThreads) k_closure_grad(StepArgs a, const f
       float z0, z1;
       tile_output(g, sh.w3, cp.b3, z0, z1);
       if (cq == 0) {
-        w.sig[16 * t + r] = 1.0f / (1.0f + expf(-z0));
-        w.sig[16 * t + r + 8] = 1.0f / (1.0f + expf(-z1));
+        w.sig[16 * t + r] = sigmoid(z0);
+        w.sig[16 * t + r + 8] = sigmoid(z1);
       }
     }
     __syncwarp();
@@ -660,7 +689,7 @@ __global__ void __launch_bounds__(kGrThreads) k_closure_grad(StepArgs a, const f
       float dFds[3][4];
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        const float sk = 0.2f + 1.3f * w.sig[k * 32 + lane];
+        const float sk = fma_(1.3f, w.sig[k * 32 + lane], 0.2f);
         face_flux_acc<float, true>(c.U, L, UR[k], W[k], nx[k], ny[k], len[k], sk, acc);
         const float qL = fma_(L.u, nx[k], mul(L.v, ny[k]));
         const float qR = fma_(W[k].u, nx[k], mul(W[k].v, ny[k]));
@@ -881,7 +910,7 @@ cudaError_t launch_closure_scales(const StepArgs& a, const ClosureParams& cp, fl
   return cudaGetLastError();
 }
 
-cudaError_t launch_face_scales(const StepArgs& a, const int2* faces, int64_t nf,
+cudaError_t launch_face_scales(const StepArgs& a, const FaceRec* faces, int64_t nf,
                                const ClosureParams& cp, float* s_cf, cudaStream_t s) {
   if (nf <= 0) return cudaSuccess;
   return launch_chained(k_face_scales, cl_grid(k_face_scales, 32, nf), kClThreads, 0, s,

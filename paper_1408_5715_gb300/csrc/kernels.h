@@ -142,8 +142,14 @@ cudaError_t launch_closure_eval(const float* feats, float* s_out, int64_t rows,
                                 const ClosureParams& cp, cudaStream_t s);
 // The scales of a face list (each face once, both cells' slots s_cf[3c + k]
 // written) and the step that reads them (FP32; persistent one thread per cell).
-// faces[f] = (4 a + ka, 4 b + kb), or (4 a + ka, ghost code < 0).
-cudaError_t launch_face_scales(const StepArgs& a, const int2* faces, int64_t nf,
+// A face record: a = 4 c + k (cell c, its face k), b = 4 m + km for the cell
+// m across (its face km) or a ghost code < 0, and face k's normal of cell c
+// (times the face length) in FP32, as in the cell's geometry record.
+struct __align__(16) FaceRec {
+  int a, b;
+  float nx, ny;
+};
+cudaError_t launch_face_scales(const StepArgs& a, const FaceRec* faces, int64_t nf,
                                const ClosureParams& cp, float* s_cf, cudaStream_t s);
 cudaError_t launch_step_scaled(int mode, const StepArgs& a, const float* s_cf, cudaStream_t s);
 cudaError_t launch_closure_scales(const StepArgs& a, const ClosureParams& cp, float* s_out,

@@ -10,9 +10,8 @@ admissible roundings and whether every rounding is determined
 (orc_closure_scale_interval).  Every face is checked on its own: a face whose
 roundings are determined must agree with the oracle's scale to 1e-5; every
 other face must lie within its interval widened by 1e-5 (the FP32 rounding of
-layers 2 and 3).  Gradients are compared on inputs where every face whose
-roundings are not determined is inert (equal states on both sides), so that
-its scale enters neither the flux nor the gradient.
+layers 2 and 3).  Gradients are compared on inputs drawn so that no face's
+admissible roundings move its scale by more than 1e-6.
 """
 import math
 
@@ -167,74 +166,45 @@ def test_closure_residual_and_errors(vortex_case):
         g64.step(torch.tensor(U0, device="cuda"), 1, 0.4, closure=cl)
 
 
-def settle_undetermined_faces(orc, om, U, theta, max_iter=100):
-    """Input generation for the gradient comparison: makes every face whose
-    bfloat16 roundings are not all determined inert -- its two states equal,
-    so its scale enters neither the flux nor the gradient.  Cells are merged
-    into clusters of one state (union-find); a cluster at an undetermined wall
-    face loses its momentum (the mirrored ghost then equals the cell), one at
-    an undetermined far-field face takes the free stream (at rest here, so
-    both hold at once).  Merging never separates two cells, so it settles."""
+SETTLED_WIDTH = 1e-6  # admissible roundings move a settled face's scale by at most this
+
+
+def random_states(rng, k):
+    """k cell states drawn independently (features O(1), no cancelling jumps)."""
+    U = W.conserved(rng.uniform(0.5, 2.0, k), rng.uniform(-0.5, 0.5, k),
+                    rng.uniform(-0.5, 0.5, k), rng.uniform(0.5, 2.0, k))
+    return U.astype(np.float32).astype(np.float64)
+
+
+def redraw_ambiguous_cells(om, U, theta, rng, max_iter=100):
+    """Input generation for the gradient comparison: every cell with a face
+    whose admissible bfloat16 roundings spread its scale by more than
+    SETTLED_WIDTH gets a new random state, until no such face is left.  A
+    face whose roundings are all determined has width 0; one whose only
+    ambiguity is a feature at rounding noise next to zero (e.g. the
+    tangential jump at a slip wall) has a width far below SETTLED_WIDTH."""
     U = U.copy()
-    n = om.n
-    parent = np.arange(n)
-    pin = np.zeros(n, int)  # 0 free, 1 no momentum (wall), 2 free stream
-
-    def find(a):
-        while parent[a] != a:
-            parent[a] = parent[parent[a]]
-            a = parent[a]
-        return a
-
     for _ in range(max_iter):
-        _, _, det = om.closure_scale_intervals(U, theta)
-        changed = False
-        for c, k in zip(*np.nonzero(~det)):
-            m, rc = om.nbr[c, k], find(c)
-            if m >= 0:
-                rm = find(m)
-                if rc == rm:
-                    continue
-                parent[rm] = rc
-                pin[rc] = max(pin[rc], pin[rm])
-            elif m == orc.WALL and pin[rc] < 1:
-                pin[rc] = 1
-            elif m == orc.FARFIELD and pin[rc] < 2:
-                pin[rc] = 2
-            else:
-                continue
-            changed = True
-        if not changed:
+        lo, hi, _ = om.closure_scale_intervals(U, theta)
+        bad = np.unique(np.nonzero(hi - lo > SETTLED_WIDTH)[0])
+        if bad.size == 0:
             return U
-        roots = np.array([find(a) for a in range(n)])
-        for r in np.unique(roots):
-            st = om.uinf.copy() if pin[r] == 2 else U[r].copy()
-            if pin[r] == 1:
-                st[1:3] = 0.0
-            U[roots == r] = st
-    raise RuntimeError("undetermined faces did not settle")
+        U[bad] = random_states(rng, bad.size)
+    raise RuntimeError("ambiguous faces did not settle")
 
 
 def test_closure_gradient_matches_oracle(orc):
     # channel with walls and far field: ghost faces take part too
     mi = W.channel_bump(36, 14, seed=12)
-    prim = (1.0, 0.0, 0.0, 1.0)  # free stream at rest (see settle_undetermined_faces)
+    prim = W.freestream(0.5)
     uinf = W.conserved(*prim)
     rng = np.random.default_rng(7)
-    # cell states drawn independently: the features are O(1), not cancelling jumps
-    n = mi.n_tri
-    U0 = W.conserved(rng.uniform(0.5, 2.0, n), rng.uniform(-0.5, 0.5, n),
-                     rng.uniform(-0.5, 0.5, n), rng.uniform(0.5, 2.0, n))
-    U0 = U0.astype(np.float32).astype(np.float64)
     th, th64 = make_theta(8, scale=0.4)
     om = orc.Mesh(mi.xy, mi.tri, None, mi.bnd, 0, uinf)
-    U0 = settle_undetermined_faces(orc, om, U0, th64)
+    U0 = redraw_ambiguous_cells(om, random_states(rng, mi.n_tri), th64, rng)
+    lo_s, hi_s, det = om.closure_scale_intervals(U0, th64)
+    assert (hi_s - lo_s).max() <= SETTLED_WIDTH and det.mean() > 0.5
     Ut = (U0 + 0.02 * rng.normal(size=U0.shape)).astype(np.float32).astype(np.float64)
-    _, _, det = om.closure_scale_intervals(U0, th64)
-    inner = om.nbr >= 0
-    active = det.copy()  # faces whose scale matters: determined, or not inert
-    active[inner] &= ~(U0[om.nbr[inner]] == U0[np.nonzero(inner)[0]]).all(-1)
-    assert active.mean() > 0.5, active.mean()
     dt, w = 2e-3, np.array([1.0, 0.5, 0.5, 2.0])
     g = B.Mesh.from_input(mi, "f32")
     g.set_freestream(*prim)

@@ -711,7 +711,7 @@ def test_closure_scale_interval_covers_sampled_roundings(orc):
             x = _bf16(np.maximum(f + e * rng.uniform(-1, 1, 8), 0.0))
             a = b1 + W1 @ x
             mag = np.abs(b1) + np.abs(W1) @ x
-            h1 = _bf16(np.maximum(a + 10.0 / 2 ** 23 * mag * rng.uniform(-1, 1, 32), 0.0))
+            h1 = _bf16(np.maximum(a + 16.0 / 2 ** 23 * mag * rng.uniform(-1, 1, 32), 0.0))
             a2 = th[1312:1344] + th[288:1312].reshape(32, 32) @ h1
             z = th[1376] + th[1344:1376] @ np.maximum(a2, 0.0)
             s = 0.2 + 1.3 / (1.0 + math.exp(-z))
