@@ -237,7 +237,7 @@ def choose_variant(m, U, variant, scheme="fe"):
         m.set_variant(variant)
         return {"variant": variant, "autotuned": False}
     best, us = m.autotune(U, scheme=scheme)
-    return {"variant": best, "tile": m.tiling()[1] if best == 6 else None, "autotuned": True,
+    return {"variant": best, "tile": m.tiling()[1] if best in (6, 7) else None, "autotuned": True,
             "us_per_step_by_variant": us}
 
 
@@ -323,7 +323,7 @@ def run_ours(args):
         tune = {"blocking": 2, "tile": args.tile, "staged": args.staged}
     else:
         tune = choose_variant(m, U0dev, args.variant, args.scheme)
-        if args.variant == 6:
+        if args.variant in (6, 7):
             m.set_blocking(1, args.tile)
             tune["tile"] = args.tile
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -349,7 +349,8 @@ def run_ours(args):
         algo = VERTEX_BYTES if args.geometry == "vertex" else ALGO_BYTES[prec]
         kbytes = algo + (COMP_BYTES if comp else 0)
         kfun = ("k_step_closure" if args.closure else
-                {5: "k_step_tma", 6: "k_step_tile"}.get(tune["variant"], "k_step"))
+                {5: "k_step_tma", 6: "k_step_tile", 7: "k_step_tile_faces"}.get(tune["variant"],
+                                                                               "k_step"))
         kname = (f"{kfun}<{'float' if prec == 'f32' else 'double'}, "
                  f"{'RK2' if stages == 2 else 'FE'}, "
                  f"{'compensated' if comp else 'plain'}, shape {tune['variant']}"

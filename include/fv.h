@@ -192,18 +192,24 @@ int fv_mesh_set_remainder(fv_mesh* mesh, void* lo);
  * whose states and primitive variables, with those of the tile's neighbour
  * ring, sit in shared memory, so each primitive is formed once per cell (the
  * tile arrays are built on the host at the next device call; FV_EINVAL from
- * fv_step if a tile with its ring does not fit in shared memory).  All give
- * bitwise identical results; only speed differs.  FV_EINVAL outside 0..6. */
+ * fv_step if a tile with its ring does not fit in shared memory); 7 the tile
+ * shape evaluating each face once: the cell that owns a face writes its flux
+ * to its own slot and the exact negation to the slot of the cell across (the
+ * face fluxes are antisymmetric bit for bit), then every cell adds its three
+ * slots -- half the face arithmetic, for three flux records per tile cell of
+ * shared memory (forward Euler and RK2; the residual runs as shape 0; not
+ * with FV_GEOM_VERTEX).  All give bitwise identical results; only speed
+ * differs.  FV_EINVAL outside 0..7. */
 int fv_mesh_set_variant(fv_mesh* mesh, int32_t variant);
 
 /* Times every step-kernel shape on this mesh (a few steps each on a device
  * copy of U with a negligible fixed dt; U itself is not changed), keeps the
  * fastest for later fv_step calls and reports it in *best (nullable);
- * us_per_step (nullable, host, [7]) receives the measured microseconds per
- * step of each shape (infinity for shape 6 when its tiles do not fit).
- * Shape 6 is timed with tiles of 512, 768, 1024 and 2048 cells and reported at its
- * best; when it wins, that tile size is kept (the tile size is shared with
- * fv_mesh_set_blocking).  Allocates and frees one state-sized device buffer
+ * us_per_step (nullable, host, [8]) receives the measured microseconds per
+ * step of each shape (infinity for a tiled shape when its tiles do not fit).
+ * Shapes 6 and 7 are timed with tiles of 512, 768, 1024 and 2048 cells (and
+ * sizes that fill whole waves) and reported at their best; when one wins, its
+ * tile size is kept (the tile size is shared with fv_mesh_set_blocking).  Allocates and frees one state-sized device buffer
  * and synchronises the stream. */
 int fv_mesh_autotune(fv_mesh* mesh, const void* U, int32_t scheme, void* stream, int32_t* best,
                      double* us_per_step);
@@ -223,7 +229,7 @@ int fv_mesh_set_wait_limit(fv_mesh* mesh, uint32_t polls);
  * fall below the one-sided speeds in strong expansions, where the first-order
  * update then loses positivity (the corner of the Mach 3 forward-facing step
  * on fine meshes); the maximum keeps it positive under the same CFL bound.
- * With FV_WAVE_MAX the step runs shape 0, 1 or 6 (shapes 2-5 run as 1);
+ * With FV_WAVE_MAX the step runs shape 0, 1, 6 or 7 (shapes 2-5 run as 1);
  * fv_step returns FV_EINVAL with a closure or two steps per launch, and
  * fv_batch_create with such a mesh.  FV_EINVAL for an unknown mode. */
 int fv_mesh_set_wave_speed(fv_mesh* mesh, int32_t mode);

@@ -16,7 +16,7 @@ import numpy as np
 from . import build as _build
 
 FV_OK, FV_EINVAL, FV_ENOMEM, FV_ECUDA, FV_ENONFINITE, FV_ETIMEOUT, FV_ESTATE, FV_EINDEX = range(8)
-N_VARIANTS = 7  # step-kernel shapes (fv_mesh_set_variant)
+N_VARIANTS = 8  # step-kernel shapes (fv_mesh_set_variant)
 FV_F32, FV_F64 = 0, 1
 FV_BC_NONE, FV_BC_WALL, FV_BC_FARFIELD, FV_BC_EXTRAP = 0, 1, 2, 3
 ORDERS = {"identity": 0, "shuffle": 1, "rcm": 2, "hilbert": 3, "am1": 4}

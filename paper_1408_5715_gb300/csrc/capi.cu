@@ -224,7 +224,8 @@ namespace {
 
 // Tiles and halos of the two-step update, built on the host for the current
 // numbering and tile size and copied to the device.
-bool uses_tiles(const fv_mesh* m) { return m->blocking == 2 || m->variant == fv::kTileVariant; }
+bool tiled_shape(int v) { return v == fv::kTileVariant || v == fv::kFaceTileVariant; }
+bool uses_tiles(const fv_mesh* m) { return m->blocking == 2 || tiled_shape(m->variant); }
 
 void ensure_tiles(fv_mesh* m, cudaStream_t s) {
   if (!uses_tiles(m) || m->h.n == 0 ||
@@ -236,7 +237,8 @@ void ensure_tiles(fv_mesh* m, cudaStream_t s) {
   fv::TileVertices V;
   if (m->vertex_tiles()) {
     V = fv::build_tile_vertices(m->h, m->pair_tile);
-    for (int64_t c = 0; c < m->h.n; ++c) L.cell_ln[2 * c + 1] |= (uint32_t)V.v0[c] << 16;
+    for (int64_t c = 0; c < m->h.n; ++c)  // node 0 replaces the reverse-face bits
+      L.cell_ln[2 * c + 1] = (L.cell_ln[2 * c + 1] & 0xFFFFu) | ((uint32_t)V.v0[c] << 16);
     const size_t ncells = (size_t)m->h.n;
     FV_CUDA(cudaMalloc((void**)&m->d_cell_vl, ncells * sizeof(unsigned)));
     FV_CUDA(cudaMalloc((void**)&m->d_inv_vol, ncells * sizeof(float)));
@@ -281,6 +283,13 @@ void ensure_tiles(fv_mesh* m, cudaStream_t s) {
 // Shared memory of the one-step tile kernel of this mesh.
 size_t tile_smem(const fv_mesh* m) {
   return fv::tile_smem_bytes(m->f64(), m->p_t1_cap, m->tiles_vertex ? m->p_v_cap : 0);
+}
+
+// ... and of the step kernel of the mesh's tiled shape (6 or 7)
+size_t step_tile_smem(const fv_mesh* m) {
+  return m->variant == fv::kFaceTileVariant
+             ? fv::tile_faces_smem_bytes(m->f64(), m->p_t1_cap, m->tiles_built)
+             : tile_smem(m);
 }
 
 // Shared memory a tiled kernel of this mesh needs, checked against the device.
@@ -457,8 +466,7 @@ void enqueue_steps(fv_mesh* m, void* U, int64_t j0, int64_t count, double cfl, d
                    int32_t scheme, cudaStream_t s, const fv_closure* cl = nullptr,
                    bool lo_alt = false) {
   fv::LoopScalars* sc = m->d_scal;
-  if (!cl && m->variant == fv::kTileVariant && count > 0)
-    check_tile_smem(m, tile_smem(m));
+  if (!cl && tiled_shape(m->variant) && count > 0) check_tile_smem(m, step_tile_smem(m));
   for (int64_t j = j0; j < j0 + count; ++j) {
     fv::StepArgs a = base_args(m);
     a.bmin_read = &sc->bmin[j % 3];
@@ -729,6 +737,8 @@ int fv_mesh_set_variant(fv_mesh* mesh, int32_t variant) {
   return guarded([&] {
     check_mesh(mesh);
     if (variant < 0 || variant >= fv::kStepVariants) invalid("unknown step-kernel variant");
+    if (variant == fv::kFaceTileVariant && mesh->vertex_tiles())
+      invalid("normals from node coordinates run the tile shape 6");
     mesh->variant = variant;
     mesh->drop_graph();
   });
@@ -885,7 +895,8 @@ int fv_mesh_autotune(fv_mesh* mesh, const void* U, int32_t scheme, void* stream,
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     double times[fv::kStepVariants];
     const int keep = mesh->variant, keep_tile = mesh->pair_tile;
-    int best_tile = keep_tile;
+    int best_tile[fv::kStepVariants];
+    for (int v = 0; v < fv::kStepVariants; ++v) best_tile[v] = keep_tile;
     try {
       FV_CUDA(cudaEventCreate(&e0));
       FV_CUDA(cudaEventCreate(&e1));
@@ -907,26 +918,27 @@ int fv_mesh_autotune(fv_mesh* mesh, const void* U, int32_t scheme, void* stream,
       };
       for (int v = 0; v < fv::kStepVariants; ++v) {
         mesh->variant = v;
-        if (v != fv::kTileVariant) {
+        if (!tiled_shape(v)) {
           // vertex geometry is a layout of the tile shape
           times[v] = mesh->vertex_tiles() ? INFINITY : time_shape();
           continue;
         }
-        // the tile shape at each tile size; tiles that do not fit (a
+        // the tiled shapes at each tile size; tiles that do not fit (a
         // long-band order) leave that size out
         times[v] = INFINITY;
+        if (v == fv::kFaceTileVariant && mesh->vertex_tiles()) continue;
         for (int tile : tile_candidates(n)) {
           mesh->pair_tile = tile;
           try {
             ensure_tiles(mesh, s);
-            check_tile_smem(mesh, tile_smem(mesh));
+            check_tile_smem(mesh, step_tile_smem(mesh));
           } catch (const fv::Error&) {
             continue;
           }
           const double us = time_shape();
           if (us < times[v]) {
             times[v] = us;
-            best_tile = tile;
+            best_tile[v] = tile;
           }
         }
       }
@@ -949,7 +961,7 @@ int fv_mesh_autotune(fv_mesh* mesh, const void* U, int32_t scheme, void* stream,
     // the tile size of the tiled shapes: the fastest for shape 6 when it wins
     // (two steps per launch keep their own tile size: the two-step kernel
     // takes the standard sizes only)
-    mesh->pair_tile = b == fv::kTileVariant && mesh->blocking == 1 ? best_tile : keep_tile;
+    mesh->pair_tile = tiled_shape(b) && mesh->blocking == 1 ? best_tile[b] : keep_tile;
     mesh->drop_graph();
     if (best) *best = b;
     if (us_per_step)

@@ -196,10 +196,17 @@ __device__ __forceinline__ rec_t<R> neighbour_state(const rec_t<R>& UL, int nb, 
 // interface averages |u-bar_n| + c-bar; kWaveMax the larger one-sided speed
 // max(|u_nL| + c_L, |u_nR| + c_R) (Rusanov), which keeps the first-order
 // update positive in strong expansions.  Both are symmetric in L <-> R.
+//
+// Each term is written so that the two cells of a face compute exact
+// opposites (the neighbour sees L and R swapped and the normal negated):
+// every product involves one side only, rounding is symmetric in sign and the
+// sums of the two sides' terms commute.  So the face flux is antisymmetric
+// bit for bit -- discrete conservation is exact -- and a kernel may evaluate a
+// face once and hand its negation to the cell across (k_step_tile_faces).
 template <typename R, bool SCALED, int WAVE = kWaveAverage>
-__device__ __forceinline__ void face_flux_acc(const rec_t<R>& UL, const Prim<R>& L,
-                                              const rec_t<R>& UR, const Prim<R>& W, R nx, R ny,
-                                              R len, R s, R acc[4]) {
+__device__ __forceinline__ void face_flux_value(const rec_t<R>& UL, const Prim<R>& L,
+                                                const rec_t<R>& UR, const Prim<R>& W, R nx, R ny,
+                                                R len, R s, R X[4]) {
   const R qL = fma_(L.u, nx, mul(L.v, ny));
   const R qR = fma_(W.u, nx, mul(W.v, ny));
   // na = -|n| (wave speed), twice the dissipation coefficient of Eq. 5
@@ -209,13 +216,22 @@ __device__ __forceinline__ void face_flux_acc(const rec_t<R>& UL, const Prim<R>&
   else
     na = -fmax(fma_(len, L.c, fabs(qL)), fma_(len, W.c, fabs(qR)));
   if (SCALED) na = mul(s, na);
-  acc[0] = add(acc[0], fma_(na, sub(UR.x, UL.x), fma_(UL.x, qL, mul(UR.x, qR))));
-  acc[1] = add(acc[1], fma_(na, sub(UR.y, UL.y),
-                            add(fma_(UL.y, qL, mul(L.p, nx)), fma_(UR.y, qR, mul(W.p, nx)))));
-  acc[2] = add(acc[2], fma_(na, sub(UR.z, UL.z),
-                            add(fma_(UL.z, qL, mul(L.p, ny)), fma_(UR.z, qR, mul(W.p, ny)))));
-  acc[3] = add(acc[3], fma_(na, sub(UR.w, UL.w),
-                            fma_(add(UL.w, L.p), qL, mul(add(UR.w, W.p), qR))));
+  X[0] = fma_(na, sub(UR.x, UL.x), add(mul(UL.x, qL), mul(UR.x, qR)));
+  X[1] = fma_(na, sub(UR.y, UL.y),
+              add(fma_(UL.y, qL, mul(L.p, nx)), fma_(UR.y, qR, mul(W.p, nx))));
+  X[2] = fma_(na, sub(UR.z, UL.z),
+              add(fma_(UL.z, qL, mul(L.p, ny)), fma_(UR.z, qR, mul(W.p, ny))));
+  X[3] = fma_(na, sub(UR.w, UL.w), add(mul(add(UL.w, L.p), qL), mul(add(UR.w, W.p), qR)));
+}
+
+template <typename R, bool SCALED, int WAVE = kWaveAverage>
+__device__ __forceinline__ void face_flux_acc(const rec_t<R>& UL, const Prim<R>& L,
+                                              const rec_t<R>& UR, const Prim<R>& W, R nx, R ny,
+                                              R len, R s, R acc[4]) {
+  R X[4];
+  face_flux_value<R, SCALED, WAVE>(UL, L, UR, W, nx, ny, len, s, X);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) acc[q] = add(acc[q], X[q]);
 }
 
 template <typename R, int WAVE = kWaveAverage>

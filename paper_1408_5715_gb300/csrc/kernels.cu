@@ -384,7 +384,9 @@ cudaError_t launch_step(bool f64, int mode, int variant, const StepArgs& a, cuda
   if (variant == 5 && a.wave == kWaveMax) variant = 1;  // the staged shape has the averages only
   if (variant == 5 && mode != kModeResidual && a.n > 0) return launch_step_tma(f64, mode, a, s);
   if (variant == kTileVariant && a.cell_ln) return launch_step_tile(f64, mode, a, s);
-  if (variant == 5 || variant == kTileVariant) variant = 0;
+  if (variant == kFaceTileVariant && a.cell_ln && mode != kModeResidual)
+    return launch_step_tile_faces(f64, mode, a, s);
+  if (variant == 5 || variant == kTileVariant || variant == kFaceTileVariant) variant = 0;
   if (f64) return launch_step_t<double, false>(mode, variant, a, s);
   return a.lo ? launch_step_t<float, true>(mode, variant, a, s)
               : launch_step_t<float, false>(mode, variant, a, s);

@@ -172,8 +172,9 @@ cudaError_t launch_pack_closure(const float* theta, unsigned* w1, unsigned* w2, 
 // registers, 3 and 4 one thread per cell capped at 40 and 32 registers,
 // 5 persistent grid with TMA-staged cell records (tma_step.cu), 6 tiles with
 // their first halo ring and primitives in shared memory (tile_step.cu).
-constexpr int kStepVariants = 7;
+constexpr int kStepVariants = 8;
 constexpr int kTileVariant = 6;
+constexpr int kFaceTileVariant = 7;
 // shared memory of the tile variant: state and primitives of tile + halo
 inline size_t tile_smem_bytes(bool f64, int t1_cap, int v_cap = 0) {
   return (size_t)t1_cap * 2 * (f64 ? 32 : 16) + (size_t)v_cap * 8;
@@ -182,6 +183,12 @@ cudaError_t launch_restrict_mean(bool fine_f64, bool coarse_f64, const void* Uf,
                                  const int* fine_of, int64_t n_coarse, int kids, void* Uc,
                                  cudaStream_t s);
 cudaError_t launch_step_tile(bool f64, int mode, const StepArgs& a, cudaStream_t s);
+// shape 7: the tile shape with each face evaluated once (its states and
+// primitives as shape 6, plus three face-flux records per tile cell)
+inline size_t tile_faces_smem_bytes(bool f64, int t1_cap, int tile) {
+  return tile_smem_bytes(f64, t1_cap) + (size_t)3 * tile * (f64 ? 32 : 16);
+}
+cudaError_t launch_step_tile_faces(bool f64, int mode, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_batch_step_tile(bool f64, int mode, const BatchArgs& b, cudaStream_t s);
 // Library-owned per-cell arrays are allocated in whole tiles of this many
 // cells (the TMA-staged variant copies whole tiles of them).

@@ -165,6 +165,126 @@ __global__ void __launch_bounds__(THREADS, sizeof(R) == 4 ? 1280 / THREADS : 1)
   }
 }
 
+// Shape 7: the tile shape with each face evaluated once.  Phase 1: every
+// tile cell evaluates the faces it owns -- faces to the ring, ghost faces, and
+// faces to a tile cell of higher local id (a face of a cell to itself across
+// a periodic seam from its lower face index) -- and writes the flux value to
+// its own slot sF[3e + k] and its negation to the slot of the cell across,
+// whose pointing-back face the tile record gives (tiles.cpp).  The face
+// fluxes are exactly antisymmetric (face_flux_value), so every slot holds the
+// bits the cell would compute itself.  Phase 2: every tile cell adds its three
+// slots in face order and finishes as the other shapes do: the same bits, with
+// about half the face arithmetic.  It pays where the arithmetic is the
+// bottleneck (FP64 on GB300); sF costs 3 records per tile cell of shared
+// memory.
+template <typename R, int MODE, bool COMP, int THREADS, int KMAX, int WAVE>
+__global__ void __launch_bounds__(THREADS, 1) k_step_tile_faces(StepArgs a) {
+  chain_entry();
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  rec_t<R>* sU = reinterpret_cast<rec_t<R>*>(smem_raw);  // [t1_cap] states
+  rec_t<R>* sP = sU + a.t1_cap;                            // [t1_cap] (u, v, p, c)
+  rec_t<R>* sF = sP + a.t1_cap;                            // [3 tile] face flux values
+  const rec_t<R>* __restrict__ U = static_cast<const rec_t<R>*>(a.U);
+  const rec_t<R>* __restrict__ geom = static_cast<const rec_t<R>*>(a.geom);
+  rec_t<R>* out = static_cast<rec_t<R>*>(a.out);
+  const int t0 = blockIdx.x * a.tile;  // cell ids are 32-bit
+  const int nt = min(a.tile, (int)a.n - t0);
+  const int hs = __ldg(a.tile_info + 2 * blockIdx.x);
+  const int h1 = __ldg(a.tile_info + 2 * blockIdx.x + 1);
+  __shared__ double s_t, s_dt;
+  if (threadIdx.x == 0 && MODE != kModeResidual) block_dt(a, s_t, s_dt);
+  stage_states<R, THREADS, kStageBatch<R, KMAX>>(U, t0, nt, h1, a.halo_id + hs, sU, sP, a.n,
+                                                 a.err);
+  __syncthreads();
+  const R* uinf = far_field<R>(a);
+  // phase 1: the faces each tile cell owns
+#pragma unroll
+  for (int k = 0; k < KMAX; ++k) {
+    const int e = threadIdx.x + k * THREADS;
+    if (e < nt) {
+      const int i = t0 + e;
+      const uint2 ln = __ldg(a.cell_ln + i);
+      const rec_t<R> g0 = Rec<R>::ld(geom + 2 * i), g1 = Rec<R>::ld(geom + 2 * i + 1);
+      const rec_t<R> UL = sU[e];
+      const Prim<R> L = rec_prim<R>(sP[e]);
+      const unsigned v[3] = {ln.x & 0xffffu, ln.x >> 16, ln.y & 0xffffu};
+      const R nx[3] = {g0.x, g0.z, g1.x}, ny[3] = {g0.y, g0.w, g1.y};
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const unsigned kv = (ln.y >> (16 + 2 * q)) & 3u;
+        const bool inner = v[q] < (unsigned)nt;
+        if (inner && (v[q] < (unsigned)e || (v[q] == (unsigned)e && kv < (unsigned)q))) continue;
+        rec_t<R> UR;
+        Prim<R> W;
+        if (v[q] < kGhostCodes) {
+          if (index_ok(v[q], nt + h1, a.err)) {
+            UR = sU[v[q]];
+            W = rec_prim<R>(sP[v[q]]);
+          } else {
+            UR = UL;
+            W = L;
+          }
+        } else {
+          UR = ghost<R>((int)v[q] - 0x10000, UL, nx[q], ny[q], uinf);
+          W = primitive<R>(UR);
+        }
+        R X[4];
+        face_flux_value<R, false, WAVE>(UL, L, UR, W, nx[q], ny[q], face_len<R>(nx[q], ny[q]),
+                                        R(1), X);
+        sF[3 * e + q] = Rec<R>::make(X[0], X[1], X[2], X[3]);
+        if (inner && index_ok(v[q], nt, a.err))
+          sF[3 * v[q] + kv] = Rec<R>::make(-X[0], -X[1], -X[2], -X[3]);
+      }
+    }
+  }
+  __syncthreads();
+  const double t = MODE != kModeResidual ? s_t : 0.0, dt = MODE != kModeResidual ? s_dt : 0.0;
+  const R dtR = R(dt);
+  R bmin = R(INFINITY);
+  bool ok = true;
+  // phase 2: the three face values in face order, then the cell's update
+#pragma unroll
+  for (int k = 0; k < KMAX; ++k) {
+    const int e = threadIdx.x + k * THREADS;
+    if (e < nt) {
+      const int i = t0 + e;
+      CellIn<R> c;
+      c.g0 = Rec<R>::ld(geom + 2 * i);
+      c.g1 = Rec<R>::ld(geom + 2 * i + 1);
+      c.U = sU[e];
+      if (MODE == kModeRK2b) c.base = static_cast<const rec_t<R>*>(a.Ubase)[i];
+      if (COMP && MODE != kModeResidual) c.lo = a.lo[i];
+      if (COMP && MODE == kModeRK2b) c.lo_stage = a.lo_stage[i];
+      R acc[4] = {R(0), R(0), R(0), R(0)};
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const rec_t<R> X = sF[3 * e + q];
+        acc[0] = add(acc[0], X.x);
+        acc[1] = add(acc[1], X.y);
+        acc[2] = add(acc[2], X.z);
+        acc[3] = add(acc[3], X.w);
+      }
+      // the perimeter (FP32 forms 2V/P from it; FP64 stores 2V/P)
+      R perim = R(0);
+      if constexpr (sizeof(R) == 4)
+        perim = add(add(face_len<R>(c.g0.x, c.g0.y), face_len<R>(c.g0.z, c.g0.w)),
+                    face_len<R>(c.g1.x, c.g1.y));
+      finish_cell<R, MODE, COMP>(a, out, i, c, acc, perim, dtR, bmin, ok);
+    }
+  }
+  if (MODE == kModeFE || MODE == kModeRK2b) {
+    if (!ok) atomicOr(a.err, 1);
+    const double m = (double)block_min<R>(bmin);
+    if (threadIdx.x == 0) {
+      atomicMin(a.bmin_write, (unsigned long long)__double_as_longlong(m));
+      if (blockIdx.x == 0) {
+        *a.t_write = t + dt;
+        *a.bmin_reset = kInfBits;
+      }
+    }
+  }
+}
+
 // Many meshes: each block is one tile of one mesh (tiles never span meshes)
 // and uses that mesh's dt, time, far field and CFL-minimum slot; the mesh's
 // first tile advances its time and clears its next slot.
@@ -268,6 +388,37 @@ cudaError_t launch_tile_t(const StepArgs& a, cudaStream_t s) {
   return launch_chained(k, (unsigned)tiles, THREADS, smem, s, a.chained, a);
 }
 
+template <typename R, int MODE, bool COMP, int THREADS, int KMAX>
+cudaError_t launch_faces_t(const StepArgs& a, cudaStream_t s) {
+  auto k = a.wave == kWaveMax ? k_step_tile_faces<R, MODE, COMP, THREADS, KMAX, kWaveMax>
+                              : k_step_tile_faces<R, MODE, COMP, THREADS, KMAX, kWaveAverage>;
+  const size_t smem = tile_faces_smem_bytes(sizeof(R) == 8, a.t1_cap, a.tile);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t tiles = (a.n + a.tile - 1) / a.tile;
+  return launch_chained(k, (unsigned)tiles, THREADS, smem, s, a.chained, a);
+}
+
+template <typename R, int MODE, bool COMP>
+cudaError_t launch_faces_size(const StepArgs& a, cudaStream_t s) {
+  if (a.tile < 1 || a.tile > kMaxTileCells) return cudaErrorInvalidValue;
+  if (a.tile <= 512) return launch_faces_t<R, MODE, COMP, 256, 2>(a, s);
+  if (a.tile <= 768) return launch_faces_t<R, MODE, COMP, 256, 3>(a, s);
+  if (a.tile <= 1024) return launch_faces_t<R, MODE, COMP, 256, 4>(a, s);
+  return launch_faces_t<R, MODE, COMP, 512, 4>(a, s);
+}
+
+template <typename R, bool COMP>
+cudaError_t launch_faces_mode(int mode, const StepArgs& a, cudaStream_t s) {
+  switch (mode) {
+    case kModeFE: return launch_faces_size<R, kModeFE, COMP>(a, s);
+    case kModeRK2a: return launch_faces_size<R, kModeRK2a, COMP>(a, s);
+    case kModeRK2b: return launch_faces_size<R, kModeRK2b, COMP>(a, s);
+    case kModeResidual: return launch_faces_size<R, kModeResidual, false>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 // Any tile size up to 2048 cells: the block shape whose KMAX x THREADS cells
 // cover it (the cells of a tile beyond nt are skipped).
 template <typename R, int MODE, bool COMP, bool VTX>
@@ -298,6 +449,14 @@ cudaError_t launch_batch_step_tile(bool f64, int mode, const BatchArgs& b, cudaS
   if (f64) return launch_tile_batch_mode<double, false>(mode, b, s);
   if (b.s.lo) return launch_tile_batch_mode<float, true>(mode, b, s);
   return launch_tile_batch_mode<float, false>(mode, b, s);
+}
+
+cudaError_t launch_step_tile_faces(bool f64, int mode, const StepArgs& a, cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  if (!a.cell_ln || !a.tile_info || !a.halo_id || a.tile_vq) return cudaErrorInvalidValue;
+  if (f64) return launch_faces_mode<double, false>(mode, a, s);
+  if (a.lo) return launch_faces_mode<float, true>(mode, a, s);
+  return launch_faces_mode<float, false>(mode, a, s);
 }
 
 cudaError_t launch_step_tile(bool f64, int mode, const StepArgs& a, cudaStream_t s) {

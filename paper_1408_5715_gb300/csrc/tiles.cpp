@@ -16,6 +16,10 @@
 // id.  Neighbours are stored as 16-bit local ids; ghost faces keep their
 // boundary code c < 0 as 0x10000 + c (0xFFFF wall, 0xFFFE far field, 0xFFFD
 // extrapolation), so a tile with its halos holds at most 0xFFFD cells.
+// Record of a tile cell: x = ids of faces 0 and 1, low half of y = id of
+// face 2; bits 16 + 2k of y hold, for a face k whose neighbour is a cell of
+// the same tile, the face of that neighbour that points back (the tile
+// kernel that evaluates each face once writes the negated flux there).
 #include <algorithm>
 
 #include "fv_internal.h"
@@ -84,16 +88,29 @@ PairTiles build_pair_tiles(const HostMesh& m, int32_t tile) {
       throw Error{FV_EINVAL, "tile halos too large for 32-bit offsets"};
     L.tile_info[2 * b] = (int32_t)hs;
     L.tile_info[2 * b + 1] = (int32_t)h1.size();
-    auto pack = [&](int64_t c, uint32_t* out) {
+    auto pack = [&](int64_t c, uint32_t* out, bool tile_cell) {
       const uint32_t a0 = local_code(m.nbr[3 * c], t0, t1, nt, halo_pos, stamp, b);
       const uint32_t a1 = local_code(m.nbr[3 * c + 1], t0, t1, nt, halo_pos, stamp, b);
       const uint32_t a2 = local_code(m.nbr[3 * c + 2], t0, t1, nt, halo_pos, stamp, b);
       out[0] = a0 | (a1 << 16);
       out[1] = a2;
+      if (!tile_cell) return;
+      for (int k = 0; k < 3; ++k) {
+        const int32_t x = m.nbr[3 * c + k];
+        if (x < t0 || x >= t1) continue;
+        int kx = -1;
+        for (int q = 0; q < 3; ++q)
+          if (m.nbr[3 * (int64_t)x + q] == (int32_t)c && !(x == c && q == k) &&
+              m.nrm[6 * (int64_t)x + 2 * q] == -m.nrm[6 * c + 2 * k] &&
+              m.nrm[6 * (int64_t)x + 2 * q + 1] == -m.nrm[6 * c + 2 * k + 1])
+            kx = q;
+        if (kx < 0) throw Error{FV_EINVAL, "tile construction: the two sides of a face differ"};
+        out[1] |= (uint32_t)kx << (16 + 2 * k);
+      }
     };
-    for (int64_t c = t0; c < t1; ++c) pack(c, &L.cell_ln[2 * c]);
+    for (int64_t c = t0; c < t1; ++c) pack(c, &L.cell_ln[2 * c], true);
     L.halo_ln.resize(2 * (hs + h1.size() + h2.size()), 0u);
-    for (size_t j = 0; j < h1.size(); ++j) pack(h1[j], &L.halo_ln[2 * (hs + j)]);
+    for (size_t j = 0; j < h1.size(); ++j) pack(h1[j], &L.halo_ln[2 * (hs + j)], false);
     L.halo_id.insert(L.halo_id.end(), h1.begin(), h1.end());
     L.halo_id.insert(L.halo_id.end(), h2.begin(), h2.end());
     L.e_cap = std::max<int32_t>(L.e_cap, (int32_t)e_size);

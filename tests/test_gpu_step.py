@@ -136,7 +136,7 @@ def test_am1_ordered_channel_fp64_parity_on_every_shape(orc):
     assert sorted(perm) == list(range(mi.n_tri))
     bw, _ = g64.diagnostics()
     assert bw < mi.n_tri // 4  # a banded order, unlike the shuffled input
-    for variant in range(7):
+    for variant in range(8):
         g64.set_variant(variant)
         U = dev(U0[perm], torch.float64)
         t = g64.step(U, 80, 0.4)
@@ -294,13 +294,13 @@ def test_kernel_shapes_give_identical_results(big_square, prec, scheme):
     mi, U0 = big_square
     dt_ = torch.float64 if prec == "f64" else torch.float32
     outs, ts = [], []
-    shapes = [(v, 1024) for v in range(B.N_VARIANTS)] + [(6, 512), (6, 2048)]
+    shapes = [(v, 1024) for v in range(B.N_VARIANTS)] + [(6, 512), (6, 2048), (7, 512)]
     for v, tile in shapes:
         g = B.Mesh.from_input(mi, prec)
         g.renumber("hilbert")
         g.set_variant(v)
-        if v == 6:
-            g.set_blocking(1, tile)  # tile size of the shared-memory shape
+        if v in (6, 7):
+            g.set_blocking(1, tile)  # tile size of the shared-memory shapes
         U = dev(U0, dt_)
         ts.append(g.step(U, 30, 0.4, scheme=scheme))
         outs.append(U)
