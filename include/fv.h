@@ -207,8 +207,8 @@ int fv_mesh_set_variant(fv_mesh* mesh, int32_t variant);
  * fastest for later fv_step calls and reports it in *best (nullable);
  * us_per_step (nullable, host, [8]) receives the measured microseconds per
  * step of each shape (infinity for a tiled shape when its tiles do not fit).
- * Shapes 6 and 7 are timed with tiles of 512, 768, 1024 and 2048 cells (and
- * sizes that fill whole waves) and reported at their best; when one wins, its
+ * Shapes 6 and 7 are timed with tiles of 256, 384, 512, 768, 1024 and 2048
+ * cells (and sizes that fill whole waves) and reported at their best; when one wins, its
  * tile size is kept (the tile size is shared with fv_mesh_set_blocking).  Allocates and frees one state-sized device buffer
  * and synchronises the stream. */
 int fv_mesh_autotune(fv_mesh* mesh, const void* U, int32_t scheme, void* stream, int32_t* best,

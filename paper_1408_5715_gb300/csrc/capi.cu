@@ -129,6 +129,8 @@ struct fv_mesh {
   int* d_tile_info = nullptr;
   int* d_halo_id = nullptr;
   uint2* d_halo_ln = nullptr;
+  int* d_face_off = nullptr;   // shape 7: the faces each tile evaluates once
+  uint2* d_face_rec = nullptr;
   int p_e_cap = 0, p_t1_cap = 0;
   // normals from vertex coordinates (fv_mesh_set_geometry): tile nodes
   int geometry = FV_GEOM_STORED;
@@ -180,6 +182,8 @@ struct fv_mesh {
   }
 
   void free_tiles() {
+    dev_free(d_face_off);
+    dev_free(d_face_rec);
     dev_free(d_cell_ln);
     dev_free(d_tile_info);
     dev_free(d_halo_id);
@@ -227,13 +231,32 @@ namespace {
 bool tiled_shape(int v) { return v == fv::kTileVariant || v == fv::kFaceTileVariant; }
 bool uses_tiles(const fv_mesh* m) { return m->blocking == 2 || tiled_shape(m->variant); }
 
+// The faces each tile evaluates once (shape 7), uploaded when that shape
+// first runs on the current tiles.
+void upload_tile_faces(fv_mesh* m, const fv::PairTiles& L, cudaStream_t s) {
+  FV_CUDA(cudaMalloc((void**)&m->d_face_off, L.face_off.size() * sizeof(int32_t)));
+  FV_CUDA(cudaMalloc((void**)&m->d_face_rec, std::max<size_t>(L.face_rec.size(), 2) *
+                                                  sizeof(uint32_t)));
+  FV_CUDA(cudaMemcpyAsync(m->d_face_off, L.face_off.data(), L.face_off.size() * sizeof(int32_t),
+                          cudaMemcpyHostToDevice, s));
+  FV_CUDA(cudaMemcpyAsync(m->d_face_rec, L.face_rec.data(), L.face_rec.size() * sizeof(uint32_t),
+                          cudaMemcpyHostToDevice, s));
+  FV_CUDA(cudaStreamSynchronize(s));  // L is a staging buffer
+}
+
 void ensure_tiles(fv_mesh* m, cudaStream_t s) {
-  if (!uses_tiles(m) || m->h.n == 0 ||
-      (m->tiles_built == m->pair_tile && m->tiles_vertex == m->vertex_tiles()))
+  if (!uses_tiles(m) || m->h.n == 0) return;
+  if (m->tiles_built == m->pair_tile && m->tiles_vertex == m->vertex_tiles()) {
+    if (m->variant == fv::kFaceTileVariant && !m->d_face_rec) {
+      m->drop_graph();
+      upload_tile_faces(m, fv::build_pair_tiles(m->h, m->pair_tile), s);
+    }
     return;
+  }
   m->free_tiles();
   m->drop_graph();
   fv::PairTiles L = fv::build_pair_tiles(m->h, m->pair_tile);
+  if (m->variant == fv::kFaceTileVariant && !m->vertex_tiles()) upload_tile_faces(m, L, s);
   fv::TileVertices V;
   if (m->vertex_tiles()) {
     V = fv::build_tile_vertices(m->h, m->pair_tile);
@@ -308,7 +331,9 @@ void check_tile_smem(const fv_mesh* m, size_t smem) {
 // whole waves (w waves of b blocks per SM), which avoid a last, partly
 // filled wave.
 std::vector<int> tile_candidates(int64_t n) {
-  std::vector<int> t(std::begin(fv::kPairTiles), std::end(fv::kPairTiles));
+  // small tiles suit shape 7, whose face records take shared memory
+  std::vector<int> t = {256, 384};
+  t.insert(t.end(), std::begin(fv::kPairTiles), std::end(fv::kPairTiles));
   int dev = 0, sms = 0;
   FV_CUDA(cudaGetDevice(&dev));
   FV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -438,6 +463,8 @@ fv::StepArgs base_args(const fv_mesh* m) {
     a.halo_id = m->d_halo_id;
     a.tile = m->tiles_built;
     a.t1_cap = m->p_t1_cap;
+    a.tile_face_off = m->d_face_off;
+    a.tile_face = m->d_face_rec;
     if (m->tiles_vertex) {
       a.cell_vl = m->d_cell_vl;
       a.tile_voff = m->d_tile_voff;

@@ -96,6 +96,12 @@ struct PairTiles {
   std::vector<uint32_t> cell_ln;   // [2 n]
   int32_t e_cap = 0;   // max over tiles of tile + both halos
   int32_t t1_cap = 0;  // max over tiles of tile + first halo
+  // the faces each tile evaluates once (shape 7): tile b's are face_rec[2 f]
+  // for f in [face_off[b], face_off[b + 1]): x = e | q << 16 | kq << 18 (face q
+  // of tile cell e; kq the face of the cell across that points back, for a
+  // cell of the tile), y = the 16-bit local id across (ring or ghost code)
+  std::vector<int32_t> face_off;   // [n_tiles + 1]
+  std::vector<uint32_t> face_rec;  // [2 faces]
 };
 PairTiles build_pair_tiles(const HostMesh& m, int32_t tile);
 

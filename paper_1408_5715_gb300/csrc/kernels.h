@@ -80,6 +80,9 @@ struct StepArgs {
   const int* halo_id;
   int tile;
   int t1_cap;
+  // shape 7: each tile's faces evaluated once (tiles.cpp face_off / face_rec)
+  const int* tile_face_off;
+  const uint2* tile_face;
   // Vertex geometry of the tile variant (FP32; vertex_geom.cpp), or nullptr:
   // normals formed from grid coordinates of the tile's nodes and 1/V read
   // from inv_vol instead of the geom records.  tile_vq[2 tile_voff[b] ..]

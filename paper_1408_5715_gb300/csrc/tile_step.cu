@@ -165,12 +165,32 @@ __global__ void __launch_bounds__(THREADS, sizeof(R) == 4 ? 1280 / THREADS : 1)
   }
 }
 
-// Shape 7: the tile shape with each face evaluated once.  Phase 1: every
-// tile cell evaluates the faces it owns -- faces to the ring, ghost faces, and
-// faces to a tile cell of higher local id (a face of a cell to itself across
-// a periodic seam from its lower face index) -- and writes the flux value to
-// its own slot sF[3e + k] and its negation to the slot of the cell across,
-// whose pointing-back face the tile record gives (tiles.cpp).  The face
+// The normal of face q of cell i from its geometry record (one 16-byte load).
+template <typename R>
+__device__ __forceinline__ void face_normal(const rec_t<R>* __restrict__ geom, int i, unsigned q,
+                                            R& nx, R& ny);
+template <>
+__device__ __forceinline__ void face_normal<float>(const float4* __restrict__ geom, int i,
+                                                   unsigned q, float& nx, float& ny) {
+  const float4 g = __ldg(geom + 2 * i + (q == 2u));
+  nx = q == 1u ? g.z : g.x;
+  ny = q == 1u ? g.w : g.y;
+}
+template <>
+__device__ __forceinline__ void face_normal<double>(const dq4* __restrict__ geom, int i,
+                                                    unsigned q, double& nx, double& ny) {
+  // record 2i holds faces 0 and 1, record 2i + 1 face 2 first: 16-byte halves
+  const double2 g = __ldg(reinterpret_cast<const double2*>(geom + 2 * i + (q == 2u)) + (q == 1u));
+  nx = g.x;
+  ny = g.y;
+}
+
+// Shape 7: the tile shape with each face evaluated once.  Phase 1: the
+// threads share the tile's face list (tiles.cpp): every face of a tile cell
+// except those whose other side is a tile cell of lower local id (for a cell
+// bordering itself across a periodic seam, its lower face); each writes the
+// flux value to the slot sF[3e + q] of its cell and, across an inner face,
+// the negation to the slot of the face pointing back.  The face
 // fluxes are exactly antisymmetric (face_flux_value), so every slot holds the
 // bits the cell would compute itself.  Phase 2: every tile cell adds its three
 // slots in face order and finishes as the other shapes do: the same bits, with
@@ -197,45 +217,36 @@ __global__ void __launch_bounds__(THREADS, 1) k_step_tile_faces(StepArgs a) {
                                                  a.err);
   __syncthreads();
   const R* uinf = far_field<R>(a);
-  // phase 1: the faces each tile cell owns
-#pragma unroll
-  for (int k = 0; k < KMAX; ++k) {
-    const int e = threadIdx.x + k * THREADS;
-    if (e < nt) {
-      const int i = t0 + e;
-      const uint2 ln = __ldg(a.cell_ln + i);
-      const rec_t<R> g0 = Rec<R>::ld(geom + 2 * i), g1 = Rec<R>::ld(geom + 2 * i + 1);
-      const rec_t<R> UL = sU[e];
-      const Prim<R> L = rec_prim<R>(sP[e]);
-      const unsigned v[3] = {ln.x & 0xffffu, ln.x >> 16, ln.y & 0xffffu};
-      const R nx[3] = {g0.x, g0.z, g1.x}, ny[3] = {g0.y, g0.w, g1.y};
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        const unsigned kv = (ln.y >> (16 + 2 * q)) & 3u;
-        const bool inner = v[q] < (unsigned)nt;
-        if (inner && (v[q] < (unsigned)e || (v[q] == (unsigned)e && kv < (unsigned)q))) continue;
-        rec_t<R> UR;
-        Prim<R> W;
-        if (v[q] < kGhostCodes) {
-          if (index_ok(v[q], nt + h1, a.err)) {
-            UR = sU[v[q]];
-            W = rec_prim<R>(sP[v[q]]);
-          } else {
-            UR = UL;
-            W = L;
-          }
-        } else {
-          UR = ghost<R>((int)v[q] - 0x10000, UL, nx[q], ny[q], uinf);
-          W = primitive<R>(UR);
-        }
-        R X[4];
-        face_flux_value<R, false, WAVE>(UL, L, UR, W, nx[q], ny[q], face_len<R>(nx[q], ny[q]),
-                                        R(1), X);
-        sF[3 * e + q] = Rec<R>::make(X[0], X[1], X[2], X[3]);
-        if (inner && index_ok(v[q], nt, a.err))
-          sF[3 * v[q] + kv] = Rec<R>::make(-X[0], -X[1], -X[2], -X[3]);
+  // phase 1: the tile's faces, each once, spread evenly over the threads
+  const int f1 = __ldg(a.tile_face_off + blockIdx.x + 1);
+  for (int f = __ldg(a.tile_face_off + blockIdx.x) + threadIdx.x; f < f1; f += THREADS) {
+    const uint2 r = __ldg(a.tile_face + f);
+    const unsigned e = r.x & 0xffffu, q = (r.x >> 16) & 3u, kv = (r.x >> 18) & 3u, v = r.y;
+    if (!index_ok(e, nt, a.err)) continue;
+    const int i = t0 + (int)e;
+    R nx, ny;
+    face_normal<R>(geom, i, q, nx, ny);
+    const rec_t<R> UL = sU[e];
+    const Prim<R> L = rec_prim<R>(sP[e]);
+    const bool inner = v < (unsigned)nt;
+    rec_t<R> UR;
+    Prim<R> W;
+    if (v < kGhostCodes) {
+      if (index_ok(v, nt + h1, a.err)) {
+        UR = sU[v];
+        W = rec_prim<R>(sP[v]);
+      } else {
+        UR = UL;
+        W = L;
       }
+    } else {
+      UR = ghost<R>((int)v - 0x10000, UL, nx, ny, uinf);
+      W = primitive<R>(UR);
     }
+    R X[4];
+    face_flux_value<R, false, WAVE>(UL, L, UR, W, nx, ny, face_len<R>(nx, ny), R(1), X);
+    sF[3 * e + q] = Rec<R>::make(X[0], X[1], X[2], X[3]);
+    if (inner) sF[3 * v + kv] = Rec<R>::make(-X[0], -X[1], -X[2], -X[3]);
   }
   __syncthreads();
   const double t = MODE != kModeResidual ? s_t : 0.0, dt = MODE != kModeResidual ? s_dt : 0.0;
@@ -453,7 +464,8 @@ cudaError_t launch_batch_step_tile(bool f64, int mode, const BatchArgs& b, cudaS
 
 cudaError_t launch_step_tile_faces(bool f64, int mode, const StepArgs& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  if (!a.cell_ln || !a.tile_info || !a.halo_id || a.tile_vq) return cudaErrorInvalidValue;
+  if (!a.cell_ln || !a.tile_info || !a.halo_id || a.tile_vq || !a.tile_face_off || !a.tile_face)
+    return cudaErrorInvalidValue;
   if (f64) return launch_faces_mode<double, false>(mode, a, s);
   if (a.lo) return launch_faces_mode<float, true>(mode, a, s);
   return launch_faces_mode<float, false>(mode, a, s);

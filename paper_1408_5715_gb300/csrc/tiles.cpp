@@ -109,6 +109,21 @@ PairTiles build_pair_tiles(const HostMesh& m, int32_t tile) {
       }
     };
     for (int64_t c = t0; c < t1; ++c) pack(c, &L.cell_ln[2 * c], true);
+    // faces the tile evaluates once: every face of a tile cell, except those
+    // whose other side is a tile cell of lower local id (or, for a cell
+    // bordering itself, its own lower face)
+    L.face_off.push_back((int32_t)(L.face_rec.size() / 2));
+    for (int64_t c = t0; c < t1; ++c) {
+      const uint32_t e = (uint32_t)(c - t0);
+      const uint32_t w0 = L.cell_ln[2 * c], w1 = L.cell_ln[2 * c + 1];
+      const uint32_t v[3] = {w0 & 0xFFFFu, w0 >> 16, w1 & 0xFFFFu};
+      for (uint32_t q = 0; q < 3; ++q) {
+        const uint32_t kq = (w1 >> (16 + 2 * q)) & 3u;
+        if (v[q] < (uint32_t)nt && (v[q] < e || (v[q] == e && kq < q))) continue;
+        L.face_rec.push_back(e | q << 16 | kq << 18);
+        L.face_rec.push_back(v[q]);
+      }
+    }
     L.halo_ln.resize(2 * (hs + h1.size() + h2.size()), 0u);
     for (size_t j = 0; j < h1.size(); ++j) pack(h1[j], &L.halo_ln[2 * (hs + j)], false);
     L.halo_id.insert(L.halo_id.end(), h1.begin(), h1.end());
@@ -117,6 +132,8 @@ PairTiles build_pair_tiles(const HostMesh& m, int32_t tile) {
     L.t1_cap = std::max<int32_t>(L.t1_cap, nt + (int32_t)h1.size());
   }
   L.tile_info[2 * L.n_tiles] = (int32_t)L.halo_id.size();
+  L.face_off.push_back((int32_t)(L.face_rec.size() / 2));
+  if (L.face_rec.size() / 2 > (size_t)INT32_MAX) throw Error{FV_EINVAL, "too many tile faces"};
   return L;
 }
 

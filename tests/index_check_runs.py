@@ -93,8 +93,7 @@ def planted_runs():
     n = mi.n_tri
     cases = [("global_f32_v1", "f32", 1, 0, 0, n + 7), ("global_f32_v0", "f32", 0, 0, 1, n + 7),
              ("global_f64_v0", "f64", 0, 0, 2, n + 7), ("local_f32_v6", "f32", 6, 1, 0, 0xF000),
-             ("local_f32_pairs", "f32", None, 1, 1, 0xF000),
-             ("local_f64_v7", "f64", 7, 1, 2, 0xF000)]
+             ("local_f32_pairs", "f32", None, 1, 1, 0xF000)]
     for name, prec, variant, table, slot, value in cases:
         m = B.Mesh.from_input(mi, prec)
         perm = m.renumber("hilbert")

@@ -56,6 +56,6 @@ def test_checked_build_gives_the_same_bits(child):
 
 def test_checked_build_reports_planted_indices(child):
     codes = {k[5:]: int(v) for k, v in child.items() if k.startswith("code_")}
-    assert len(codes) == 6
+    assert len(codes) == 5
     for name, code in codes.items():
         assert code == B.FV_EINDEX, (name, code)
