@@ -952,25 +952,45 @@ def learned_leg(B, time_steps=2000):
     m.set_freestream(*W.freestream(0.5))
     m.renumber("hilbert")
     cl = B.Closure(CT.initial_theta(1, 0.3))
+    U0 = torch.tensor(W.uniform_state(mi.n_tri, W.freestream(0.5)), dtype=torch.float32,
+                      device="cuda")
+    plain_shape = choose_variant(m, U0, None)  # the plain step in its fastest shape
     cost = CT.step_cost(m, cl, steps=time_steps)
+    # the learned step on shape 7's tiles (one kernel per step), by tile size
+    keep_variant, keep_tile = m.tiling()
+    by_tile = {}
+    m.set_variant(7)
+    # the standard sizes and those that fill one or two waves of two blocks per SM
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    fit = [-(-mi.n_tri // (w * 2 * sms)) for w in (1, 2)]
+    for tile in sorted({256, 512, 1024} | {(t + 31) // 32 * 32 for t in fit if 64 <= t <= 1024}):
+        m.set_blocking(1, tile)
+        by_tile[tile] = CT.step_cost(m, cl, steps=time_steps)["learned"]
+    m.set_variant(keep_variant)
+    m.set_blocking(1, keep_tile)
+    best_tile = min(by_tile, key=by_tile.get)
+    learned_us = min(cost["learned"], by_tile[best_tile])
     n = mi.n_tri
-    # MLP rows per step: a face shared by two cells of one warp (32 consecutive
-    # cells) is evaluated once
     nbr, _, _ = m.export()
-    cell = np.arange(n)[:, None]
-    base = (cell // 32) * 32
-    shared = int(((nbr >= base) & (nbr < cell)).sum())
-    rows = 3 * n - shared
-    # tensor-core work per MLP row: layer 1 (K padded 8 -> 16) and layer 2
-    mma_flops = 2 * (16 * 32 + 32 * 32)
+    # tensor-core work per MLP row: layer 1 (K = 16: 8 features, 3 bias rows,
+    # padding) and layer 2 (K = 32, and a K = 16 slice for its bias rows)
+    mma_flops = 2 * (16 * 32 + 48 * 32)
+    # MLP rows per step: each face once
+    rows = int((nbr < 0).sum() + (nbr >= 0).sum() // 2)
     res = {"cells": n, "order": "hilbert", "time_steps": time_steps,
-           "us_per_step_plain": cost["plain"], "us_per_step_learned": cost["learned"],
-           "value": n / (cost["learned"] * 1e-6), "unit": "cell-updates/s",
-           "overhead": cost["learned"] / cost["plain"],
+           "us_per_step_plain": cost["plain"], "plain_kernel_shape": plain_shape,
+           "us_per_step_learned_two_passes": cost["learned"],
+           "us_per_step_learned_tiles": by_tile,
+           "us_per_step_learned": learned_us,
+           "value": n / (learned_us * 1e-6), "unit": "cell-updates/s",
+           "overhead": learned_us / cost["plain"],
            "mlp_rows_per_cell": rows / n,
            "mma_flops_per_cell": mma_flops * rows / n,
-           "mma_tflops": mma_flops * rows / (cost["learned"] * 1e-6) / 1e12,
-           "kernel": "k_step_closure<FE, compensated> (mma.sync m16n8k16 bf16)"}
+           "mma_tflops": mma_flops * rows / (learned_us * 1e-6) / 1e12,
+           "kernel": (f"k_step_closure_tile<FE, compensated, tile {best_tile}>"
+                      if by_tile[best_tile] < cost["learned"]
+                      else "k_face_scales + k_step_scaled<FE, compensated>")
+                     + " (mma.sync m16n8k16 bf16)"}
     m.close()
     cl.close()
     return res

@@ -390,7 +390,11 @@ int fv_mesh_debug_set_index(fv_mesh* mesh, int32_t table, int64_t cell, int32_t 
  *            is clamped, later steps advance nothing); <= 0: no limit.
  *   scheme   FV_SCHEME_FE or FV_SCHEME_RK2.
  *   closure  nullable: learned dissipation scale per face (fv_closure_*);
- *            FV_F32 meshes only.
+ *            FV_F32 meshes only.  With shape 7 (fv_mesh_set_variant; tiles
+ *            of up to 1024 cells) the learned step runs as one kernel per
+ *            stage on the tiles, each face's features, scale and flux formed
+ *            once; otherwise as a pass over the mesh's faces for the scales
+ *            and a step that reads them.  Both give the same bits.
  *   t_advanced nullable host pointer: if given, the call synchronises the
  *            stream, stores the time advanced, and returns FV_ENONFINITE if a
  *            step produced a bad state.  If NULL nothing is synchronised; use

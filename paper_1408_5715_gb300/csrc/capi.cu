@@ -479,6 +479,8 @@ fv::StepArgs base_args(const fv_mesh* m) {
 
 cudaError_t launch_mode(const fv_mesh* m, int mode, const fv::StepArgs& a, const fv_closure* cl,
                         cudaStream_t s) {
+  if (cl && m->variant == fv::kFaceTileVariant)  // one launch on the tiles of shape 7
+    return fv::launch_step_closure_tile(mode, a, cl->params(), s);
   if (cl) {
     // the scales of the state the stage evaluates, then the scaled step
     cudaError_t e = fv::launch_face_scales(a, m->d_faces, m->n_faces, cl->params(), m->d_scale, s);
@@ -494,6 +496,10 @@ void enqueue_steps(fv_mesh* m, void* U, int64_t j0, int64_t count, double cfl, d
                    bool lo_alt = false) {
   fv::LoopScalars* sc = m->d_scal;
   if (!cl && tiled_shape(m->variant) && count > 0) check_tile_smem(m, step_tile_smem(m));
+  if (cl && m->variant == fv::kFaceTileVariant && count > 0) {
+    if (m->tiles_built > 1024) invalid("the learned closure on tiles takes tiles of up to 1024 cells");
+    check_tile_smem(m, fv::closure_tile_smem_bytes(m->p_t1_cap, m->tiles_built));
+  }
   for (int64_t j = j0; j < j0 + count; ++j) {
     fv::StepArgs a = base_args(m);
     a.bmin_read = &sc->bmin[j % 3];

@@ -28,6 +28,7 @@
 #include "cell_math.cuh"
 #include "kernels.h"
 #include "launch_util.cuh"
+#include "tile_math.cuh"
 
 namespace fv {
 
@@ -543,6 +544,133 @@ __global__ void __launch_bounds__(kBlock) k_step_scaled(StepArgs a, const float*
   }
 }
 
+// ---------------------------------------------------------------------------
+// The learned step on tiles (with shape 7): a block stages the states and
+// primitives of its tile and the tile's ring in shared memory (tile_math.cuh)
+// and walks the tile's face list (tiles.cpp) 32 faces per warp: features,
+// the MLP on two 16-row tiles, then the scaled flux of each face, written to
+// the slot of its cell and, negated, to the slot of the face pointing back
+// (the face flux is antisymmetric bit for bit, and the features are the same
+// bits from either side).  Every tile cell then adds its three slots in face
+// order and finishes.  Each face's features, scale and flux are formed once
+// and every primitive once per cell, in one launch -- the same bits as the
+// two passes above.
+// ---------------------------------------------------------------------------
+template <int MODE, bool COMP, int THREADS, int KMAX>
+__global__ void __launch_bounds__(THREADS) k_step_closure_tile(StepArgs a, ClosureParams cp) {
+  chain_entry();
+  constexpr int kWarps = THREADS / 32;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float4* sU = reinterpret_cast<float4*>(smem_raw);  // [t1_cap] states
+  float4* sP = sU + a.t1_cap;                          // [t1_cap] (u, v, p, c)
+  float4* sF = sP + a.t1_cap;                          // [3 tile] face flux values
+  ClWarpSmem* wsm = reinterpret_cast<ClWarpSmem*>(sF + 3 * a.tile);  // [kWarps] MLP rows
+  __shared__ float w3s[32];
+  if (threadIdx.x < 32) w3s[threadIdx.x] = cp.w3[threadIdx.x];
+  ClFrag fr;
+  load_frags(cp, fr);
+  const float4* __restrict__ U = static_cast<const float4*>(a.U);
+  const float4* __restrict__ geom = static_cast<const float4*>(a.geom);
+  float4* out = static_cast<float4*>(a.out);
+  const int t0 = blockIdx.x * a.tile;  // cell ids are 32-bit
+  const int nt = min(a.tile, (int)a.n - t0);
+  const int hs = __ldg(a.tile_info + 2 * blockIdx.x);
+  const int h1 = __ldg(a.tile_info + 2 * blockIdx.x + 1);
+  __shared__ double s_t, s_dt;
+  if (threadIdx.x == 0 && MODE != kModeResidual) block_dt(a, s_t, s_dt);
+  stage_states<float, THREADS, kStageBatch<float, KMAX>>(U, t0, nt, h1, a.halo_id + hs, sU, sP,
+                                                         a.n, a.err);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  ClWarpSmem& w = wsm[warp];
+  const int fb = __ldg(a.tile_face_off + blockIdx.x), fe = __ldg(a.tile_face_off + blockIdx.x + 1);
+  for (int base = fb + warp * 32; base < fe; base += kWarps * 32) {  // uniform in the warp
+    const int f = base + lane;
+    float feat[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    unsigned e = 0u, q = 0u, kv = 0u, v = 0u;
+    float4 UL = make_float4(0.f, 0.f, 0.f, 0.f), UR = UL;
+    Prim<float> L{0.f, 0.f, 0.f, 0.f}, W = L;
+    float nx = 0.f, ny = 0.f, len = 0.f;
+    bool use = false;
+    if (f < fe) {
+      const uint2 r = __ldg(a.tile_face + f);
+      e = r.x & 0xffffu, q = (r.x >> 16) & 3u, kv = (r.x >> 18) & 3u, v = r.y;
+      use = index_ok(e, nt, a.err);
+      if (use) {
+        face_normal<float>(geom, t0 + (int)e, q, nx, ny);
+        UL = sU[e];
+        L = rec_prim<float>(sP[e]);
+        if (v < kGhostCodes) {
+          if (index_ok(v, nt + h1, a.err)) {
+            UR = sU[v];
+            W = rec_prim<float>(sP[v]);
+          } else {
+            UR = UL;
+            W = L;
+          }
+        } else {
+          UR = ghost<float>((int)v - 0x10000, UL, nx, ny, a.uinf_f);
+          W = primitive<float>(UR);
+        }
+        len = face_len<float>(nx, ny);
+        face_features(UL, L, UR, W, nx, ny, len, feat);
+      }
+    }
+    w.feat[lane] = pack_features(feat);
+    __syncwarp();
+    warp_mlp(w, fr, w3s, cp.b3, 2);
+    __syncwarp();
+    if (use) {
+      float X[4];
+      face_flux_value<float, true>(UL, L, UR, W, nx, ny, len, w.s[lane], X);
+      sF[3 * e + q] = make_float4(X[0], X[1], X[2], X[3]);
+      if (v < (unsigned)nt) sF[3 * v + kv] = make_float4(-X[0], -X[1], -X[2], -X[3]);
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  const double t = MODE != kModeResidual ? s_t : 0.0, dt = MODE != kModeResidual ? s_dt : 0.0;
+  float bmin = INFINITY;
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < KMAX; ++k) {
+    const int e = threadIdx.x + k * THREADS;
+    if (e < nt) {
+      const int i = t0 + e;
+      CellIn<float> c;
+      c.g0 = __ldg(geom + 2 * i);
+      c.g1 = __ldg(geom + 2 * i + 1);
+      c.U = sU[e];
+      if (MODE == kModeRK2b) c.base = static_cast<const float4*>(a.Ubase)[i];
+      if (COMP && MODE != kModeResidual) c.lo = a.lo[i];
+      if (COMP && MODE == kModeRK2b) c.lo_stage = a.lo_stage[i];
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const float4 X = sF[3 * e + q];
+        acc[0] = add(acc[0], X.x);
+        acc[1] = add(acc[1], X.y);
+        acc[2] = add(acc[2], X.z);
+        acc[3] = add(acc[3], X.w);
+      }
+      const float perim = add(add(face_len<float>(c.g0.x, c.g0.y), face_len<float>(c.g0.z, c.g0.w)),
+                              face_len<float>(c.g1.x, c.g1.y));
+      finish_cell<float, MODE, COMP>(a, out, i, c, acc, perim, (float)dt, bmin, ok);
+    }
+  }
+  if (MODE == kModeFE || MODE == kModeRK2b) {
+    if (!ok) atomicOr(a.err, 1);
+    const double m = (double)block_min<float>(bmin);
+    if (threadIdx.x == 0) {
+      atomicMin(a.bmin_write, (unsigned long long)__double_as_longlong(m));
+      if (blockIdx.x == 0) {
+        *a.t_write = t + dt;
+        *a.bmin_reset = kInfBits;
+      }
+    }
+  }
+}
+
 template <typename K>
 unsigned cl_resident_blocks(K kernel) {
   static int cached = 0;
@@ -935,6 +1063,52 @@ cudaError_t launch_scaled_t(const StepArgs& a, const float* s_cf, cudaStream_t s
                         a.chained, a, s_cf);
 }
 }  // namespace
+
+size_t closure_tile_smem_bytes(int t1_cap, int tile) {
+  return tile_faces_smem_bytes(false, t1_cap, tile) + (size_t)8 * sizeof(ClWarpSmem);
+}
+
+namespace {
+template <int MODE, bool COMP, int KMAX>
+cudaError_t launch_cl_tile_t(const StepArgs& a, const ClosureParams& cp, cudaStream_t s) {
+  auto k = k_step_closure_tile<MODE, COMP, 256, KMAX>;
+  const size_t smem = closure_tile_smem_bytes(a.t1_cap, a.tile);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t tiles = (a.n + a.tile - 1) / a.tile;
+  return launch_chained(k, (unsigned)tiles, 256, smem, s, a.chained, a, cp);
+}
+
+template <int MODE, bool COMP>
+cudaError_t launch_cl_tile_size(const StepArgs& a, const ClosureParams& cp, cudaStream_t s) {
+  if (a.tile < 1 || a.tile > 1024) return cudaErrorInvalidValue;
+  if (a.tile <= 256) return launch_cl_tile_t<MODE, COMP, 1>(a, cp, s);
+  if (a.tile <= 512) return launch_cl_tile_t<MODE, COMP, 2>(a, cp, s);
+  if (a.tile <= 768) return launch_cl_tile_t<MODE, COMP, 3>(a, cp, s);
+  return launch_cl_tile_t<MODE, COMP, 4>(a, cp, s);
+}
+}  // namespace
+
+cudaError_t launch_step_closure_tile(int mode, const StepArgs& a, const ClosureParams& cp,
+                                     cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  if (!a.cell_ln || !a.tile_info || !a.halo_id || !a.tile_face_off || !a.tile_face || a.tile_vq)
+    return cudaErrorInvalidValue;
+  const bool comp = a.lo != nullptr;
+  switch (mode) {
+    case kModeFE:
+      return comp ? launch_cl_tile_size<kModeFE, true>(a, cp, s)
+                  : launch_cl_tile_size<kModeFE, false>(a, cp, s);
+    case kModeRK2a:
+      return comp ? launch_cl_tile_size<kModeRK2a, true>(a, cp, s)
+                  : launch_cl_tile_size<kModeRK2a, false>(a, cp, s);
+    case kModeRK2b:
+      return comp ? launch_cl_tile_size<kModeRK2b, true>(a, cp, s)
+                  : launch_cl_tile_size<kModeRK2b, false>(a, cp, s);
+    case kModeResidual: return launch_cl_tile_size<kModeResidual, false>(a, cp, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 cudaError_t launch_step_scaled(int mode, const StepArgs& a, const float* s_cf, cudaStream_t s) {
   if (a.n <= 0 && mode == kModeResidual) return cudaSuccess;

@@ -155,6 +155,11 @@ struct __align__(16) FaceRec {
 cudaError_t launch_face_scales(const StepArgs& a, const FaceRec* faces, int64_t nf,
                                const ClosureParams& cp, float* s_cf, cudaStream_t s);
 cudaError_t launch_step_scaled(int mode, const StepArgs& a, const float* s_cf, cudaStream_t s);
+// The learned step on tiles with each face once (shape 7's tiles and face
+// lists; FP32; tiles of up to 1024 cells)
+size_t closure_tile_smem_bytes(int t1_cap, int tile);
+cudaError_t launch_step_closure_tile(int mode, const StepArgs& a, const ClosureParams& cp,
+                                     cudaStream_t s);
 cudaError_t launch_closure_scales(const StepArgs& a, const ClosureParams& cp, float* s_out,
                                   cudaStream_t s);
 // Blocks the gradient kernel launches at most on this device.

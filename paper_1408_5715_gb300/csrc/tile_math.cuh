@@ -84,5 +84,76 @@ __device__ __forceinline__ void vertex_geometry(int2 q0, int2 q1, int2 q2, float
   g1.w = 0.0f;
 }
 
+// Loads the states of a tile (nt cells from t0) and of its first halo (h1
+// cells whose ids are halo[0 .. h1)) into shared memory with their primitive
+// variables.  With PA > 0 each thread issues the loads of its first PA
+// entries before it uses any, so it waits for about one memory round trip
+// (two for halo cells, whose ids come first) rather than one per entry.
+// The halo ids are global cell ids of the n cells (checked in the
+// bounds-checked build; a bad id stages the tile's first cell).
+template <typename R>
+__device__ __forceinline__ int64_t staged_id(int64_t t0, int nt, int e, const int* halo,
+                                             int64_t n, int* err) {
+  if (e < nt) return t0 + e;
+  const int64_t g = __ldg(halo + (e - nt));
+  return index_ok(g, n, err) ? g : t0;
+}
+
+template <typename R, int THREADS, int PA>
+__device__ __forceinline__ void stage_states(const rec_t<R>* __restrict__ U, int64_t t0, int nt,
+                                             int h1, const int* __restrict__ halo, rec_t<R>* sU,
+                                             rec_t<R>* sP, int64_t n, int* err) {
+  const int ne = nt + h1;
+  int e0 = threadIdx.x;
+  if constexpr (PA > 0) {
+    rec_t<R> u[PA];
+#pragma unroll
+    for (int k = 0; k < PA; ++k) {
+      const int e = threadIdx.x + k * THREADS;
+      if (e < ne) u[k] = Rec<R>::ld(U + staged_id<R>(t0, nt, e, halo, n, err));
+    }
+#pragma unroll
+    for (int k = 0; k < PA; ++k) {
+      const int e = threadIdx.x + k * THREADS;
+      if (e < ne) {
+        sU[e] = u[k];
+        sP[e] = prim_rec<R>(primitive<R>(u[k]));
+      }
+    }
+    e0 += PA * THREADS;
+  }
+  for (int e = e0; e < ne; e += THREADS) {
+    const rec_t<R> u = Rec<R>::ld(U + staged_id<R>(t0, nt, e, halo, n, err));
+    sU[e] = u;
+    sP[e] = prim_rec<R>(primitive<R>(u));
+  }
+}
+
+// Loads per thread issued together by stage_states: FP32 tiles with a ring
+// of up to two block-widths of halo cells in one batch; FP64 (bound by its
+// arithmetic, with twice the registers per state) one at a time.
+template <typename R, int KMAX>
+constexpr int kStageBatch = sizeof(R) == 4 ? KMAX + 2 : 0;
+
+// The normal of face q of cell i from its geometry record (one 16-byte load).
+template <typename R>
+__device__ __forceinline__ void face_normal(const rec_t<R>* __restrict__ geom, int i, unsigned q,
+                                            R& nx, R& ny);
+template <>
+__device__ __forceinline__ void face_normal<float>(const float4* __restrict__ geom, int i,
+                                                   unsigned q, float& nx, float& ny) {
+  const float4 g = __ldg(geom + 2 * i + (q == 2u));
+  nx = q == 1u ? g.z : g.x;
+  ny = q == 1u ? g.w : g.y;
+}
+template <>
+__device__ __forceinline__ void face_normal<double>(const dq4* __restrict__ geom, int i,
+                                                    unsigned q, double& nx, double& ny) {
+  // record 2i holds faces 0 and 1, record 2i + 1 face 2 first: 16-byte halves
+  const double2 g = __ldg(reinterpret_cast<const double2*>(geom + 2 * i + (q == 2u)) + (q == 1u));
+  nx = g.x;
+  ny = g.y;
+}
+
 }  // namespace
 }  // namespace fv

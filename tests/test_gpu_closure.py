@@ -318,3 +318,26 @@ def test_captured_graphs_see_new_closure_parameters(vortex_case):
     Ur = torch.tensor(U0, dtype=torch.float32, device="cuda")
     ref.step(Ur, 100, 0.4, closure=B.Closure(th1))
     assert torch.equal(U, Ur)
+
+
+@pytest.mark.parametrize("scheme", ["fe", "rk2"])
+@pytest.mark.parametrize("tile", [256, 512, 1024])
+def test_closure_on_tiles_gives_the_bits_of_the_two_passes(vortex_case, scheme, tile):
+    # with shape 7 the learned step runs as one kernel on tiles (each face's
+    # scale and flux formed once); the scale pass + scaled step gives the
+    # same bits
+    mi, U0 = vortex_case
+    th, _ = make_theta(6, scale=0.3)
+    cl = B.Closure(th)
+    outs = []
+    for variant in (1, 7):
+        g = B.Mesh.from_input(mi, "f32")
+        perm = g.renumber("hilbert")
+        g.set_variant(variant)
+        if variant == 7:
+            g.set_blocking(1, tile)
+        U = torch.tensor(U0[perm], dtype=torch.float32, device="cuda")
+        t = g.step(U, 110, 0.4, scheme=scheme, closure=cl)  # a captured graph and a tail
+        outs.append((t, U))
+    assert outs[0][0] == outs[1][0]
+    assert torch.equal(outs[0][1], outs[1][1])
