@@ -240,10 +240,11 @@ struct PairArgs {
 constexpr int kPairTiles[4] = {512, 768, 1024, 2048};
 // The one-step tile shape takes any tile size from 1 to this many cells.
 constexpr int kMaxTileCells = 2048;
-// dynamic shared memory of one block for the given capacities; the staged
-// kernel adds two stages of the tile's own records (64 bytes a cell each)
+// dynamic shared memory of one block for the given capacities (the states
+// only, 16 bytes a cell); the staged kernel adds two stages of the tile's own
+// records (64 bytes a cell each)
 inline size_t pair_smem_bytes(int e_cap, int t1_cap, int tile, bool staged) {
-  return (size_t)(2 * e_cap + 2 * t1_cap) * 16 + (staged ? (size_t)2 * 64 * tile : 0);
+  return (size_t)(e_cap + t1_cap) * 16 + (staged ? (size_t)2 * 64 * tile : 0);
 }
 // staged: 0 loads through the caches; 1 persistent blocks whose tile records
 // arrive by bulk copies (cp.async.bulk) into double-buffered stages

@@ -3,11 +3,14 @@
 // The paper chains processors so that the output of one update feeds the next
 // without another trip through memory (Sec. 7).  Here one block owns a tile
 // of consecutive cells.  It loads the states of the tile and of its two halo
-// rings (tiles.cpp) into shared memory, together with their primitive
-// variables (Eq. 2), then
-//   step 1: updates tile and first halo, keeping U^{n+1} (and its primitives)
-//           in shared memory and the tile's remainders in registers;
+// rings (tiles.cpp) into shared memory, then
+//   step 1: updates tile and first halo, keeping U^{n+1} in shared memory and
+//           the tile's remainders in registers;
 //   step 2: updates the tile from U^{n+1} and writes U^{n+2}.
+// Shared memory holds states only (16 bytes a cell per step); a cell forms
+// the primitive variables (Eq. 2) of its neighbours from their states at
+// each use, which costs instructions but halves the block's shared memory
+// and so doubles the blocks an SM keeps resident.
 // Per pair of updates a tile cell moves its state, remainder and geometry
 // through DRAM once instead of twice; the price is the halo cells' extra
 // loads and the first halo's repeated first step.
@@ -46,15 +49,14 @@ namespace fv {
 
 namespace {
 
-__device__ __forceinline__ float4 prim4(const Prim<float>& w) { return prim_rec<float>(w); }
-
-// Residual sum of one cell from shared-memory neighbours (tile_math.cuh):
-// entries [0, cap) of sU and sP.
+// Residual sum of one cell from shared-memory neighbour states (tile_math.cuh):
+// entries [0, cap) of sU, their primitives formed from the states.
 __device__ __forceinline__ float cell_fluxes(const float4& g0, const float4& g1, uint2 ln,
                                              const float4& UL, const Prim<float>& L,
-                                             const float4* sU, const float4* sP,
-                                             const float* uinf, float acc[4], int cap, int* err) {
-  return cell_fluxes<float>(g0, g1, ln, UL, L, sU, sP, uinf, acc, cap, err);
+                                             const float4* sU, const float* uinf, float acc[4],
+                                             int cap, int* err) {
+  return cell_fluxes<float, kWaveAverage, false>(g0, g1, ln, UL, L, sU, nullptr, uinf, acc, cap,
+                                                 err);
 }
 
 // Global id of halo entry j (checked in the bounds-checked build; a bad id
@@ -115,27 +117,23 @@ __device__ __forceinline__ void pair_dt(const PairArgs& a, PairDt& d) {
 }
 
 // Step 1 of one cell (tile or first halo) from the states of the pair's start:
-// writes U^{n+1} and its primitives to shared memory, returns the remainder;
-// `check` tests the new state as the one-step kernel does.
+// writes U^{n+1} to shared memory, returns the remainder; `check` tests the
+// new state as the one-step kernel does.
 template <bool COMP>
 __device__ __forceinline__ uint2 step1_cell(const float4& g0, const float4& g1, uint2 ln,
-                                            uint2 lo0, int e, const float4* sU0,
-                                            const float4* sP0, float4* sU1, float4* sP1,
+                                            uint2 lo0, int e, const float4* sU0, float4* sU1,
                                             const float* uinf, float dt, bool check, bool& ok,
                                             int cap, int* err) {
   const float4 UL = sU0[e];
-  const float4 p = sP0[e];
-  const Prim<float> L{p.x, p.y, p.z, p.w};
+  const Prim<float> L = primitive<float>(UL);
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
-  const float perim = cell_fluxes(g0, g1, ln, UL, L, sU0, sP0, uinf, acc, cap, err);
+  const float perim = cell_fluxes(g0, g1, ln, UL, L, sU0, uinf, acc, cap, err);
   uint2 lo1 = make_uint2(0u, 0u);
   const float4 U1 = fe_update<COMP>(UL, g1.z, acc, dt, lo0, lo1);
-  const Prim<float> w = primitive<float>(U1);
   sU1[e] = U1;
-  sP1[e] = prim4(w);
   if (check) {
     bool c_ok;
-    bound_of<float>(U1, w, inradius<float>(g1, perim), c_ok);
+    bound_of<float>(U1, primitive<float>(U1), inradius<float>(g1, perim), c_ok);
     ok = ok && c_ok;
   }
   return lo1;
@@ -146,14 +144,12 @@ __device__ __forceinline__ uint2 step1_cell(const float4& g0, const float4& g1, 
 template <bool COMP>
 __device__ __forceinline__ float4 step2_cell(const float4& g0, const float4& g1, uint2 ln,
                                              uint2 lo1, int e, const float4* sU1,
-                                             const float4* sP1, const float* uinf, float dt,
-                                             uint2& lo2, float& bmin, bool& ok, int cap,
-                                             int* err) {
+                                             const float* uinf, float dt, uint2& lo2, float& bmin,
+                                             bool& ok, int cap, int* err) {
   const float4 UL = sU1[e];
-  const float4 p = sP1[e];
-  const Prim<float> L{p.x, p.y, p.z, p.w};
+  const Prim<float> L = primitive<float>(UL);
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
-  const float perim = cell_fluxes(g0, g1, ln, UL, L, sU1, sP1, uinf, acc, cap, err);
+  const float perim = cell_fluxes(g0, g1, ln, UL, L, sU1, uinf, acc, cap, err);
   const float4 U2 = fe_update<COMP>(UL, g1.z, acc, dt, lo1, lo2);
   bool c_ok;
   bmin = fmin(bmin, cell_bound<float>(U2, inradius<float>(g1, perim), c_ok));
@@ -163,11 +159,10 @@ __device__ __forceinline__ float4 step2_cell(const float4& g0, const float4& g1,
 
 // Step 1 of the first-halo cells of a tile (global gathers); their states are
 // checked by the tiles that own them.
-// ne: the entries staged in sU0 and sP0 (tile and both halos).
+// ne: the entries staged in sU0 (tile and both halos).
 template <int THREADS, bool COMP>
 __device__ __forceinline__ void step1_halo(const PairArgs& a, int nt, int hs, int h1, int ne,
-                                           const float4* sU0, const float4* sP0, float4* sU1,
-                                           float4* sP1, float dt) {
+                                           const float4* sU0, float4* sU1, float dt) {
   for (int e = nt + threadIdx.x; e < nt + h1; e += THREADS) {
     const int j = hs + (e - nt);
     const int g = halo_cell(a, j);
@@ -175,8 +170,7 @@ __device__ __forceinline__ void step1_halo(const PairArgs& a, int nt, int hs, in
     const uint2 ln = __ldg(a.halo_ln + j);
     const uint2 lo0 = COMP ? __ldg(a.lo_in + g) : make_uint2(0u, 0u);
     bool unused = true;
-    step1_cell<COMP>(g0, g1, ln, lo0, e, sU0, sP0, sU1, sP1, a.uinf, dt, false, unused, ne,
-                     a.err);
+    step1_cell<COMP>(g0, g1, ln, lo0, e, sU0, sU1, a.uinf, dt, false, unused, ne, a.err);
   }
 }
 
@@ -199,10 +193,8 @@ template <int THREADS, int KMAX, bool COMP>
 __global__ void __launch_bounds__(THREADS) k_step_pair(PairArgs a) {
   chain_entry();
   extern __shared__ float4 smem[];
-  float4* sU0 = smem;                 // [e_cap]  U^n of tile + both halos
-  float4* sP0 = smem + a.e_cap;       // [e_cap]  their primitives (u, v, p, c)
-  float4* sU1 = smem + 2 * a.e_cap;   // [t1_cap] U^{n+1} of tile + first halo
-  float4* sP1 = sU1 + a.t1_cap;       // [t1_cap]
+  float4* sU0 = smem;              // [e_cap]  U^n of tile + both halos
+  float4* sU1 = smem + a.e_cap;    // [t1_cap] U^{n+1} of tile + first halo
   const int t0 = blockIdx.x * a.tile;  // cell ids are 32-bit
   const int nt = min(a.tile, (int)a.n - t0);
   const int hs = __ldg(a.tile_info + 2 * blockIdx.x);
@@ -211,12 +203,10 @@ __global__ void __launch_bounds__(THREADS) k_step_pair(PairArgs a) {
   __shared__ PairDt sdt;
   if (threadIdx.x == 0) pair_dt(a, sdt);
 
-  // states at the start of the pair, with their primitives
+  // states at the start of the pair
   for (int e = threadIdx.x; e < nt + h12; e += THREADS) {
     const int g = e < nt ? t0 + e : halo_cell(a, hs + (e - nt));
-    const float4 u = __ldg(a.U + g);
-    sU0[e] = u;
-    sP0[e] = prim4(primitive<float>(u));
+    sU0[e] = __ldg(a.U + g);
   }
   __syncthreads();
   const float dt1f = sdt.dt1f, dt2f = sdt.dt2f;
@@ -232,11 +222,11 @@ __global__ void __launch_bounds__(THREADS) k_step_pair(PairArgs a) {
       const int g = t0 + e;
       const uint2 lo0 = COMP ? __ldg(a.lo_in + g) : make_uint2(0u, 0u);
       lo1[k] = step1_cell<COMP>(__ldg(a.geom + 2 * g), __ldg(a.geom + 2 * g + 1),
-                                __ldg(a.cell_ln + g), lo0, e, sU0, sP0, sU1, sP1, a.uinf, dt1f,
-                                true, ok, nt + h12, a.err);
+                                __ldg(a.cell_ln + g), lo0, e, sU0, sU1, a.uinf, dt1f, true, ok,
+                                nt + h12, a.err);
     }
   }
-  step1_halo<THREADS, COMP>(a, nt, hs, h1, nt + h12, sU0, sP0, sU1, sP1, dt1f);
+  step1_halo<THREADS, COMP>(a, nt, hs, h1, nt + h12, sU0, sU1, dt1f);
   __syncthreads();
 
   // step 2: the tile, from U^{n+1}
@@ -248,8 +238,8 @@ __global__ void __launch_bounds__(THREADS) k_step_pair(PairArgs a) {
       const int g = t0 + e;
       uint2 lo2;
       const float4 U2 = step2_cell<COMP>(__ldg(a.geom + 2 * g), __ldg(a.geom + 2 * g + 1),
-                                         __ldg(a.cell_ln + g), lo1[k], e, sU1, sP1, a.uinf, dt2f,
-                                         lo2, bmin, ok, nt + h1, a.err);
+                                         __ldg(a.cell_ln + g), lo1[k], e, sU1, a.uinf, dt2f, lo2,
+                                         bmin, ok, nt + h1, a.err);
       a.out[g] = U2;
       if (COMP) a.lo_out[g] = lo2;
     }
@@ -289,9 +279,7 @@ __global__ void __launch_bounds__(THREADS) k_step_pair_tma(PairArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   Stage* stages = reinterpret_cast<Stage*>(smem_raw);
   float4* sU0 = reinterpret_cast<float4*>(smem_raw + 2 * sizeof(Stage));
-  float4* sP0 = sU0 + a.e_cap;
-  float4* sU1 = sP0 + a.e_cap;
-  float4* sP1 = sU1 + a.t1_cap;
+  float4* sU1 = sU0 + a.e_cap;
   __shared__ __align__(8) uint64_t bars[2];
   __shared__ int abort_flag;
   __shared__ PairDt sdt;
@@ -335,11 +323,8 @@ __global__ void __launch_bounds__(THREADS) k_step_pair_tma(PairArgs a) {
     const int hs = __ldg(a.tile_info + 2 * b);
     const int h1 = __ldg(a.tile_info + 2 * b + 1);
     const int h12 = __ldg(a.tile_info + 2 * b + 2) - hs;
-    for (int e = tid; e < nt + h12; e += THREADS) {
-      const float4 u = e < nt ? st.U[e] : __ldg(a.U + halo_cell(a, hs + (e - nt)));
-      sU0[e] = u;
-      sP0[e] = prim4(primitive<float>(u));
-    }
+    for (int e = tid; e < nt + h12; e += THREADS)
+      sU0[e] = e < nt ? st.U[e] : __ldg(a.U + halo_cell(a, hs + (e - nt)));
     __syncthreads();
     uint2 lo1[KMAX];
 #pragma unroll
@@ -348,10 +333,10 @@ __global__ void __launch_bounds__(THREADS) k_step_pair_tma(PairArgs a) {
       lo1[q] = make_uint2(0u, 0u);
       if (e < nt)
         lo1[q] = step1_cell<COMP>(st.geom[2 * e], st.geom[2 * e + 1], st.ln[e],
-                                  COMP ? st.lo[e] : make_uint2(0u, 0u), e, sU0, sP0, sU1, sP1,
-                                  a.uinf, dt1f, true, ok, nt + h12, a.err);
+                                  COMP ? st.lo[e] : make_uint2(0u, 0u), e, sU0, sU1, a.uinf,
+                                  dt1f, true, ok, nt + h12, a.err);
     }
-    step1_halo<THREADS, COMP>(a, nt, hs, h1, nt + h12, sU0, sP0, sU1, sP1, dt1f);
+    step1_halo<THREADS, COMP>(a, nt, hs, h1, nt + h12, sU0, sU1, dt1f);
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < KMAX; ++q) {
@@ -359,8 +344,7 @@ __global__ void __launch_bounds__(THREADS) k_step_pair_tma(PairArgs a) {
       if (e < nt) {
         uint2 lo2;
         const float4 U2 = step2_cell<COMP>(st.geom[2 * e], st.geom[2 * e + 1], st.ln[e], lo1[q],
-                                           e, sU1, sP1, a.uinf, dt2f, lo2, bmin, ok, nt + h1,
-                                           a.err);
+                                           e, sU1, a.uinf, dt2f, lo2, bmin, ok, nt + h1, a.err);
         a.out[t0 + e] = U2;
         if (COMP) a.lo_out[t0 + e] = lo2;
       }

@@ -1,8 +1,10 @@
 // tile_math.cuh -- the cell update on tiles staged in shared memory, shared by
 // the one-step tile kernel (tile_step.cu) and the two-step kernels
-// (pair_step.cu).  A tile holds the states of its cells and halo cells and
-// their primitive variables (u, v, p, c), each computed once; neighbours are
-// 16-bit tile-local ids (tiles.cpp), ghost faces the codes 0xFFFD..0xFFFF.
+// (pair_step.cu).  A tile holds the states of its cells and halo cells and,
+// in the one-step kernel, their primitive variables (u, v, p, c), each
+// computed once (the two-step kernels stage states only and form a
+// neighbour's primitives at each use); neighbours are 16-bit tile-local ids
+// (tiles.cpp), ghost faces the codes 0xFFFD..0xFFFF.
 // The face arithmetic is cell_math.cuh's, so results are bitwise those of the
 // one-step kernel that forms every neighbour's primitives itself.
 #pragma once
@@ -25,8 +27,9 @@ __device__ __forceinline__ Prim<R> rec_prim(const rec_t<R>& p) {
 }
 
 // One face of a cell whose neighbour state and primitives are in shared
-// memory (entries [0, cap) of sU and sP).
-template <typename R, int WAVE = kWaveAverage>
+// memory (entries [0, cap) of sU and sP).  PRIMS = false: only the states are
+// staged (sP unused) and the neighbour's primitives are formed here.
+template <typename R, int WAVE = kWaveAverage, bool PRIMS = true>
 __device__ __forceinline__ R smem_face(const rec_t<R>& UL, const Prim<R>& L, unsigned v, R nx, R ny,
                                        const rec_t<R>* sU, const rec_t<R>* sP, const R* uinf,
                                        R acc[4], int cap, int* err) {
@@ -35,7 +38,7 @@ __device__ __forceinline__ R smem_face(const rec_t<R>& UL, const Prim<R>& L, uns
   if (v < kGhostCodes) {
     if (index_ok(v, cap, err)) {
       UR = sU[v];
-      W = rec_prim<R>(sP[v]);
+      W = PRIMS ? rec_prim<R>(sP[v]) : primitive<R>(UR);
     } else {
       UR = UL;
       W = L;
@@ -51,18 +54,18 @@ __device__ __forceinline__ R smem_face(const rec_t<R>& UL, const Prim<R>& L, uns
 
 // Residual sum of one cell (faces in the order 0, 1, 2) and its perimeter;
 // the tile-local ids of ln index entries [0, cap) of sU and sP.
-template <typename R, int WAVE = kWaveAverage>
+template <typename R, int WAVE = kWaveAverage, bool PRIMS = true>
 __device__ __forceinline__ R cell_fluxes(const rec_t<R>& g0, const rec_t<R>& g1, uint2 ln,
                                          const rec_t<R>& UL, const Prim<R>& L, const rec_t<R>* sU,
                                          const rec_t<R>* sP, const R* uinf, R acc[4], int cap,
                                          int* err) {
-  R perim =
-      smem_face<R, WAVE>(UL, L, ln.x & 0xffffu, g0.x, g0.y, sU, sP, uinf, acc, cap, err);
-  perim = add(perim,
-              smem_face<R, WAVE>(UL, L, ln.x >> 16, g0.z, g0.w, sU, sP, uinf, acc, cap, err));
+  R perim = smem_face<R, WAVE, PRIMS>(UL, L, ln.x & 0xffffu, g0.x, g0.y, sU, sP, uinf, acc, cap,
+                                      err);
+  perim = add(perim, smem_face<R, WAVE, PRIMS>(UL, L, ln.x >> 16, g0.z, g0.w, sU, sP, uinf, acc,
+                                               cap, err));
   // the high half of ln.y holds a node id in the vertex-geometry layout
-  perim = add(perim, smem_face<R, WAVE>(UL, L, ln.y & 0xffffu, g1.x, g1.y, sU, sP, uinf, acc,
-                                        cap, err));
+  perim = add(perim, smem_face<R, WAVE, PRIMS>(UL, L, ln.y & 0xffffu, g1.x, g1.y, sU, sP, uinf,
+                                               acc, cap, err));
   return perim;
 }
 
