@@ -84,6 +84,8 @@ def parse_args():
                    help="with --blocking 2: tile records by bulk copies (512 or 1024 cells)")
     p.add_argument("--closure", action="store_true",
                    help="step with the learned dissipation scale (untrained initial weights)")
+    p.add_argument("--closure-engine", default="mma.sync", choices=["mma.sync", "tcgen05"],
+                   help="tensor-core engine of the closure's MLP")
     p.add_argument("--variant", type=int, default=None,
                    help="force a step-kernel shape instead of autotuning")
     p.add_argument("--geometry", default="stored", choices=["stored", "vertex"],
@@ -312,6 +314,7 @@ def run_ours(args):
             raise SystemExit("--closure runs FP32, one step per launch")
         from paper_1408_5715_gb300 import closure_training as CT
         closure = B.Closure(CT.initial_theta(1, 0.3))
+        m.set_closure_engine(args.closure_engine)
     if args.geometry == "vertex":
         if prec != "f32" or args.blocking != 1 or args.closure:
             raise SystemExit("--geometry vertex runs FP32, one step per launch, no closure")
@@ -378,8 +381,8 @@ def run_ours(args):
                                 m.nodes()[1]) if args.geometry == "vertex" else "stored normals",
                    "dt": "CFL bound of the state at the start of each pair" if args.blocking == 2
                          else "CFL bound of the state at the start of each step",
-                   "closure": "learned dissipation scale, initial weights" if args.closure
-                              else None,
+                   "closure": f"learned dissipation scale, initial weights, MLP on "
+                              f"{args.closure_engine}" if args.closure else None,
                    "parallelism": f"replicas{world}" if world > 1 else "single",
                    "kernel_shape": tune,
                    "l2": "256 MB written between steps (L2 flushed); state+geometry "
@@ -966,9 +969,15 @@ def learned_leg(B, time_steps=2000):
     for tile in sorted({256, 512, 1024} | {(t + 31) // 32 * 32 for t in fit if 64 <= t <= 1024}):
         m.set_blocking(1, tile)
         by_tile[tile] = CT.step_cost(m, cl, steps=time_steps)["learned"]
+    best_tile = min(by_tile, key=by_tile.get)
+    # the same two forms with the MLP on tcgen05 (128-row MMAs into tensor memory)
+    m.set_closure_engine("tcgen05")
+    m.set_blocking(1, best_tile)
+    tc = {"tile_%d" % best_tile: CT.step_cost(m, cl, steps=time_steps)["learned"]}
     m.set_variant(keep_variant)
     m.set_blocking(1, keep_tile)
-    best_tile = min(by_tile, key=by_tile.get)
+    tc["two_passes"] = CT.step_cost(m, cl, steps=time_steps)["learned"]
+    m.set_closure_engine("mma.sync")
     learned_us = min(cost["learned"], by_tile[best_tile])
     n = mi.n_tri
     nbr, _, _ = m.export()
@@ -982,6 +991,7 @@ def learned_leg(B, time_steps=2000):
            "us_per_step_learned_two_passes": cost["learned"],
            "us_per_step_learned_tiles": by_tile,
            "us_per_step_learned": learned_us,
+           "us_per_step_learned_tcgen05": tc,
            "value": n / (learned_us * 1e-6), "unit": "cell-updates/s",
            "overhead": learned_us / cost["plain"],
            "mlp_rows_per_cell": rows / n,

@@ -75,6 +75,10 @@ extern "C" {
 #define FV_GEOM_STORED 0 /* per-cell records computed on the host (Sec. 7: precomputed) */
 #define FV_GEOM_VERTEX 1 /* formed from node coordinates on a fixed-point grid (Sec. 7) */
 
+/* Tensor-core engine of the learned closure's MLP (fv_mesh_set_closure_engine) */
+#define FV_CLOSURE_MMA_SYNC 0 /* warp-level mma.sync m16n8k16, registers */
+#define FV_CLOSURE_TCGEN05 1  /* tcgen05.mma, 128-row tiles, accumulator in TMEM */
+
 /* Wave speed in the Lax-Friedrichs dissipation (fv_mesh_set_wave_speed) */
 #define FV_WAVE_AVERAGE 0 /* |average normal velocity| + average sound speed (Sec. 6.2.2) */
 #define FV_WAVE_MAX 1     /* max over both sides of |normal velocity| + sound speed */
@@ -459,6 +463,18 @@ int fv_closure_eval(const fv_closure* closure, const float* features, float* sca
  * cell c at 3c + k. */
 int fv_closure_scales(fv_mesh* mesh, const void* U, const fv_closure* closure, float* scales,
                       void* stream);
+
+/* Tensor-core engine of the MLP in this mesh's learned steps (fv_step,
+ * fv_residual, fv_closure_scales; both the two-pass form and the one kernel
+ * on shape 7's tiles).  FV_CLOSURE_MMA_SYNC (default): a warp evaluates 16
+ * rows per mma.sync, accumulators in registers.  FV_CLOSURE_TCGEN05: 128
+ * threads evaluate 128 rows per tcgen05.mma from shared-memory operands into
+ * tensor memory (32 columns per 128 rows), each thread reading its row back;
+ * waits on the MMAs are bounded by fv_mesh_set_wait_limit (FV_ETIMEOUT /
+ * FV_ESTATE as for shape 5).  Both engines give the same bits.  The training
+ * kernels (fv_closure_loss_grad, fv_closure_eval) use mma.sync.  FV_EINVAL for
+ * an unknown engine. */
+int fv_mesh_set_closure_engine(fv_mesh* mesh, int32_t engine);
 
 /* Training signal of the closure: one forward-Euler step with fixed dt from
  * U0 (device FP32 [4n]) with the closure, compared with the target Ut:

@@ -77,6 +77,7 @@ def load():
             "fv_mesh_set_blocking": (ctypes.c_int, [_vp, _i32, _i32, _i32]),
             "fv_mesh_set_launch_chaining": (ctypes.c_int, [_vp, _i32]),
             "fv_mesh_set_wave_speed": (ctypes.c_int, [_vp, _i32]),
+            "fv_mesh_set_closure_engine": (ctypes.c_int, [_vp, _i32]),
             "fv_mesh_set_geometry": (ctypes.c_int, [_vp, _i32]),
             "fv_mesh_get_tiling": (ctypes.c_int, [_vp, _P(_i32), _P(_i32)]),
             "fv_mesh_tile_nodes": (ctypes.c_int, [_vp, _i32, _i64, _vp, _i64, _P(_i64), _vp]),
@@ -268,6 +269,12 @@ class Mesh:
         """'average' (the paper's interface averages, default) or 'max'
         (larger one-sided |u_n| + c, Rusanov)."""
         _check(load().fv_mesh_set_wave_speed(self._h, {"average": 0, "max": 1}[mode]))
+
+    def set_closure_engine(self, engine="mma.sync"):
+        """Tensor-core engine of the learned closure's MLP: "mma.sync" (warp
+        MMAs, the default) or "tcgen05" (128-row MMAs into tensor memory);
+        both give the same bits."""
+        _check(load().fv_mesh_set_closure_engine(self._h, {"mma.sync": 0, "tcgen05": 1}[engine]))
 
     def set_geometry(self, form: str):
         """'stored' (precomputed normals and 1/V, default) or 'vertex'

@@ -97,6 +97,7 @@ struct fv_closure {
     p.b2 = d_b + 32;
     p.w3 = d_b + 64;
     p.b3 = b3;
+    p.tc = false;
     return p;
   }
 };
@@ -124,6 +125,7 @@ struct fv_mesh {
   int pair_staged = 0;  // 1: bulk-copy staged two-step kernel
   bool chained = true;  // programmatic dependent launch of the step kernels
   int wave = FV_WAVE_AVERAGE;  // wave speed of the dissipation (fv_mesh_set_wave_speed)
+  int closure_engine = FV_CLOSURE_MMA_SYNC;  // fv_mesh_set_closure_engine
   int tiles_built = 0;  // tile size of the arrays below (0: none)
   uint2* d_cell_ln = nullptr;
   int* d_tile_info = nullptr;
@@ -477,13 +479,21 @@ fv::StepArgs base_args(const fv_mesh* m) {
   return a;
 }
 
+// The closure's parameters with the mesh's tensor-core engine.
+fv::ClosureParams closure_params(const fv_mesh* m, const fv_closure* cl) {
+  fv::ClosureParams p = cl->params();
+  p.tc = m->closure_engine == FV_CLOSURE_TCGEN05;
+  return p;
+}
+
 cudaError_t launch_mode(const fv_mesh* m, int mode, const fv::StepArgs& a, const fv_closure* cl,
                         cudaStream_t s) {
   if (cl && m->variant == fv::kFaceTileVariant)  // one launch on the tiles of shape 7
-    return fv::launch_step_closure_tile(mode, a, cl->params(), s);
+    return fv::launch_step_closure_tile(mode, a, closure_params(m, cl), s);
   if (cl) {
     // the scales of the state the stage evaluates, then the scaled step
-    cudaError_t e = fv::launch_face_scales(a, m->d_faces, m->n_faces, cl->params(), m->d_scale, s);
+    cudaError_t e =
+        fv::launch_face_scales(a, m->d_faces, m->n_faces, closure_params(m, cl), m->d_scale, s);
     if (e != cudaSuccess) return e;
     return fv::launch_step_scaled(mode, a, m->d_scale, s);
   }
@@ -498,7 +508,8 @@ void enqueue_steps(fv_mesh* m, void* U, int64_t j0, int64_t count, double cfl, d
   if (!cl && tiled_shape(m->variant) && count > 0) check_tile_smem(m, step_tile_smem(m));
   if (cl && m->variant == fv::kFaceTileVariant && count > 0) {
     if (m->tiles_built > 1024) invalid("the learned closure on tiles takes tiles of up to 1024 cells");
-    check_tile_smem(m, fv::closure_tile_smem_bytes(m->p_t1_cap, m->tiles_built));
+    check_tile_smem(m, fv::closure_tile_smem_bytes(m->p_t1_cap, m->tiles_built,
+                                                   m->closure_engine == FV_CLOSURE_TCGEN05));
   }
   for (int64_t j = j0; j < j0 + count; ++j) {
     fv::StepArgs a = base_args(m);
@@ -894,6 +905,16 @@ int fv_mesh_set_wave_speed(fv_mesh* mesh, int32_t mode) {
   });
 }
 
+int fv_mesh_set_closure_engine(fv_mesh* mesh, int32_t engine) {
+  return guarded([&] {
+    check_mesh(mesh);
+    if (engine != FV_CLOSURE_MMA_SYNC && engine != FV_CLOSURE_TCGEN05)
+      invalid("unknown closure engine");
+    mesh->closure_engine = engine;
+    mesh->drop_graph();
+  });
+}
+
 int fv_mesh_set_launch_chaining(fv_mesh* mesh, int32_t enable) {
   return guarded([&] {
     check_mesh(mesh);
@@ -1170,8 +1191,8 @@ int fv_residual(fv_mesh* mesh, const void* U, void* R, const fv_closure* closure
     if (shape == fv::kTileVariant) check_tile_smem(mesh, tile_smem(mesh));
     if (closure) {
       ensure_faces(mesh, s);
-      FV_CUDA(fv::launch_face_scales(a, mesh->d_faces, mesh->n_faces, closure->params(),
-                                     mesh->d_scale, s));
+      FV_CUDA(fv::launch_face_scales(a, mesh->d_faces, mesh->n_faces,
+                                     closure_params(mesh, closure), mesh->d_scale, s));
       FV_CUDA(fv::launch_step_scaled(fv::kModeResidual, a, mesh->d_scale, s));
     } else
       FV_CUDA(fv::launch_step(mesh->f64(), fv::kModeResidual, shape, a, s));
@@ -1868,7 +1889,8 @@ int fv_closure_scales(fv_mesh* mesh, const void* U, const fv_closure* closure, f
     ensure_faces(mesh, s);
     fv::StepArgs a = base_args(mesh);
     a.U = U;
-    FV_CUDA(fv::launch_face_scales(a, mesh->d_faces, mesh->n_faces, closure->params(), scales, s));
+    FV_CUDA(fv::launch_face_scales(a, mesh->d_faces, mesh->n_faces, closure_params(mesh, closure),
+                                   scales, s));
   });
 }
 

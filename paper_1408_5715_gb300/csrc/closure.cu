@@ -28,6 +28,7 @@
 #include "cell_math.cuh"
 #include "kernels.h"
 #include "launch_util.cuh"
+#include "tc_util.cuh"
 #include "tile_math.cuh"
 
 namespace fv {
@@ -176,6 +177,13 @@ __device__ __forceinline__ void tile_forward(const ClWarpSmem& w, int t, const C
   }
 }
 
+// Layer 3 in a fixed order of explicitly rounded operations, the same in
+// both tensor-core forms: four partial sums p_c over the column pairs
+// (nt * 8 + 2c, +1), nt = 0..3, then ((p0 + p1) + (p2 + p3)) + b3.
+__device__ __forceinline__ float out_pair(float acc, float g0, float g1, float w0, float w1) {
+  return add(acc, fma_(relu(g1), w1, mul(relu(g0), w0)));
+}
+
 // z of rows r and r+8 of a tile (all four lanes of a quad get both).
 __device__ __forceinline__ void tile_output(const float g[4][4], const float* w3, float b3,
                                             float& z0, float& z1) {
@@ -185,15 +193,15 @@ __device__ __forceinline__ void tile_output(const float g[4][4], const float* w3
 #pragma unroll
   for (int nt = 0; nt < 4; ++nt) {
     const int col = nt * 8 + 2 * c;
-    z0 += relu(g[nt][0]) * w3[col] + relu(g[nt][1]) * w3[col + 1];
-    z1 += relu(g[nt][2]) * w3[col] + relu(g[nt][3]) * w3[col + 1];
+    z0 = out_pair(z0, g[nt][0], g[nt][1], w3[col], w3[col + 1]);
+    z1 = out_pair(z1, g[nt][2], g[nt][3], w3[col], w3[col + 1]);
   }
-  z0 += __shfl_xor_sync(0xffffffffu, z0, 1);
-  z0 += __shfl_xor_sync(0xffffffffu, z0, 2);
-  z1 += __shfl_xor_sync(0xffffffffu, z1, 1);
-  z1 += __shfl_xor_sync(0xffffffffu, z1, 2);
-  z0 += b3;
-  z1 += b3;
+  z0 = add(z0, __shfl_xor_sync(0xffffffffu, z0, 1));
+  z0 = add(z0, __shfl_xor_sync(0xffffffffu, z0, 2));
+  z1 = add(z1, __shfl_xor_sync(0xffffffffu, z1, 1));
+  z1 = add(z1, __shfl_xor_sync(0xffffffffu, z1, 2));
+  z0 = add(z0, b3);
+  z1 = add(z1, b3);
 }
 
 // Scales of the warp's first 16 * ntile rows, from the features in w.feat
@@ -207,10 +215,9 @@ __device__ __forceinline__ void warp_mlp(ClWarpSmem& w, const ClFrag& fr, const 
     tile_forward(w, t, fr, a1, A2, g);
     float z0, z1;
     tile_output(g, w3, b3, z0, z1);
-    if (c == 0) {
-      w.s[16 * t + r] = scale_of(z0);
-      w.s[16 * t + r + 8] = scale_of(z1);
-    }
+    // lane c = 0 of a quad forms row r's scale, lane c = 1 row r + 8's
+    const float sv = scale_of((c & 1) ? z1 : z0);
+    if (c < 2) w.s[16 * t + r + 8 * c] = sv;
   }
 }
 
@@ -486,6 +493,272 @@ __global__ void __launch_bounds__(kClThreads) k_face_scales(StepArgs a, const Fa
   }
 }
 
+// ---------------------------------------------------------------------------
+// The MLP on the fifth-generation tensor cores (tcgen05), 128 rows at a time.
+// A group of 128 threads owns 128 rows, one per thread.  Each thread writes
+// its row's features (bfloat16, K columns 0..7; columns 8..10 hold 1.0
+// against the bias parts of W1) into the layer-1 A operand in shared memory;
+// one thread issues layer 1 (M 128, N 32, K 16) into the group's 32 TMEM
+// columns and commits to the group's mbarrier; every thread reads its row of
+// the accumulator (tcgen05.ld), applies ReLU, rounds to bfloat16 and writes
+// its row of the layer-2 A operand (K 0..31; columns 32..34 hold 1.0 against
+// the bias parts of W2); layer 2 (K 48, three MMAs) reuses the same TMEM
+// columns; each thread reads its row back and forms layer 3 in registers
+// (out_pair, the order of the mma.sync form).  The tensor core gives the
+// accumulators of the mma.sync form bit for bit (tested: both forms give the
+// same step), so the engines are interchangeable.
+// Operands are K-major without swizzling (tc_util.cuh): element (r, k) of an
+// operand of 16 k16 K columns sits at (r / 8) * 128 k16 + (k / 8) * 128 +
+// (r % 8) * 16 + (k % 8) * 2 bytes.  Waits are bounded (polls); one that
+// gives up sets the block's abort flag: the groups stop at their next
+// barrier, the block records error bit 2, waits (bounded) for its MMAs still
+// in flight (bit 4 if that gives up too) and frees its TMEM.
+// ---------------------------------------------------------------------------
+constexpr int kTcRows = 128;
+constexpr unsigned kTcCols = 32;  // TMEM columns of one group: a 128 x 32 FP32 accumulator
+
+struct __align__(128) TcRows {     // one group's A operands
+  unsigned char a2[kTcRows * 96];  // layer 2: 128 x 48 (sbo 768)
+  unsigned char a1[kTcRows * 32];  // layer 1: 128 x 16 (sbo 256)
+};
+
+struct __align__(128) TcWeights {  // B operands
+  unsigned char w2[32 * 96];       // layer 2: 32 x 48 (sbo 768)
+  unsigned char w1[32 * 32];       // layer 1: 32 x 16 (sbo 256)
+  float w3[32];
+};
+
+struct TcBlock {
+  uint64_t bar[2];  // per group
+  unsigned tmem;
+  int abort;
+};
+
+__device__ __forceinline__ unsigned tc_off(int r, int k, int sbo) {
+  return (unsigned)((r >> 3) * sbo + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ unsigned short bf16_bits(float x) {
+  return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+
+// The bias parts of b (hi, mid, lo: together its 24-bit significand), as
+// bias_parts above.
+__device__ __forceinline__ void bias3(float b, float p[3]) {
+  p[0] = __bfloat162float(__float2bfloat16_rn(b));
+  const float r1 = sub(b, p[0]);
+  p[1] = __bfloat162float(__float2bfloat16_rn(r1));
+  p[2] = sub(r1, p[1]);
+}
+
+// Barrier of group g's 128 threads (named barriers 1 and 2; literal ids, so
+// the kernels reserve three barriers, not sixteen).
+__device__ __forceinline__ void group_sync(int g) {
+  if (g == 0)
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+  else
+    asm volatile("bar.sync 2, 128;" ::: "memory");
+}
+
+// Block setup for `groups` groups of 128 threads (blockDim = 128 groups):
+// B operands, the constant columns of every row, TMEM (32 columns a group)
+// and the groups' mbarriers.  Ends with a block barrier.
+__device__ __forceinline__ void tc_setup(const ClosureParams& cp, TcWeights& w, TcRows* rows,
+                                         TcBlock& tb, int groups) {
+  const int tid = threadIdx.x, nthr = groups * kTcRows;
+  const unsigned short* w1 = reinterpret_cast<const unsigned short*>(cp.w1);
+  const unsigned short* w2 = reinterpret_cast<const unsigned short*>(cp.w2);
+  for (int i = tid; i < 32 * 16; i += nthr) {
+    const int n = i >> 4, k = i & 15;
+    unsigned short v = 0;
+    if (k < 8) {
+      v = __ldg(w1 + n * 8 + k);
+    } else if (k < 11) {
+      float p[3];
+      bias3(__ldg(cp.b1 + n), p);
+      v = bf16_bits(p[k - 8]);
+    }
+    *reinterpret_cast<unsigned short*>(w.w1 + tc_off(n, k, 256)) = v;
+  }
+  for (int i = tid; i < 32 * 48; i += nthr) {
+    const int n = i / 48, k = i % 48;
+    unsigned short v = 0;
+    if (k < 32) {
+      v = __ldg(w2 + n * 32 + k);
+    } else if (k < 35) {
+      float p[3];
+      bias3(__ldg(cp.b2 + n), p);
+      v = bf16_bits(p[k - 32]);
+    }
+    *reinterpret_cast<unsigned short*>(w.w2 + tc_off(n, k, 768)) = v;
+  }
+  // this thread's row: A1 columns 8..15 = (1, 1, 1, 0, ...), A2 columns 32..47 likewise
+  TcRows& r = rows[tid / kTcRows];
+  const int row = tid % kTcRows;
+  const uint4 ones = make_uint4(0x3F803F80u, 0x00003F80u, 0u, 0u);
+  *reinterpret_cast<uint4*>(r.a1 + tc_off(row, 8, 256)) = ones;
+  *reinterpret_cast<uint4*>(r.a2 + tc_off(row, 32, 768)) = ones;
+  *reinterpret_cast<uint4*>(r.a2 + tc_off(row, 40, 768)) = make_uint4(0u, 0u, 0u, 0u);
+  if (tid < 32) w.w3[tid] = __ldg(cp.w3 + tid);
+  if (tid < 32) tc_alloc(&tb.tmem, kTcCols * (unsigned)groups);  // warp 0
+  if (tid == 0) {
+    for (int g = 0; g < groups; ++g) mbar_init(&tb.bar[g], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    tb.abort = 0;
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+}
+
+// One group's state across its chunks of 128 rows.
+struct TcGroup {
+  int id;          // group index (0 or 1)
+  int row;         // this thread's row
+  unsigned tmem;   // the group's first TMEM column, lane 0
+  unsigned tlane;  // the same at this warp's 32 lanes
+  unsigned phase;  // parity of the group's mbarrier
+  bool pending;    // MMAs committed and not yet seen complete
+};
+
+__device__ __forceinline__ TcGroup tc_group(const TcBlock& tb) {
+  TcGroup G;
+  G.id = threadIdx.x / kTcRows;
+  G.row = threadIdx.x % kTcRows;
+  G.tmem = tb.tmem + kTcCols * (unsigned)G.id;
+  G.tlane = G.tmem + ((unsigned)(32 * ((threadIdx.x >> 5) & 3)) << 16);
+  G.phase = 0u;
+  G.pending = false;
+  return G;
+}
+
+// Layers 1-3 of the group's current 128 rows, whose features this group's
+// threads wrote to rows.a1.  Returns false (in every thread of the group)
+// when the block is aborting; else z of this thread's row, with ok = false
+// if a wait gave up (z is then not formed).
+__device__ __forceinline__ bool tc_mlp(TcGroup& G, TcRows& r, const TcWeights& w, TcBlock& tb,
+                                       float b3, unsigned limit, float& z, bool& ok) {
+  constexpr unsigned idesc = tc_idesc_bf16(kTcRows, 32);
+  volatile int* abort = &tb.abort;
+  fence_async_smem();
+  tc_fence_before();
+  group_sync(G.id);
+  if (*abort) return false;
+  if (G.row == 0) {
+    tc_fence_after();
+    tc_mma(G.tmem, tc_desc(smem_addr(r.a1), 128, 256), tc_desc(smem_addr(w.w1), 128, 256), idesc,
+           false);
+    tc_commit(&tb.bar[G.id]);
+  }
+  G.pending = true;
+  ok = mbar_wait(&tb.bar[G.id], G.phase, limit);
+  float v[32];
+  if (ok) {
+    G.phase ^= 1u;
+    G.pending = false;
+    tc_fence_after();
+    tc_ld32(G.tlane, v);
+    uint4* dst = reinterpret_cast<uint4*>(r.a2 + tc_off(G.row, 0, 768));
+#pragma unroll
+    for (int g = 0; g < 4; ++g)
+      dst[g * 8] = make_uint4(pack_bf16_relu(v[8 * g], v[8 * g + 1]),
+                              pack_bf16_relu(v[8 * g + 2], v[8 * g + 3]),
+                              pack_bf16_relu(v[8 * g + 4], v[8 * g + 5]),
+                              pack_bf16_relu(v[8 * g + 6], v[8 * g + 7]));
+  } else {
+    *abort = 1;
+  }
+  fence_async_smem();
+  tc_fence_before();
+  group_sync(G.id);
+  if (*abort) return false;
+  if (G.row == 0) {
+    tc_fence_after();
+    const unsigned a2 = smem_addr(r.a2), w2 = smem_addr(w.w2);
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      tc_mma(G.tmem, tc_desc(a2 + 256 * k, 128, 768), tc_desc(w2 + 256 * k, 128, 768), idesc,
+             k > 0);
+    tc_commit(&tb.bar[G.id]);
+  }
+  G.pending = true;
+  ok = mbar_wait(&tb.bar[G.id], G.phase, limit);
+  if (!ok) {
+    *abort = 1;  // the group stops at its next barrier
+    return true;
+  }
+  G.phase ^= 1u;
+  G.pending = false;
+  tc_fence_after();
+  tc_ld32(G.tlane, v);
+  float p[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    p[c] = 0.0f;
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+      const int col = nt * 8 + 2 * c;
+      p[c] = out_pair(p[c], v[col], v[col + 1], w.w3[col], w.w3[col + 1]);
+    }
+  }
+  z = add(add(add(p[0], p[1]), add(p[2], p[3])), b3);
+  return true;
+}
+
+// Block teardown: error bits of an abort, a bounded wait for each group's
+// MMAs still in flight, TMEM freed.  Every thread of the block calls it.
+__device__ __forceinline__ void tc_teardown(const TcGroup& G, TcBlock& tb, int groups, int* err,
+                                            unsigned drain_limit) {
+  if (tb.abort && G.row == 0) {
+    atomicOr(err, 2);
+    if (G.pending && !mbar_wait(&tb.bar[G.id], G.phase, drain_limit)) atomicOr(err, 4);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    tc_fence_after();
+    tc_dealloc(tb.tmem, kTcCols * (unsigned)groups);
+  }
+}
+
+// k_face_scales with the MLP on tcgen05: one group per block, 128 faces at
+// a time, persistent.
+__global__ void __launch_bounds__(kTcRows) k_face_scales_tc(StepArgs a, const FaceRec* faces,
+                                                            int64_t nf, ClosureParams cp,
+                                                            float* s_cf) {
+  chain_entry();
+  __shared__ TcRows rows;
+  __shared__ TcWeights w;
+  __shared__ TcBlock tb;
+  tc_setup(cp, w, &rows, tb, 1);
+  TcGroup G = tc_group(tb);
+  for (int64_t base = (int64_t)blockIdx.x * kTcRows; base < nf;
+       base += (int64_t)gridDim.x * kTcRows) {
+    const int64_t row = base + G.row;
+    const bool valid = row < nf;
+    FaceIn cur;
+    float f[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (valid) {
+      load_face(a, faces, row, cur);
+      const Prim<float> L = primitive<float>(cur.UL), W = primitive<float>(cur.UR);
+      face_features(cur.UL, L, cur.UR, W, cur.f.nx, cur.f.ny, face_len<float>(cur.f.nx, cur.f.ny),
+                    f);
+    }
+    *reinterpret_cast<uint4*>(rows.a1 + tc_off(G.row, 0, 256)) = pack_features(f);
+    float z;
+    bool ok;
+    if (!tc_mlp(G, rows, w, tb, cp.b3, a.wait_limit, z, ok)) break;
+    if (ok && valid) {
+      const float sv = scale_of(z);
+      s_cf[3 * (int64_t)(cur.f.a >> 2) + (cur.f.a & 3)] = sv;
+      if (cur.f.b >= 0 && index_ok(cur.f.b >> 2, a.n, a.err))
+        s_cf[3 * (int64_t)(cur.f.b >> 2) + (cur.f.b & 3)] = sv;
+    }
+  }
+  tc_teardown(G, tb, 1, a.err, a.drain_limit);
+}
+
 template <int MODE, bool COMP>
 __global__ void __launch_bounds__(kBlock) k_step_scaled(StepArgs a, const float* s_cf) {
   chain_entry();
@@ -660,6 +933,127 @@ __global__ void __launch_bounds__(THREADS) k_step_closure_tile(StepArgs a, Closu
   }
   if (MODE == kModeFE || MODE == kModeRK2b) {
     if (!ok) atomicOr(a.err, 1);
+    const double m = (double)block_min<float>(bmin);
+    if (threadIdx.x == 0) {
+      atomicMin(a.bmin_write, (unsigned long long)__double_as_longlong(m));
+      if (blockIdx.x == 0) {
+        *a.t_write = t + dt;
+        *a.bmin_reset = kInfBits;
+      }
+    }
+  }
+}
+
+// The learned step on shape 7's tiles with the MLP on tcgen05: as
+// k_step_closure_tile, but the block's 256 threads are two groups of 128
+// that take the tile's faces 128 at a time (group g: faces fb + 256 j + 128 g
+// + row), one face per thread, whose features, scale and flux stay in that
+// thread.  Dynamic shared memory: states, primitives and face fluxes as in
+// k_step_closure_tile, then the groups' operands and the weights.
+template <int MODE, bool COMP, int KMAX>
+__global__ void __launch_bounds__(2 * kTcRows) k_step_closure_tile_tc(StepArgs a,
+                                                                      ClosureParams cp) {
+  chain_entry();
+  constexpr int THREADS = 2 * kTcRows;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float4* sU = reinterpret_cast<float4*>(smem_raw);  // [t1_cap] states
+  float4* sP = sU + a.t1_cap;                          // [t1_cap] (u, v, p, c)
+  float4* sF = sP + a.t1_cap;                          // [3 tile] face flux values
+  const size_t tc_at = ((size_t)(2 * a.t1_cap + 3 * a.tile) * 16 + 127) & ~(size_t)127;
+  TcRows* rows = reinterpret_cast<TcRows*>(smem_raw + tc_at);  // [2]
+  TcWeights& w = *reinterpret_cast<TcWeights*>(rows + 2);
+  __shared__ TcBlock tb;
+  tc_setup(cp, w, rows, tb, 2);
+  TcGroup G = tc_group(tb);
+  const float4* __restrict__ U = static_cast<const float4*>(a.U);
+  const float4* __restrict__ geom = static_cast<const float4*>(a.geom);
+  float4* out = static_cast<float4*>(a.out);
+  const int t0 = blockIdx.x * a.tile;  // cell ids are 32-bit
+  const int nt = min(a.tile, (int)a.n - t0);
+  const int hs = __ldg(a.tile_info + 2 * blockIdx.x);
+  const int h1 = __ldg(a.tile_info + 2 * blockIdx.x + 1);
+  __shared__ double s_t, s_dt;
+  if (threadIdx.x == 0 && MODE != kModeResidual) block_dt(a, s_t, s_dt);
+  stage_states<float, THREADS, kStageBatch<float, KMAX>>(U, t0, nt, h1, a.halo_id + hs, sU, sP,
+                                                         a.n, a.err);
+  __syncthreads();
+  TcRows& r = rows[G.id];
+  const int fb = __ldg(a.tile_face_off + blockIdx.x), fe = __ldg(a.tile_face_off + blockIdx.x + 1);
+  for (int base = fb + G.id * kTcRows; base < fe; base += THREADS) {  // uniform in the group
+    const int f = base + G.row;
+    float feat[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    unsigned e = 0u, q = 0u, kv = 0u, v = 0u;
+    float4 UL = make_float4(0.f, 0.f, 0.f, 0.f), UR = UL;
+    Prim<float> L{0.f, 0.f, 0.f, 0.f}, W = L;
+    float nx = 0.f, ny = 0.f, len = 0.f;
+    bool use = false;
+    if (f < fe) {
+      const uint2 rec = __ldg(a.tile_face + f);
+      e = rec.x & 0xffffu, q = (rec.x >> 16) & 3u, kv = (rec.x >> 18) & 3u, v = rec.y;
+      use = index_ok(e, nt, a.err);
+      if (use) {
+        face_normal<float>(geom, t0 + (int)e, q, nx, ny);
+        UL = sU[e];
+        L = rec_prim<float>(sP[e]);
+        if (v < kGhostCodes) {
+          if (index_ok(v, nt + h1, a.err)) {
+            UR = sU[v];
+            W = rec_prim<float>(sP[v]);
+          } else {
+            UR = UL;
+            W = L;
+          }
+        } else {
+          UR = ghost<float>((int)v - 0x10000, UL, nx, ny, a.uinf_f);
+          W = primitive<float>(UR);
+        }
+        len = face_len<float>(nx, ny);
+        face_features(UL, L, UR, W, nx, ny, len, feat);
+      }
+    }
+    *reinterpret_cast<uint4*>(r.a1 + tc_off(G.row, 0, 256)) = pack_features(feat);
+    float z;
+    bool ok;
+    if (!tc_mlp(G, r, w, tb, cp.b3, a.wait_limit, z, ok)) break;
+    if (use && ok) {
+      float X[4];
+      face_flux_value<float, true>(UL, L, UR, W, nx, ny, len, scale_of(z), X);
+      sF[3 * e + q] = make_float4(X[0], X[1], X[2], X[3]);
+      if (v < (unsigned)nt) sF[3 * v + kv] = make_float4(-X[0], -X[1], -X[2], -X[3]);
+    }
+  }
+  tc_teardown(G, tb, 2, a.err, a.drain_limit);  // ends with a block barrier
+  const double t = MODE != kModeResidual ? s_t : 0.0, dt = MODE != kModeResidual ? s_dt : 0.0;
+  float bmin = INFINITY;
+  bool cell_ok = true;
+#pragma unroll
+  for (int k = 0; k < KMAX; ++k) {
+    const int e = threadIdx.x + k * THREADS;
+    if (e < nt) {
+      const int i = t0 + e;
+      CellIn<float> c;
+      c.g0 = __ldg(geom + 2 * i);
+      c.g1 = __ldg(geom + 2 * i + 1);
+      c.U = sU[e];
+      if (MODE == kModeRK2b) c.base = static_cast<const float4*>(a.Ubase)[i];
+      if (COMP && MODE != kModeResidual) c.lo = a.lo[i];
+      if (COMP && MODE == kModeRK2b) c.lo_stage = a.lo_stage[i];
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const float4 X = sF[3 * e + q];
+        acc[0] = add(acc[0], X.x);
+        acc[1] = add(acc[1], X.y);
+        acc[2] = add(acc[2], X.z);
+        acc[3] = add(acc[3], X.w);
+      }
+      const float perim = add(add(face_len<float>(c.g0.x, c.g0.y), face_len<float>(c.g0.z, c.g0.w)),
+                              face_len<float>(c.g1.x, c.g1.y));
+      finish_cell<float, MODE, COMP>(a, out, i, c, acc, perim, (float)dt, bmin, cell_ok);
+    }
+  }
+  if (MODE == kModeFE || MODE == kModeRK2b) {
+    if (!cell_ok) atomicOr(a.err, 1);
     const double m = (double)block_min<float>(bmin);
     if (threadIdx.x == 0) {
       atomicMin(a.bmin_write, (unsigned long long)__double_as_longlong(m));
@@ -1041,6 +1435,21 @@ cudaError_t launch_closure_scales(const StepArgs& a, const ClosureParams& cp, fl
 cudaError_t launch_face_scales(const StepArgs& a, const FaceRec* faces, int64_t nf,
                                const ClosureParams& cp, float* s_cf, cudaStream_t s) {
   if (nf <= 0) return cudaSuccess;
+  if (cp.tc) {
+    // eight resident blocks per SM (58 registers and 21 KB of shared memory
+    // allow eight; each holds kTcCols of the SM's 512 TMEM columns)
+    static unsigned cap = 0;
+    if (cap == 0) {
+      int dev = 0, sms = 0;
+      cudaError_t e = cudaGetDevice(&dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (e != cudaSuccess) return e;
+      cap = (unsigned)sms * 8u;
+    }
+    const int64_t want = (nf + kTcRows - 1) / kTcRows;
+    return launch_chained(k_face_scales_tc, (unsigned)std::min<int64_t>(want, cap), kTcRows, 0,
+                          s, a.chained, a, faces, nf, cp, s_cf);
+  }
   return launch_chained(k_face_scales, cl_grid(k_face_scales, 32, nf), kClThreads, 0, s,
                         a.chained, a, faces, nf, cp, s_cf);
 }
@@ -1064,15 +1473,20 @@ cudaError_t launch_scaled_t(const StepArgs& a, const float* s_cf, cudaStream_t s
 }
 }  // namespace
 
-size_t closure_tile_smem_bytes(int t1_cap, int tile) {
+size_t closure_tile_smem_bytes(int t1_cap, int tile, bool tc) {
+  if (tc) {
+    const size_t at = (tile_faces_smem_bytes(false, t1_cap, tile) + 127) & ~(size_t)127;
+    return at + 2 * sizeof(TcRows) + sizeof(TcWeights);
+  }
   return tile_faces_smem_bytes(false, t1_cap, tile) + (size_t)8 * sizeof(ClWarpSmem);
 }
 
 namespace {
 template <int MODE, bool COMP, int KMAX>
 cudaError_t launch_cl_tile_t(const StepArgs& a, const ClosureParams& cp, cudaStream_t s) {
-  auto k = k_step_closure_tile<MODE, COMP, 256, KMAX>;
-  const size_t smem = closure_tile_smem_bytes(a.t1_cap, a.tile);
+  auto k = cp.tc ? k_step_closure_tile_tc<MODE, COMP, KMAX>
+                 : k_step_closure_tile<MODE, COMP, 256, KMAX>;
+  const size_t smem = closure_tile_smem_bytes(a.t1_cap, a.tile, cp.tc);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int64_t tiles = (a.n + a.tile - 1) / a.tile;

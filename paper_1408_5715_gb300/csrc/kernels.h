@@ -137,6 +137,7 @@ struct ClosureParams {
   const float* b2;     // [32]
   const float* w3;     // [32]
   float b3;
+  bool tc;             // MLP on tcgen05 (else mma.sync): same bits
 };
 
 cudaError_t launch_step_closure(int mode, const StepArgs& a, const ClosureParams& cp,
@@ -157,7 +158,7 @@ cudaError_t launch_face_scales(const StepArgs& a, const FaceRec* faces, int64_t 
 cudaError_t launch_step_scaled(int mode, const StepArgs& a, const float* s_cf, cudaStream_t s);
 // The learned step on tiles with each face once (shape 7's tiles and face
 // lists; FP32; tiles of up to 1024 cells)
-size_t closure_tile_smem_bytes(int t1_cap, int tile);
+size_t closure_tile_smem_bytes(int t1_cap, int tile, bool tc);
 cudaError_t launch_step_closure_tile(int mode, const StepArgs& a, const ClosureParams& cp,
                                      cudaStream_t s);
 cudaError_t launch_closure_scales(const StepArgs& a, const ClosureParams& cp, float* s_out,

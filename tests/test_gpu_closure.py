@@ -341,3 +341,68 @@ def test_closure_on_tiles_gives_the_bits_of_the_two_passes(vortex_case, scheme, 
         outs.append((t, U))
     assert outs[0][0] == outs[1][0]
     assert torch.equal(outs[0][1], outs[1][1])
+
+
+def test_tcgen05_scales_match_oracle(orc, vortex_case):
+    # the MLP on tcgen05 (128-row MMAs into tensor memory), per face against
+    # the oracle as the mma.sync engine is checked above
+    mi, U0 = vortex_case
+    th, th64 = make_theta(3)
+    cl = B.Closure(th)
+    g = B.Mesh.from_input(mi, "f32")
+    g.set_closure_engine("tcgen05")
+    U = torch.tensor(U0, dtype=torch.float32, device="cuda")
+    s = cl.scales(g, U).cpu().numpy()
+    om = orc.Mesh(mi.xy, mi.tri, mi.canon, None, 0)
+    _, so = om.residual(U0, theta=th64, bf16_acts=True, return_scales=True)
+    lo, hi, det = om.closure_scale_intervals(U0, th64)
+    check_scales(s, so, lo, hi, det)
+
+
+@pytest.mark.parametrize("scheme", ["fe", "rk2"])
+@pytest.mark.parametrize("variant,tile", [(1, None), (7, 256), (7, 832)])
+def test_tcgen05_engine_gives_the_bits_of_mma_sync(vortex_case, scheme, variant, tile):
+    # both tensor-core engines, in both forms of the learned step (scale pass +
+    # scaled step; one kernel on shape 7's tiles), give the same bits
+    mi, U0 = vortex_case
+    th, _ = make_theta(6, scale=0.3)
+    cl = B.Closure(th)
+    outs = []
+    for engine in ("mma.sync", "tcgen05"):
+        g = B.Mesh.from_input(mi, "f32")
+        perm = g.renumber("hilbert")
+        g.set_variant(variant)
+        if tile:
+            g.set_blocking(1, tile)
+        g.set_closure_engine(engine)
+        U = torch.tensor(U0[perm], dtype=torch.float32, device="cuda")
+        s = cl.scales(g, U)
+        t = g.step(U, 110, 0.4, scheme=scheme, closure=cl)  # a captured graph and a tail
+        outs.append((t, U, s))
+    assert outs[0][0] == outs[1][0]
+    assert torch.equal(outs[0][2], outs[1][2])
+    assert torch.equal(outs[0][1], outs[1][1])
+
+
+@pytest.mark.parametrize("variant", [1, 7])
+def test_tcgen05_wait_timeout_is_reported(vortex_case, variant):
+    # a wait limit of 0 polls makes every wait on the MMAs give up: the step
+    # reports FV_ETIMEOUT after the block has drained its MMAs and freed its
+    # tensor memory, and the mesh and device stay usable
+    mi, U0 = vortex_case
+    th, _ = make_theta(6, scale=0.3)
+    cl = B.Closure(th)
+    g = B.Mesh.from_input(mi, "f32")
+    g.set_variant(variant)
+    g.set_closure_engine("tcgen05")
+    g.set_wait_limit(0)
+    U = torch.tensor(U0, dtype=torch.float32, device="cuda")
+    with pytest.raises(B.FVError) as e:
+        g.step(U, 3, 0.4, closure=cl)
+    assert e.value.code == B.FV_ETIMEOUT
+    g.set_wait_limit(1 << 24)
+    ref = B.Mesh.from_input(mi, "f32")
+    ref.set_variant(variant)
+    V, W_ = (torch.tensor(U0, dtype=torch.float32, device="cuda") for _ in range(2))
+    assert g.step(V, 5, 0.4, closure=cl) == ref.step(W_, 5, 0.4, closure=cl)
+    assert torch.equal(V, W_)
