@@ -5,14 +5,18 @@
 // s = 0.2 + 1.3 sigmoid(z) of the Lax-Friedrichs dissipation of Eq. 5.
 // Weights of the two hidden layers are bfloat16, accumulation is FP32.
 //
-// Tensor-core mapping: a warp updates 32 cells; their 3 faces are 96 rows
-// of the MLP, six 16-row tiles.  The features of all 96 rows are written to
-// shared memory as bfloat16; for each tile, layer 1 is one mma.sync
-// m16n8k16 per 8 hidden units (K = 8 features padded to 16), layer 2 two
-// per 8 units (K = 32), with the FP32 accumulators of layer 1 re-packed in
-// registers as the A operand of layer 2; layer 3 (32 -> 1) is an FP32 dot
-// product finished with two quad shuffles.  The scales go back through
-// shared memory to the threads that own the cells.
+// Each face is one row of the MLP, evaluated once: either by a pass over the
+// mesh's face list that writes the scale to both cells' slots, followed by
+// the step reading them (k_face_scales, k_step_scaled), or inside one kernel
+// on shape 7's tiles (k_step_closure_tile).  Two tensor-core engines give the
+// same bits.  mma.sync: a warp writes the bfloat16 features of 32 rows to
+// shared memory; per 16-row tile, layer 1 is one m16n8k16 per 8 hidden units
+// (K = 8 features, the bias parts, padding), layer 2 two per 8 units
+// (K = 32) plus one for its bias parts, with the FP32 accumulators of layer 1
+// re-packed in registers as the A operand of layer 2; layer 3 (32 -> 1) is an
+// FP32 dot product finished with two quad shuffles.  tcgen05: 128 rows per
+// MMA from shared-memory operands into tensor memory (the *_tc kernels
+// below).  The training kernels (loss, gradient, Adam) use mma.sync.
 //
 // Conservation: the features are computed with explicitly rounded operations
 // that give the same bits from either side of a face (the swap L <-> R,
@@ -242,120 +246,6 @@ __device__ __forceinline__ void cell_normals(const CellIn<float>& c, float nx[3]
   nx[2] = c.g1.x, ny[2] = c.g1.y;
 }
 
-// The fused step with the learned scale (FP32 meshes).  Persistent grid of
-// resident blocks; each warp takes 32 consecutive cells at a time.  A face
-// between two of the warp's cells is one MLP row, evaluated by the cell with
-// the lower number; the other cell reads that row's scale (the features, and
-// so the scale, are the same bits from either side).  In Hilbert or RCM order
-// about a third of a warp's 96 faces are such shared faces.
-template <int MODE, bool COMP>
-__global__ void __launch_bounds__(kClThreads) k_step_closure(StepArgs a, ClosureParams cp) {
-  __shared__ ClShared sh;
-  load_small_params(cp, sh);
-  ClFrag fr;
-  load_frags(cp, fr);
-  const float4* __restrict__ U = static_cast<const float4*>(a.U);
-  const float4* __restrict__ geom = static_cast<const float4*>(a.geom);
-  float4* out = static_cast<float4*>(a.out);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  ClWarpSmem& w = sh.warp[warp];
-  double t = 0.0, dt = 0.0;
-  if (MODE != kModeResidual) dt = step_dt(a, t);
-  float bmin = INFINITY;
-  bool ok = true;
-  const int64_t wstride = (int64_t)gridDim.x * kClWarps * 32;
-  for (int64_t base = ((int64_t)blockIdx.x * kClWarps + warp) * 32; base < a.n; base += wstride) {
-    const int64_t i = base + lane;
-    const bool valid = i < a.n;
-    CellIn<float> c;
-    float4 UR[3];
-    Prim<float> L, W[3];
-    float nx[3] = {0.f, 0.f, 0.f}, ny[3] = {0.f, 0.f, 0.f}, len[3];
-    int nb[3] = {-1, -1, -1};
-    unsigned own = 0u;  // bit k: this cell evaluates face k's row
-    if (valid) {
-      load_cell<float, MODE, COMP>(a, U, geom, i, c);
-      L = primitive<float>(c.U);
-      cell_normals(c, nx, ny);
-      nb[0] = c.n0, nb[1] = c.n1, nb[2] = c.n2;
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        UR[k] = neighbour_state<float>(c.U, nb[k], nx[k], ny[k], U, a.uinf_f, a.n, a.err);
-        W[k] = primitive<float>(UR[k]);
-        len[k] = face_len<float>(nx[k], ny[k]);
-        if (!(nb[k] >= base && nb[k] < i)) own |= 1u << k;
-      }
-    }
-    // the warp's rows, compacted: this lane's come at off .. off + popc(own)
-    const int cnt = __popc(own);
-    int off = cnt;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const int v = __shfl_up_sync(0xffffffffu, off, d);
-      if (lane >= d) off += v;
-    }
-    const int total = __shfl_sync(0xffffffffu, off, 31);
-    off -= cnt;
-    if (valid) {
-      int r = off;
-#pragma unroll
-      for (int k = 0; k < 3; ++k)
-        if ((own >> k) & 1u) {
-          float f[8];
-          face_features(c.U, L, UR[k], W[k], nx[k], ny[k], len[k], f);
-          w.feat[r++] = pack_features(f);
-        }
-    }
-    const int ntile = (total + 15) >> 4;
-    for (int j = total + lane; j < 16 * ntile; j += 32) w.feat[j] = make_uint4(0u, 0u, 0u, 0u);
-    __syncwarp();
-    warp_mlp(w, fr, sh.w3, cp.b3, ntile);
-    __syncwarp();
-    // each face's row: its own, or the one the neighbouring lane evaluated for
-    // the same face (the neighbour's face pointing back with the negated normal)
-    int row[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const bool borrowed = valid && !((own >> k) & 1u);
-      const int src = borrowed ? (int)(nb[k] - base) : lane;
-      const int off_s = __shfl_sync(0xffffffffu, off, src);
-      const unsigned own_s = __shfl_sync(0xffffffffu, own, src);
-      int kk = 0;
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        const int nq = __shfl_sync(0xffffffffu, nb[q], src);
-        const float xq = __shfl_sync(0xffffffffu, nx[q], src);
-        const float yq = __shfl_sync(0xffffffffu, ny[q], src);
-        if (nq == (int)i && xq == -nx[k] && yq == -ny[k]) kk = q;
-      }
-      row[k] = borrowed ? off_s + __popc(own_s & ((1u << kk) - 1u))
-                        : off + __popc(own & ((1u << k) - 1u));
-    }
-    if (valid) {
-      float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-      float perim = 0.0f;
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        face_flux_acc<float, true>(c.U, L, UR[k], W[k], nx[k], ny[k], len[k], w.s[row[k]], acc);
-        perim = add(perim, len[k]);
-      }
-      finish_cell<float, MODE, COMP>(a, out, i, c, acc, perim, (float)dt, bmin, ok);
-    }
-    __syncwarp();
-  }
-  if (MODE == kModeFE || MODE == kModeRK2b) {
-    if (!ok) atomicOr(a.err, 1);
-    const double m = (double)block_min<float>(bmin);
-    if (threadIdx.x == 0) {
-      atomicMin(a.bmin_write, (unsigned long long)__double_as_longlong(m));
-      if (blockIdx.x == 0) {
-        *a.t_write = t + dt;
-        *a.bmin_reset = kInfBits;
-      }
-    }
-  }
-}
-
 // The MLP alone on given FP32 features (rounded to bfloat16 like the step's).
 __global__ void __launch_bounds__(kClThreads) k_closure_eval(const float* feats, float* s_out,
                                                              int64_t rows, ClosureParams cp) {
@@ -379,49 +269,6 @@ __global__ void __launch_bounds__(kClThreads) k_closure_eval(const float* feats,
     __syncwarp();
     for (int j = lane; j < kRows; j += 32)
       if (base + j < rows) s_out[base + j] = w.s[j];
-    __syncwarp();
-  }
-}
-
-// Per-face scales the step would use for state U (3 per cell, face order).
-__global__ void __launch_bounds__(kClThreads) k_closure_scales(StepArgs a, ClosureParams cp,
-                                                               float* s_out) {
-  __shared__ ClShared sh;
-  load_small_params(cp, sh);
-  ClFrag fr;
-  load_frags(cp, fr);
-  const float4* __restrict__ U = static_cast<const float4*>(a.U);
-  const float4* __restrict__ geom = static_cast<const float4*>(a.geom);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  ClWarpSmem& w = sh.warp[warp];
-  const int64_t wstride = (int64_t)gridDim.x * kClWarps * 32;
-  for (int64_t base = ((int64_t)blockIdx.x * kClWarps + warp) * 32; base < a.n; base += wstride) {
-    const int64_t i = base + lane;
-    if (i < a.n) {
-      CellIn<float> c;
-      load_cell<float, kModeResidual, false>(a, U, geom, i, c);
-      const Prim<float> L = primitive<float>(c.U);
-      float nx[3], ny[3];
-      cell_normals(c, nx, ny);
-      const int nb[3] = {c.n0, c.n1, c.n2};
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const float4 UR = neighbour_state<float>(c.U, nb[k], nx[k], ny[k], U, a.uinf_f, a.n, a.err);
-        const Prim<float> W = primitive<float>(UR);
-        float f[8];
-        face_features(c.U, L, UR, W, nx[k], ny[k], face_len<float>(nx[k], ny[k]), f);
-        w.feat[k * 32 + lane] = pack_features(f);
-      }
-    } else {
-#pragma unroll
-      for (int k = 0; k < 3; ++k) w.feat[k * 32 + lane] = make_uint4(0u, 0u, 0u, 0u);
-    }
-    __syncwarp();
-    warp_mlp(w, fr, sh.w3, cp.b3);
-    __syncwarp();
-    if (i < a.n)
-#pragma unroll
-      for (int k = 0; k < 3; ++k) s_out[3 * i + k] = w.s[k * 32 + lane];
     __syncwarp();
   }
 }
@@ -1089,12 +936,6 @@ unsigned cl_grid(K kernel, int64_t items_per_warp_group, int64_t n) {
   return (unsigned)std::min<int64_t>(want, cap);
 }
 
-template <int MODE, bool COMP>
-cudaError_t launch_cl(const StepArgs& a, const ClosureParams& cp, cudaStream_t s) {
-  auto kernel = k_step_closure<MODE, COMP>;
-  kernel<<<cl_grid(kernel, 32, a.n), kClThreads, 0, s>>>(a, cp);
-  return cudaGetLastError();
-}
 
 // ---------------------------------------------------------------------------
 // Training: one-step loss and its gradient.
@@ -1366,20 +1207,6 @@ cudaError_t launch_pack_closure(const float* theta, unsigned* w1, unsigned* w2, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_step_closure(int mode, const StepArgs& a, const ClosureParams& cp,
-                                cudaStream_t s) {
-  if (a.n <= 0 && mode == kModeResidual) return cudaSuccess;
-  const bool comp = a.lo != nullptr;
-  switch (mode) {
-    case kModeFE: return comp ? launch_cl<kModeFE, true>(a, cp, s) : launch_cl<kModeFE, false>(a, cp, s);
-    case kModeRK2a:
-      return comp ? launch_cl<kModeRK2a, true>(a, cp, s) : launch_cl<kModeRK2a, false>(a, cp, s);
-    case kModeRK2b:
-      return comp ? launch_cl<kModeRK2b, true>(a, cp, s) : launch_cl<kModeRK2b, false>(a, cp, s);
-    case kModeResidual: return launch_cl<kModeResidual, false>(a, cp, s);
-    default: return cudaErrorInvalidValue;
-  }
-}
 
 int closure_grad_blocks() {
   static int cached = 0;
@@ -1425,12 +1252,6 @@ cudaError_t launch_closure_eval(const float* feats, float* s_out, int64_t rows,
   return cudaGetLastError();
 }
 
-cudaError_t launch_closure_scales(const StepArgs& a, const ClosureParams& cp, float* s_out,
-                                  cudaStream_t s) {
-  if (a.n <= 0) return cudaSuccess;
-  k_closure_scales<<<cl_grid(k_closure_scales, 32, a.n), kClThreads, 0, s>>>(a, cp, s_out);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_face_scales(const StepArgs& a, const FaceRec* faces, int64_t nf,
                                const ClosureParams& cp, float* s_cf, cudaStream_t s) {

@@ -140,8 +140,6 @@ struct ClosureParams {
   bool tc;             // MLP on tcgen05 (else mma.sync): same bits
 };
 
-cudaError_t launch_step_closure(int mode, const StepArgs& a, const ClosureParams& cp,
-                                cudaStream_t s);
 cudaError_t launch_closure_eval(const float* feats, float* s_out, int64_t rows,
                                 const ClosureParams& cp, cudaStream_t s);
 // The scales of a face list (each face once, both cells' slots s_cf[3c + k]
@@ -161,8 +159,6 @@ cudaError_t launch_step_scaled(int mode, const StepArgs& a, const float* s_cf, c
 size_t closure_tile_smem_bytes(int t1_cap, int tile, bool tc);
 cudaError_t launch_step_closure_tile(int mode, const StepArgs& a, const ClosureParams& cp,
                                      cudaStream_t s);
-cudaError_t launch_closure_scales(const StepArgs& a, const ClosureParams& cp, float* s_out,
-                                  cudaStream_t s);
 // Blocks the gradient kernel launches at most on this device.
 int closure_grad_blocks();
 // One-step loss and gradient; gpart [max_blocks * kClosureParams], lpart
