@@ -351,9 +351,14 @@ def run_ours(args):
     else:
         algo = VERTEX_BYTES if args.geometry == "vertex" else ALGO_BYTES[prec]
         kbytes = algo + (COMP_BYTES if comp else 0)
-        kfun = ("k_step_closure" if args.closure else
-                {5: "k_step_tma", 6: "k_step_tile", 7: "k_step_tile_faces"}.get(tune["variant"],
-                                                                               "k_step"))
+        if args.closure:
+            kfun = ("k_step_closure_tile" + ("_tc" if args.closure_engine == "tcgen05" else "")
+                    if tune["variant"] == 7 else
+                    "k_face_scales" + ("_tc" if args.closure_engine == "tcgen05" else "")
+                    + " + k_step_scaled")
+        else:
+            kfun = {5: "k_step_tma", 6: "k_step_tile", 7: "k_step_tile_faces"}.get(
+                tune["variant"], "k_step")
         kname = (f"{kfun}<{'float' if prec == 'f32' else 'double'}, "
                  f"{'RK2' if stages == 2 else 'FE'}, "
                  f"{'compensated' if comp else 'plain'}, shape {tune['variant']}"
