@@ -629,7 +629,7 @@ def extras(args, B, spec, mi, U0, U0p, perm, m32, S, U32_final, out):
         r["rel_l2_rho_vs_fp64"] = rel_l2_rho(U, U64)
         out[f"fp32_{other}"] = r
         del U64, U
-    # ---- the other single-mesh workload of the survey: the 1M channel (L2-sized,
+    # ---- the other single-mesh workload: the 1M channel (L2-sized,
     # 10,000 steps, compensated update) or the 16.8M square (the HBM headline)
     name = "channel_bump_1m" if args.workload != "channel_bump_1m" else "square_16m"
     spec2 = WORKLOADS[name]
