@@ -65,10 +65,15 @@ def clean_runs():
     out["vertex"] = U.cpu().numpy()
     rng = np.random.default_rng(3)
     cl = B.Closure((rng.normal(size=B.CLOSURE_PARAMS) * 0.3).astype(np.float32))
-    m = B.Mesh.from_input(mi, "f32")
-    U = torch.tensor(U0, dtype=torch.float32, device="cuda")
-    m.step(U, 30, 0.4, closure=cl)
-    out["closure"] = U.cpu().numpy()
+    for engine in ("mma.sync", "tcgen05"):
+        for variant in (1, 7):  # scale pass + scaled step; one kernel on tiles
+            m = B.Mesh.from_input(mi, "f32")
+            perm = m.renumber("hilbert")
+            m.set_variant(variant)
+            m.set_closure_engine(engine)
+            U = torch.tensor(U0[perm], dtype=torch.float32, device="cuda")
+            m.step(U, 30, 0.4, closure=cl)
+            out[f"closure_{engine}_v{variant}"] = U.cpu().numpy()
     meshes, states = [], []
     for k, (nx, ny) in enumerate(((20, 12), (44, 20), (30, 30))):
         mk = W.periodic_square(nx, ny, seed=40 + k)
