@@ -17,7 +17,7 @@ compensated FP32 update; the 1M-triangle channel with a circular-arc bump
 kernel; two steps per launch; normals from node coordinates; the 256-mesh
 batch; the learned closure; the Mach 3 forward-facing step; the FP64 CPU
 oracle timed on one host core; an end-to-end figure with host buffers.  The
-key figures are repeated in a short `summary` object at the end of the line.
+key figures are repeated in a short `summary` object right after the scalars.
 `--impl reference` times the CPU oracle alone.
 """
 from __future__ import annotations
@@ -412,6 +412,12 @@ def run_ours(args):
     if rank == 0 and not args.no_extras and world == 1:
         extras(args, B, spec, mi, U0, U0p, perm, m, S, U_final, out)
         out["summary"] = summary(out)
+        # the key figures right after the contract's scalars: the first
+        # kilobyte of the line carries them
+        head = ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "summary")
+        out = {**{k: out[k] for k in head if k in out},
+               **{k: v for k, v in out.items() if k not in head}}
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:
@@ -669,7 +675,8 @@ def extras(args, B, spec, mi, U0, U0p, perm, m32, S, U32_final, out):
 
 
 def summary(out):
-    """The key figures of the line in a few hundred bytes (printed last)."""
+    """The key figures of the line in a few hundred bytes (placed right after
+    the contract's scalar keys)."""
     def g(d, *path):
         for p in path:
             if not isinstance(d, dict) or p not in d:
