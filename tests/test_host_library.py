@@ -251,6 +251,17 @@ def test_two_step_blocking_validation():
     assert m32.tiling() == (6, 1024)
 
 
+def test_closure_engine_validation():
+    # the engine is a host-side setting: both known engines are accepted on a
+    # mesh that has never touched a device, anything else is FV_EINVAL
+    m = B.Mesh.from_input(W.periodic_square(8, 8, seed=1), "f32")
+    for engine in ("tcgen05", "mma.sync"):
+        m.set_closure_engine(engine)
+    for bad in (2, -1):
+        rc = B.load().fv_mesh_set_closure_engine(m._h, bad)
+        assert rc == B.FV_EINVAL and "engine" in B.load().fv_last_error().decode()
+
+
 def test_tile_halo_limit_is_reported():
     # tile-local ids are 16 bits: a tile whose rings exceed 65533 cells (a
     # huge tile in a shuffled numbering) is refused, not wrapped
