@@ -65,13 +65,13 @@ __device__ __forceinline__ void mma_bf16(float d[4], unsigned a0, unsigned a1, u
 
 __device__ __forceinline__ float relu(float x) { return x > 0.0f ? x : 0.0f; }
 
-// ReLU of two values packed to bfloat16: rounding keeps the sign, so the
-// ReLU of the rounded pair is the rounding of the ReLU (the next layer sees
-// the same values), with one packed maximum for both.
+// ReLU of two values packed to bfloat16 in one conversion that clamps
+// negative results to zero: rounding keeps the sign, so this is the rounding
+// of the ReLU (the next layer sees the same values).
 __device__ __forceinline__ unsigned pack_bf16_relu(float lo, float hi) {
-  const __nv_bfloat162 v =
-      __hmax2(__floats2bfloat162_rn(lo, hi), __floats2bfloat162_rn(0.0f, 0.0f));
-  return *reinterpret_cast<const unsigned*>(&v);
+  unsigned d;
+  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
 }
 
 // sigmoid(z) with the special-function unit's exponential and reciprocal
@@ -182,10 +182,11 @@ __device__ __forceinline__ void tile_forward(const ClWarpSmem& w, int t, const C
 }
 
 // Layer 3 in a fixed order of explicitly rounded operations, the same in
-// both tensor-core forms: four partial sums p_c over the column pairs
-// (nt * 8 + 2c, +1), nt = 0..3, then ((p0 + p1) + (p2 + p3)) + b3.
+// both tensor-core engines: four partial sums p_c, each a chain of fused
+// multiply-adds over the column pairs (nt * 8 + 2c, +1), nt = 0..3, then
+// ((p0 + p1) + (p2 + p3)) + b3.
 __device__ __forceinline__ float out_pair(float acc, float g0, float g1, float w0, float w1) {
-  return add(acc, fma_(relu(g1), w1, mul(relu(g0), w0)));
+  return fma_(relu(g1), w1, fma_(relu(g0), w0, acc));
 }
 
 // z of rows r and r+8 of a tile (all four lanes of a quad get both).
