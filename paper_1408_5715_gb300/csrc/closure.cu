@@ -358,9 +358,11 @@ __global__ void __launch_bounds__(kClThreads) k_face_scales(StepArgs a, const Fa
 // Operands are K-major without swizzling (tc_util.cuh): element (r, k) of an
 // operand of 16 k16 K columns sits at (r / 8) * 128 k16 + (k / 8) * 128 +
 // (r % 8) * 16 + (k % 8) * 2 bytes.  Waits are bounded (polls); one that
-// gives up sets the block's abort flag: the groups stop at their next
-// barrier, the block records error bit 2, waits (bounded) for its MMAs still
-// in flight (bit 4 if that gives up too) and frees its TMEM.
+// gives up (in any lane of a warp: the warp takes the result together) sets
+// its group's abort flag, which the group's threads read only after the
+// group's barrier, so the whole group stops there; the block records error
+// bit 2, waits (bounded) for the group's MMAs still in flight (bit 4 if that
+// gives up too) and frees its TMEM.
 // ---------------------------------------------------------------------------
 constexpr int kTcRows = 128;
 constexpr unsigned kTcCols = 32;  // TMEM columns of one group: a 128 x 32 FP32 accumulator
@@ -378,8 +380,8 @@ struct __align__(128) TcWeights {  // B operands
 
 struct TcBlock {
   uint64_t bar[2];  // per group
+  int abort[2];     // per group: written by the group's threads only
   unsigned tmem;
-  int abort;
 };
 
 __device__ __forceinline__ unsigned tc_off(int r, int k, int sbo) {
@@ -450,9 +452,11 @@ __device__ __forceinline__ void tc_setup(const ClosureParams& cp, TcWeights& w, 
   if (tid < 32) w.w3[tid] = __ldg(cp.w3 + tid);
   if (tid < 32) tc_alloc(&tb.tmem, kTcCols * (unsigned)groups);  // warp 0
   if (tid == 0) {
-    for (int g = 0; g < groups; ++g) mbar_init(&tb.bar[g], 1);
+    for (int g = 0; g < groups; ++g) {
+      mbar_init(&tb.bar[g], 1);
+      tb.abort[g] = 0;
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    tb.abort = 0;
   }
   fence_async_smem();
   tc_fence_before();
@@ -483,12 +487,12 @@ __device__ __forceinline__ TcGroup tc_group(const TcBlock& tb) {
 
 // Layers 1-3 of the group's current 128 rows, whose features this group's
 // threads wrote to rows.a1.  Returns false (in every thread of the group)
-// when the block is aborting; else z of this thread's row, with ok = false
-// if a wait gave up (z is then not formed).
+// when the group is stopping; else z of this thread's row, with ok = false
+// if a wait gave up (z is then not formed; the group stops at its next call).
 __device__ __forceinline__ bool tc_mlp(TcGroup& G, TcRows& r, const TcWeights& w, TcBlock& tb,
                                        float b3, unsigned limit, float& z, bool& ok) {
   constexpr unsigned idesc = tc_idesc_bf16(kTcRows, 32);
-  volatile int* abort = &tb.abort;
+  volatile int* abort = &tb.abort[G.id];
   fence_async_smem();
   tc_fence_before();
   group_sync(G.id);
@@ -500,7 +504,7 @@ __device__ __forceinline__ bool tc_mlp(TcGroup& G, TcRows& r, const TcWeights& w
     tc_commit(&tb.bar[G.id]);
   }
   G.pending = true;
-  ok = mbar_wait(&tb.bar[G.id], G.phase, limit);
+  ok = __all_sync(0xffffffffu, mbar_wait(&tb.bar[G.id], G.phase, limit));
   float v[32];
   if (ok) {
     G.phase ^= 1u;
@@ -531,7 +535,7 @@ __device__ __forceinline__ bool tc_mlp(TcGroup& G, TcRows& r, const TcWeights& w
     tc_commit(&tb.bar[G.id]);
   }
   G.pending = true;
-  ok = mbar_wait(&tb.bar[G.id], G.phase, limit);
+  ok = __all_sync(0xffffffffu, mbar_wait(&tb.bar[G.id], G.phase, limit));
   if (!ok) {
     *abort = 1;  // the group stops at its next barrier
     return true;
@@ -558,7 +562,7 @@ __device__ __forceinline__ bool tc_mlp(TcGroup& G, TcRows& r, const TcWeights& w
 // MMAs still in flight, TMEM freed.  Every thread of the block calls it.
 __device__ __forceinline__ void tc_teardown(const TcGroup& G, TcBlock& tb, int groups, int* err,
                                             unsigned drain_limit) {
-  if (tb.abort && G.row == 0) {
+  if (tb.abort[G.id] && G.row == 0) {
     atomicOr(err, 2);
     if (G.pending && !mbar_wait(&tb.bar[G.id], G.phase, drain_limit)) atomicOr(err, 4);
   }
